@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: one step = stage 0 indexing of both banks,
+stages 1-2 (ungapped extension of every pair of every shared key), survivor
+sort and stage 3.1 (small gapped extension), on the 10,000 x 100,000
+synthetic protein workload, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is ungapped pairs per second of the
+whole step with the banks' codes resident in device memory; ``e2e`` is the
+same metric with the codes copied from pinned host memory and the records
+copied back inside the timed region.  ``roofline`` rates the dominant kernel
+(stage 2) against the integer ALU peak; ``cpu_baseline`` times the CPU oracle
+on a bounded sample of the same workload.  ``--impl reference`` times the CPU
+oracle alone (the reference arm of this comparison).
+
+Multi-GPU (torchrun): every rank compares the shared bank 1 with its own
+bank-2 shard (weak scaling); no collective touches the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0804_3643_gb300 import synth  # noqa: E402
+
+WORKLOAD = "plastp_full"
+CELLS_PER_PAIR = 48        # ungapped window: 26 right + 22 left cells
+ALU_OPS_PER_PAIR = 2 * CELLS_PER_PAIR  # one add and one max per cell (int16)
+METRIC = "ungapped pairs/s and GCUPS at 1 GB300 (bit-exact), % of int/HBM roofline"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------------------
+# nvidia-smi clock sampler (runs during the timed region)
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path:
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [x for x in sm if x >= 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("[N/A]",))}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------
+def oracle_sample_keys(o1, o2, target_pairs: float, seed: int = 7):
+    n1 = np.diff(o1.idx.key_off)
+    n2 = np.diff(o2.idx.key_off)
+    order = np.random.default_rng(seed).permutation(len(n1))
+    keys, pairs = [], 0
+    for k in order:
+        p = int(n1[k] * n2[k])
+        if p == 0:
+            continue
+        keys.append(int(k))
+        pairs += p
+        if pairs >= target_pairs:
+            break
+    return sorted(keys), pairs
+
+
+def oracle_step(oracle, o1, o2, keys, threads):
+    """Stages 1-2 over the sampled keys, then stage 3.1 of their hits."""
+    h = oracle.ungapped(o1, o2, keys=keys, threads=threads)
+    oracle.small_gapped(o1, o2, h)
+    return len(h)
+
+
+def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int):
+    import oracle
+
+    threads = os.cpu_count() or 1
+    t0 = time.time()
+    o1 = oracle.make_bank(b1.codes, b1.seq_off)
+    o2 = oracle.make_bank(b2.codes, b2.seq_off)
+    t_index = time.time() - t0
+    # calibrate the sample: a small probe, then scale to the time budget
+    probe_keys, probe_pairs = oracle_sample_keys(o1, o2, 2e7, seed=3)
+    t0 = time.time()
+    oracle_step(oracle, o1, o2, probe_keys, threads)
+    rate = probe_pairs / max(time.time() - t0, 1e-3)
+    keys, pairs = oracle_sample_keys(o1, o2, rate * seconds_per_step)
+    for _ in range(warmup):
+        oracle_step(oracle, o1, o2, keys, threads)
+    times = []
+    for _ in range(steps):
+        t0 = time.time()
+        oracle_step(oracle, o1, o2, keys, threads)
+        times.append(time.time() - t0)
+    per = sum(times) / len(times)
+    return {
+        "value": pairs / per, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        "sample": f"{len(keys)} of 8800 keys drawn at random ({pairs:.3e} of "
+                  f"{float((np.diff(o1.idx.key_off) * np.diff(o2.idx.key_off)).sum()):.3e} pairs): stages 1-2 "
+                  f"and 3.1 of those keys per step, plain C -O2 with {threads} threads; stage-0 indexing "
+                  f"of the full banks took {t_index:.2f} s once, outside the timed steps",
+        "seconds_per_step": per,
+    }
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ungapped.cu", "ungapped.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_0804_3643_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """Per-launch DRAM traffic of the stage-2 kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ungapped_traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return t
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_0804_3643_gb300 import binding as B
+    from paper_0804_3643_gb300 import build
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if not os.path.exists(build.LIB):
+        build.build()
+    B.lib()
+    B.plast_set_schedule(1 if args.schedule == "per_key" else 0)
+
+    t0 = time.time()
+    b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale)
+    if rank == 0:
+        _, b2 = synth.workload(WORKLOAD, seed=1, scale=args.scale)
+    else:  # weak scaling: each rank its own bank-2 shard of the same size
+        _, b2 = synth.workload(WORKLOAD, seed=1 + rank, scale=args.scale)
+    log(f"[rank {rank}] banks generated in {time.time() - t0:.1f}s: {b1.n_seqs} x {b2.n_seqs} proteins, "
+        f"{len(b1.codes)} / {len(b2.codes)} residues")
+
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h1c, h1o = pin(b1.codes.view(np.int8)), pin(b1.seq_off)
+    h2c, h2o = pin(b2.codes.view(np.int8)), pin(b2.seq_off)
+    d1c, d1o = h1c.to(dev), h1o.to(dev)
+    d2c, d2o = h2c.to(dev), h2o.to(dev)
+    stream = torch.cuda.current_stream()
+
+    # size the output once
+    g1 = B.plast_index_bank(d1c, d1o)
+    g2 = B.plast_index_bank(d2c, d2o)
+    pairs = B.plast_pair_count(g1, g2)
+    recs, n_ung = B.plast_search(g1, g2)
+    cap = int(recs.shape[0] * 1.05) + 1024
+    out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device=dev)
+    n_recs = recs.shape[0]
+    del recs
+    nb_gb = (g1.n_positions + g2.n_positions) * CELLS_PER_PAIR / 1e9
+    g1.free()
+    g2.free()
+    torch.cuda.synchronize()
+    log(f"[rank {rank}] pairs/step {pairs:.4e}, stage-2 hits {n_ung}, records {n_recs}")
+
+    stage_ms = []
+
+    def step(c1, o1_, c2, o2_):
+        a = B.plast_index_bank(c1, o1_)
+        b = B.plast_index_bank(c2, o2_)
+        r, _ = B.plast_search(a, b, out=out, cap=cap)
+        stage_ms.append(B.plast_stage_times())
+        a.free()
+        b.free()
+        return r
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident arm
+    B.plast_set_timing(True)
+    for _ in range(args.warmup):
+        step(d1c, d1o, d2c, d2o)
+    stage_ms.clear()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        launches0 = B.plast_kernel_launches()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(d1c, d1o, d2c, d2o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = B.plast_kernel_launches() - launches0
+        barrier()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    clocks = clk.summary()
+    ung_ms = statistics.mean(s["stage2_kernel"] for s in stage_ms)
+    stages = {name: round(statistics.mean(s[name] for s in stage_ms), 3) for name in B.STAGES}
+
+    # ---- end-to-end arm: host buffers in, records out
+    rec_bytes = n_recs * B.GAPPED_BYTES
+    host_out = torch.empty(max(rec_bytes, 1), dtype=torch.uint8).pin_memory()
+
+    def e2e_step():
+        c1, o1_ = h1c.to(dev, non_blocking=True), h1o.to(dev, non_blocking=True)
+        c2, o2_ = h2c.to(dev, non_blocking=True), h2o.to(dev, non_blocking=True)
+        r = step(c1, o1_, c2, o2_)
+        host_out[: r.numel()].copy_(r.reshape(-1), non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    B.plast_set_timing(False)
+    h2d = int(h1c.numel() + h1o.numel() * 8 + h2c.numel() + h2o.numel() * 8)
+
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peak_ops = n_sm * 128 * 2 * sm_max * 1e6  # int16 lanes: 128 per SM per clock, 2 per 32-bit lane
+    achieved_ops = pairs * ALU_OPS_PER_PAIR / (ung_ms / 1e3)
+    tr = committed_traffic()
+    traffic = None
+    if tr is not None:
+        traffic = tr["dram_bytes_per_pair"] * pairs
+    result = {
+        "metric": METRIC,
+        "value": world * pairs / (ms_step / 1e3),
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int16",
+        "data": "synthetic",
+        "config": {
+            "workload": f"PLAST-P full scale: {b1.n_seqs} x {b2.n_seqs} synthetic proteins "
+                        f"({len(b1.codes)} / {len(b2.codes)} residues), 5% planted homologs, seed 1",
+            "step": "index both banks + ungapped all pairs + sort + small gapped",
+            "pairs_per_step": pairs,
+            "stage2_hits_per_step": n_ung,
+            "records_per_step": n_recs,
+            "params": B.plast_default_params().as_dict(),
+            "schedule": args.schedule,
+            "l2": f"inputs larger than L2 (129 MB): {nb_gb:.2f} GB of neighbourhood arrays rebuilt and "
+                  "read every step, no explicit flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        },
+        "gcups": world * pairs * CELLS_PER_PAIR / (ms_step / 1e3) / 1e9,
+        "stage_ms": stages,
+        "roofline": {
+            "bound": "alu",
+            "kernel": "k_ungapped",
+            "achieved": achieved_ops / 1e12,
+            "peak": peak_ops / 1e12,
+            "unit": "Tops/s (int16)",
+            "frac": achieved_ops / peak_ops,
+            "traffic": traffic,
+            "ops_per_pair": ALU_OPS_PER_PAIR,
+            "kernel_ms": ung_ms,
+            "peak_basis": f"{n_sm} SMs x 128 int32 lanes x 2 int16 halves x {sm_max:.0f} MHz (max SM clock)",
+            "frac_at_measured_clock": (achieved_ops / (n_sm * 256 * clocks["sm_mhz"] * 1e6)
+                                       if clocks.get("sm_mhz") else None),
+        },
+        "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(rec_bytes), "ms_per_step": e2e_ms},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
+    }
+    return result, (b1, b2)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_key"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the CPU oracle, on rank 0 only
+        if rank != 0:
+            return
+        b1, b2 = synth.workload(WORKLOAD, seed=1, scale=args.scale)
+        per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        cb = run_oracle(b1, b2, per_step, args.steps, args.warmup)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"PLAST-P full scale: {b1.n_seqs} x {b2.n_seqs} synthetic proteins, seed 1",
+                       "step": "CPU oracle: stages 1-2 and 3.1 over a bounded random sample of keys"},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    result, banks = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0)
+            result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * plast.h -- C ABI of the GB300 (sm_103a) implementation of the hot path of
+ * PLAST's bank-to-bank comparison (Nguyen & Lavenier, "Fine-grained
+ * parallelization of similarity search between protein sequences", INRIA
+ * RR-6513, 2008).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer to sequence data, offsets or records is a DEVICE pointer
+ *   on the current CUDA device (for example a torch tensor's data_ptr()).
+ *   Scalar outputs (n_out, n_aa_out, bank handles) are HOST pointers.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is queued on it; calls that return a count read that
+ *   count back and therefore synchronise with the stream before returning.
+ * - The caller owns every input and output buffer.  The library owns
+ *   `plast_bank` objects (freed by plast_bank_free) and the scratch memory
+ *   it allocates inside a call (stream-ordered, returned before the call
+ *   returns).
+ * - Return value: PLAST_OK (0) or a negative PLAST_E_* code; plast_strerror
+ *   names it.  On PLAST_E_CAPACITY, *n_out holds the number of records the
+ *   call needs and no record has been written.
+ * - Residue codes (int8): 0..19 = A R N D C Q E G H I L K M F P S T W Y V,
+ *   20 = stop '*' (translated banks).  Nucleotide codes (uint8): A C G T =
+ *   0 1 2 3.  Any other code is PLAST_E_INVALID.
+ * - Positions in records are 0-based and local to their sequence; seq1 /
+ *   seq2 index the sequences of bank 1 / bank 2.
+ */
+#ifndef PLAST_H
+#define PLAST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLAST_OK 0
+#define PLAST_E_INVALID (-1)  /* bad argument, code, offset or parameter */
+#define PLAST_E_OOM (-2)      /* a device allocation failed */
+#define PLAST_E_CAPACITY (-3) /* output buffer too small; *n_out = needed */
+#define PLAST_E_CUDA (-4)     /* a CUDA runtime call or kernel failed */
+#define PLAST_E_TIMEOUT (-5)  /* a bounded device-side wait expired */
+
+#define PLAST_NKEYS 8800 /* subset-seed keys: 20 * 2 * 11 * 20 */
+#define PLAST_MAX_STAGES 5 /* stage intervals reported by plast_stage_times */
+
+/* Opaque, device-resident, library-owned indexed bank. */
+typedef struct plast_bank plast_bank;
+
+/*
+ * Parameters (Section 3.2: thresholds S1, S2; Section 3.3.2 neighbourhoods;
+ * Section 3.3.4 small gapped extension).
+ *   w          seed length; must be 4 (the subset seed of Section 3.3.1)
+ *   nl, nr     neighbourhood residues left of the seed start and right of
+ *              the seed end; must be 22 and 22 (the 48-residue window of
+ *              Annex 4, run as 26 cells right then 22 cells left)
+ *   s1         ungapped threshold: a hit is kept if its score >= s1
+ *   lg         residues per side of the small gapped extension; must be 64
+ *   band       half width of the diagonal band; must be 8
+ *   gap_open, gap_extend  a gap of length k costs gap_open + k*gap_extend
+ *              (both >= 0)
+ *   s2         small gapped threshold: kept if the score >= s2
+ * Defaults (plast_default_params): 4, 22, 22, 38, 64, 8, 11, 1, 47.
+ */
+typedef struct {
+  int32_t w, nl, nr, s1, lg, band, gap_open, gap_extend, s2;
+} plast_params;
+
+/*
+ * Ungapped hit (stage 2).  score = R + max(0, L) as defined by Section
+ * 3.3.3 and the loop of Annex 4; rlen = 1 + index of the first right cell
+ * reaching R (0 if R = 0); llen = number of left cells up to the first one
+ * reaching the final maximum (0 if the left part adds nothing).  20 bytes.
+ */
+typedef struct {
+  int32_t seq1, pos1, seq2, pos2;
+  int16_t score;
+  int8_t rlen, llen;
+} plast_hit;
+
+/*
+ * Small gapped extension (stage 3.1, Section 3.3.4): score = right side +
+ * left side, ungapped = the stage-2 score of the same hit, (r_i, r_j) and
+ * (l_i, l_j) = residues of bank 1 / bank 2 covered by the best cell of the
+ * right and left side (first maximum in row-major order).  28 bytes.
+ */
+typedef struct {
+  int32_t seq1, pos1, seq2, pos2;
+  int16_t score, ungapped;
+  int16_t r_i, r_j, l_i, l_j;
+} plast_gapped;
+
+/* Fill *p with the default parameters listed above. */
+void plast_default_params(plast_params* p);
+
+/*
+ * Six-frame translation of a nucleotide bank (Section 6, TPLAST-N: a protein
+ * bank is compared with the six translated frames of a DNA bank).
+ *   dna         [contig_off[n_contigs]] nucleotide codes 0..3 (device)
+ *   contig_off  [n_contigs + 1] int64 offsets, contig_off[0] = 0 (device)
+ *   aa_out      [aa_cap] residue codes 0..20 written here (device)
+ *   seq_off_out [6 * n_contigs + 1] int64 offsets of the translated
+ *               sequences (device)
+ *   frame_meta_out [6 * n_contigs][2] int32 (contig, frame) per sequence,
+ *               frame in +1 +2 +3 -1 -2 -3 (device)
+ *   *n_aa_out   number of residues written (host)
+ * Frames +f read the contig from offset f-1, frames -f its reverse
+ * complement from offset f-1; only whole codons; standard genetic code
+ * (NCBI table 1), stops as code 20.  Sequences are ordered contig by contig,
+ * frames +1 +2 +3 -1 -2 -3.  Errors: PLAST_E_INVALID for a code > 3 or bad
+ * offsets; PLAST_E_CAPACITY if aa_cap is too small (*n_aa_out = needed).
+ */
+int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,
+                     int64_t aa_cap, int64_t* seq_off_out, int32_t* frame_meta_out, int64_t* n_aa_out,
+                     void* stream);
+
+/*
+ * Stage 0 (Section 3.3.1): index a bank by the subset seed.  Every word of
+ * four residues inside one sequence (words holding a stop are skipped) is
+ * mapped to its key; the positions of each key are kept in increasing
+ * order, and the 48-residue neighbourhood of each position (Section 3.3.2)
+ * is laid out next to it for stage 2.
+ *   codes   [seq_off[n_seqs]] residue codes 0..20 (device)
+ *   seq_off [n_seqs + 1] int64 offsets, seq_off[0] = 0, non-decreasing
+ *           (device); total length < 2^31 - 2^26
+ *   params  may be NULL (defaults)
+ *   *out    receives the new bank (host)
+ * The inputs are copied; the caller may free them after the call.
+ * Errors: PLAST_E_INVALID (code outside 0..20, bad offsets, n_seqs < 0,
+ * unsupported params), PLAST_E_OOM, PLAST_E_CUDA.
+ */
+int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs, const plast_params* params,
+                     void* stream, plast_bank** out);
+
+/* Release a bank and its device memory (NULL is ignored). */
+void plast_bank_free(plast_bank* bank);
+
+/* Number of sequences / residues / indexed positions of a bank (host). */
+int plast_bank_stats(const plast_bank* bank, int32_t* n_seqs, int64_t* n_residues, int64_t* n_positions);
+
+/*
+ * Copy a bank's index out: key_off [8801] int64 and pos [n] int32 global
+ * residue indices (into the concatenated codes given to plast_index_bank),
+ * increasing within each key (device pointers).  Section 3.3.1's look-up
+ * table and linked lists in CSR form.  PLAST_E_CAPACITY if cap < n.
+ */
+int plast_bank_export_index(const plast_bank* bank, int64_t* key_off, int32_t* pos, int64_t cap, int64_t* n_out,
+                            void* stream);
+
+/*
+ * Stages 1-2 (Sections 3.3.2-3.3.3, Annex 4): for every key present in both
+ * banks, every pair of occurrences gets an ungapped extension; pairs scoring
+ * >= params->s1 are written to out[0 .. *n_out) sorted by
+ * (seq1, pos1, seq2, pos2).  out: [cap] plast_hit (device).
+ * Errors: PLAST_E_INVALID, PLAST_E_CAPACITY (*n_out = needed), PLAST_E_OOM,
+ * PLAST_E_CUDA, PLAST_E_TIMEOUT.
+ */
+int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_hit* out,
+                   int64_t cap, int64_t* n_out, void* stream);
+
+/*
+ * Number of ungapped pairs (sum over keys of n1 * n2) the two banks give;
+ * pure host arithmetic on the indexes, no device work.
+ */
+int64_t plast_pair_count(const plast_bank* b1, const plast_bank* b2);
+
+/*
+ * Stage 3.1 (Section 3.3.4, Section 5.2.2): small gapped extension of
+ * n_in ungapped hits `in` (device; positions must be seed starts of the two
+ * banks).  Hits scoring >= params->s2 are written to out in input order.
+ * out: [cap] plast_gapped (device).  Errors as plast_ungapped.
+ */
+int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+                       const plast_hit* in, int64_t n_in, plast_gapped* out, int64_t cap, int64_t* n_out,
+                       void* stream);
+
+/*
+ * Stages 1-3.1 in one call (Section 3.2's loop without stages 3.2 and 4):
+ * ungapped extension of every pair, small gapped extension of the hits
+ * scoring >= s1, and the records scoring >= s2 written to out sorted by
+ * (seq1, pos1, seq2, pos2).  *n_ungapped_out (host, may be NULL) receives
+ * the number of stage-2 hits.  Errors as plast_ungapped.
+ */
+int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
+                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream);
+
+/*
+ * Scheduling of stage 2.  0 (default): one persistent launch, CTAs pull
+ * profile tiles from a device work queue, largest first.  1: the plain
+ * form, one launch per key.  Applies to later calls in this process.
+ */
+int plast_set_schedule(int mode);
+
+/*
+ * Instrumentation (no effect on results).
+ * plast_set_timing(1) makes later plast_ungapped / plast_small_gapped /
+ * plast_search calls of the calling thread record CUDA events on their stream
+ * at the stage boundaries; plast_stage_times then fills ms[0 .. n) with the
+ * device time of the last call's intervals (-1 where not recorded):
+ *   ms[0] work list upload   ms[1] stage-2 kernel   ms[2] survivor count read
+ *   and sort                 ms[3] stage-3.1 kernel ms[4] threshold scan and
+ *   record write-out.
+ * plast_kernel_launches returns how many kernels the library has launched in
+ * this process so far.
+ */
+int plast_set_timing(int on);
+int plast_stage_times(double* ms, int n);
+long long plast_kernel_launches(void);
+
+/* Static name of a PLAST_OK / PLAST_E_* return code. */
+const char* plast_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLAST_H */

@@ -96,7 +96,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_gapped_side.restype = i32
         L.oracle_small_gapped_pair.argtypes = [P, i64, i64, P, i64, i64, P, P, P, P, P]
         L.oracle_small_gapped_pair.restype = i32
-        L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, i32, P, P]
+        L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, P, i32, P, P]
         L.oracle_ungapped.restype = i64
         L.oracle_small_gapped.argtypes = [P, P, P, P, P, P, i64, P]
         L.oracle_small_gapped.restype = i64
@@ -194,18 +194,23 @@ def make_bank(codes, seq_off) -> Bank:
 
 
 def ungapped(b1: Bank, b2: Bank, params: Params = Params(), key_lo: int = 0, key_hi: int = NKEYS,
-             threads: int = 1, return_pairs: bool = False):
-    """Stages 1-2 over keys [key_lo, key_hi): ungapped hits with U >= s1,
-    sorted by (seq1, pos1, seq2, pos2)."""
+             threads: int = 1, return_pairs: bool = False, keys=None):
+    """Stages 1-2 over keys [key_lo, key_hi) (or over the key list ``keys``):
+    ungapped hits with U >= s1, sorted by (seq1, pos1, seq2, pos2)."""
     b1.indexed()
     b2.indexed()
+    klist = None
+    if keys is not None:
+        klist = np.ascontiguousarray(keys, dtype=np.int32)
+        key_lo, key_hi = 0, len(klist)
     out = ctypes.c_void_p()
     pairs = ctypes.c_int64()
     prm = params.c()
     L = lib()
     n = L.oracle_ungapped(_p(b1.codes), _p(b1.seq_off), b1.n_seqs, _p(b1.idx.key_off), _p(b1.idx.pos),
                           _p(b2.codes), _p(b2.seq_off), b2.n_seqs, _p(b2.idx.key_off), _p(b2.idx.pos),
-                          ctypes.byref(prm), key_lo, key_hi, threads, ctypes.byref(out), ctypes.byref(pairs))
+                          ctypes.byref(prm), key_lo, key_hi, _p(klist) if klist is not None else None, threads,
+                          ctypes.byref(out), ctypes.byref(pairs))
     buf = (ctypes.c_char * (n * HIT_DTYPE.itemsize)).from_address(out.value) if n else b""
     hits = np.frombuffer(bytes(buf), dtype=HIT_DTYPE).copy()
     L.oracle_free(out)

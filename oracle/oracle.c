@@ -360,6 +360,7 @@ typedef struct {
   const bank_view* b1;
   const bank_view* b2;
   const oracle_params* prm;
+  const int32_t* key_list; /* NULL: keys are the counter values themselves */
   int32_t key_hi;
   int32_t* next_key;
   pthread_mutex_t* lock;
@@ -382,9 +383,10 @@ static void* ungapped_worker(void* arg) {
   const bank_view* b2 = j->b2;
   for (;;) {
     pthread_mutex_lock(j->lock);
-    int32_t k = (*j->next_key)++;
+    int32_t at = (*j->next_key)++;
     pthread_mutex_unlock(j->lock);
-    if (k >= j->key_hi) break;
+    if (at >= j->key_hi) break;
+    int32_t k = j->key_list ? j->key_list[at] : at;
     for (int64_t u = b1->key_off[k]; u < b1->key_off[k + 1]; u++) {
       int64_t g1 = b1->pos[u];
       int32_t q1 = seq_of(b1->seq_off, b1->n_seqs, g1);
@@ -416,13 +418,15 @@ static void* ungapped_worker(void* arg) {
   return NULL;
 }
 
-/* Ungapped hits of all keys in [key_lo, key_hi).  *out is malloc'ed (free it
+/* Ungapped hits of all keys in [key_lo, key_hi), or, when key_list is not
+ * NULL, of the keys key_list[key_lo .. key_hi).  *out is malloc'ed (free it
  * with oracle_free); *pairs receives the number of pairs extended.  Returns
  * the number of hits. */
 int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n1, const int64_t* key_off1,
                         const int32_t* pos1, const int8_t* codes2, const int64_t* seq_off2, int32_t n2,
                         const int64_t* key_off2, const int32_t* pos2, const oracle_params* prm, int32_t key_lo,
-                        int32_t key_hi, int32_t n_threads, oracle_hit** out, int64_t* pairs) {
+                        int32_t key_hi, const int32_t* key_list, int32_t n_threads, oracle_hit** out,
+                        int64_t* pairs) {
   bank_view b1 = {codes1, seq_off1, n1, key_off1, pos1};
   bank_view b2 = {codes2, seq_off2, n2, key_off2, pos2};
   if (n_threads < 1) n_threads = 1;
@@ -435,6 +439,7 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
     jobs[t].b1 = &b1;
     jobs[t].b2 = &b2;
     jobs[t].prm = prm;
+    jobs[t].key_list = key_list;
     jobs[t].key_hi = key_hi;
     jobs[t].next_key = &next_key;
     jobs[t].lock = &lock;

@@ -1,0 +1,316 @@
+"""Python binding of the C ABI in include/plast.h (ctypes; argument marshalling
+only).  Every function keeps the C name.  Device memory and streams come from
+PyTorch; every computation runs in libplast.so's CUDA kernels.  There is no
+CPU path: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+PLAST_OK = 0
+PLAST_E_INVALID = -1
+PLAST_E_OOM = -2
+PLAST_E_CAPACITY = -3
+PLAST_E_CUDA = -4
+PLAST_E_TIMEOUT = -5
+NKEYS = 8800
+
+HIT_DTYPE = np.dtype(
+    [("seq1", "<i4"), ("pos1", "<i4"), ("seq2", "<i4"), ("pos2", "<i4"),
+     ("score", "<i2"), ("rlen", "i1"), ("llen", "i1")])
+GAPPED_DTYPE = np.dtype(
+    [("seq1", "<i4"), ("pos1", "<i4"), ("seq2", "<i4"), ("pos2", "<i4"),
+     ("score", "<i2"), ("ungapped", "<i2"), ("r_i", "<i2"), ("r_j", "<i2"),
+     ("l_i", "<i2"), ("l_j", "<i2")])
+HIT_BYTES = HIT_DTYPE.itemsize        # 20
+GAPPED_BYTES = GAPPED_DTYPE.itemsize  # 28
+
+
+class plast_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class PlastError(RuntimeError):
+    def __init__(self, call: str, code: int, needed: int | None = None):
+        self.code = code
+        self.needed = needed
+        msg = f"{call}: {plast_strerror(code)} ({code})"
+        if needed is not None:
+            msg += f", needed {needed}"
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libplast.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run paper_0804_3643_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        pI64 = ctypes.POINTER(ctypes.c_int64)
+        pI32 = ctypes.POINTER(ctypes.c_int32)
+        pPrm = ctypes.POINTER(plast_params)
+        L.plast_default_params.argtypes = [pPrm]
+        L.plast_default_params.restype = None
+        L.plast_strerror.argtypes = [ctypes.c_int]
+        L.plast_strerror.restype = ctypes.c_char_p
+        L.plast_set_schedule.argtypes = [ctypes.c_int]
+        L.plast_set_schedule.restype = ctypes.c_int
+        L.plast_translate6.argtypes = [P, P, i32, P, i64, P, P, pI64, P]
+        L.plast_translate6.restype = ctypes.c_int
+        L.plast_index_bank.argtypes = [P, P, i32, pPrm, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.plast_index_bank.restype = ctypes.c_int
+        L.plast_bank_free.argtypes = [P]
+        L.plast_bank_free.restype = None
+        L.plast_bank_stats.argtypes = [P, pI32, pI64, pI64]
+        L.plast_bank_stats.restype = ctypes.c_int
+        L.plast_bank_export_index.argtypes = [P, P, P, i64, pI64, P]
+        L.plast_bank_export_index.restype = ctypes.c_int
+        L.plast_ungapped.argtypes = [P, P, pPrm, P, i64, pI64, P]
+        L.plast_ungapped.restype = ctypes.c_int
+        L.plast_pair_count.argtypes = [P, P]
+        L.plast_pair_count.restype = i64
+        L.plast_small_gapped.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
+        L.plast_small_gapped.restype = ctypes.c_int
+        L.plast_search.argtypes = [P, P, pPrm, P, i64, pI64, pI64, P]
+        L.plast_search.restype = ctypes.c_int
+        L.plast_set_timing.argtypes = [ctypes.c_int]
+        L.plast_set_timing.restype = ctypes.c_int
+        L.plast_stage_times.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.plast_stage_times.restype = ctypes.c_int
+        L.plast_kernel_launches.argtypes = []
+        L.plast_kernel_launches.restype = ctypes.c_longlong
+        _lib = L
+    return _lib
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None and t.numel() else 0)
+
+
+def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    return t.to(dtype).contiguous()
+
+
+def plast_strerror(code: int) -> str:
+    return lib().plast_strerror(code).decode()
+
+
+def plast_default_params(**overrides) -> plast_params:
+    p = plast_params()
+    lib().plast_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, int(v))
+    return p
+
+
+def plast_set_schedule(mode: int) -> None:
+    """0: one persistent launch with a device work queue; 1: one launch per key."""
+    rc = lib().plast_set_schedule(int(mode))
+    if rc:
+        raise PlastError("plast_set_schedule", rc)
+
+
+STAGES = ("upload_work_list", "stage2_kernel", "count_and_sort", "stage31_kernel", "threshold_and_write")
+
+
+def plast_set_timing(on: bool) -> None:
+    lib().plast_set_timing(1 if on else 0)
+
+
+def plast_stage_times() -> dict:
+    """Device ms of the stage intervals of this thread's last timed call."""
+    ms = (ctypes.c_double * len(STAGES))()
+    lib().plast_stage_times(ms, len(STAGES))
+    return dict(zip(STAGES, list(ms)))
+
+
+def plast_kernel_launches() -> int:
+    return int(lib().plast_kernel_launches())
+
+
+class Bank:
+    """Owner of a plast_bank handle (freed with the object)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+        n_seqs, n_res, n_idx = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        lib().plast_bank_stats(handle, ctypes.byref(n_seqs), ctypes.byref(n_res), ctypes.byref(n_idx))
+        self.n_seqs, self.n_residues, self.n_positions = n_seqs.value, n_res.value, n_idx.value
+
+    def free(self):
+        if self.handle:
+            lib().plast_bank_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def plast_index_bank(codes: torch.Tensor, seq_off: torch.Tensor, params: plast_params | None = None,
+                     stream=None) -> Bank:
+    codes = _dev(codes, torch.int8)
+    seq_off = _dev(seq_off, torch.int64)
+    h = ctypes.c_void_p()
+    rc = lib().plast_index_bank(_ptr(codes), _ptr(seq_off), seq_off.numel() - 1,
+                                ctypes.byref(params) if params is not None else None, _stream(stream),
+                                ctypes.byref(h))
+    if rc:
+        raise PlastError("plast_index_bank", rc)
+    return Bank(h)
+
+
+def plast_bank_export_index(bank: Bank, stream=None):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    key_off = torch.empty(NKEYS + 1, dtype=torch.int64, device=dev)
+    pos = torch.empty(max(bank.n_positions, 1), dtype=torch.int32, device=dev)
+    n = ctypes.c_int64()
+    rc = lib().plast_bank_export_index(bank.handle, _ptr(key_off), _ptr(pos), pos.numel(), ctypes.byref(n),
+                                       _stream(stream))
+    if rc:
+        raise PlastError("plast_bank_export_index", rc, n.value)
+    return key_off, pos[:n.value]
+
+
+def plast_pair_count(b1: Bank, b2: Bank) -> int:
+    return int(lib().plast_pair_count(b1.handle, b2.handle))
+
+
+def _records(out: torch.Tensor | None, cap: int, nbytes: int) -> torch.Tensor:
+    if out is not None and out.numel() >= cap * nbytes:
+        return out
+    return torch.empty(max(cap, 1) * nbytes, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+
+
+def plast_ungapped(b1: Bank, b2: Bank, params: plast_params | None = None, cap: int | None = None,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Stage-2 hits as a uint8 device tensor [n, 20] (plast_hit records).
+    With neither ``cap`` nor ``out`` given the output is sized automatically
+    (one retry with the exact count); otherwise PLAST_E_CAPACITY raises."""
+    auto = cap is None and out is None
+    if cap is None:
+        cap = out.numel() // HIT_BYTES if out is not None else plast_pair_count(b1, b2) // 64 + 4096
+    for _ in range(2):
+        buf = _records(out, cap, HIT_BYTES)
+        n = ctypes.c_int64()
+        rc = lib().plast_ungapped(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                  _ptr(buf), cap, ctypes.byref(n), _stream(stream))
+        if rc == PLAST_E_CAPACITY and auto:
+            cap, out = n.value, None
+            continue
+        if rc:
+            raise PlastError("plast_ungapped", rc, n.value)
+        return buf[: n.value * HIT_BYTES].view(-1, HIT_BYTES)
+    raise PlastError("plast_ungapped", PLAST_E_CAPACITY, cap)
+
+
+def plast_small_gapped(b1: Bank, b2: Bank, hits: torch.Tensor, params: plast_params | None = None,
+                       cap: int | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Stage-3.1 records (uint8 device tensor [n, 28]) of ``hits`` ([m, 20] plast_hit)."""
+    hits = hits.contiguous()
+    m = hits.numel() // HIT_BYTES
+    if cap is None:
+        cap = out.numel() // GAPPED_BYTES if out is not None else m
+    buf = _records(out, cap, GAPPED_BYTES)
+    n = ctypes.c_int64()
+    rc = lib().plast_small_gapped(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                  _ptr(hits), m, _ptr(buf), cap, ctypes.byref(n), _stream(stream))
+    if rc:
+        raise PlastError("plast_small_gapped", rc, n.value)
+    return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES)
+
+
+def plast_search(b1: Bank, b2: Bank, params: plast_params | None = None, cap: int | None = None,
+                 out: torch.Tensor | None = None, stream=None):
+    """(records [n, 28] uint8 device tensor, number of stage-2 hits); sized
+    automatically unless ``cap`` or ``out`` is given, as plast_ungapped."""
+    auto = cap is None and out is None
+    if cap is None:
+        cap = out.numel() // GAPPED_BYTES if out is not None else plast_pair_count(b1, b2) // 256 + 4096
+    for _ in range(2):
+        buf = _records(out, cap, GAPPED_BYTES)
+        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().plast_search(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                _ptr(buf), cap, ctypes.byref(n), ctypes.byref(nu), _stream(stream))
+        if rc == PLAST_E_CAPACITY and auto:
+            cap, out = n.value, None
+            continue
+        if rc:
+            raise PlastError("plast_search", rc, n.value)
+        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
+    raise PlastError("plast_search", PLAST_E_CAPACITY, cap)
+
+
+def plast_translate6(dna: torch.Tensor, contig_off: torch.Tensor, stream=None):
+    """(aa int8 [n], seq_off int64 [6c+1], meta int32 [6c, 2]) device tensors."""
+    dna = _dev(dna, torch.uint8)
+    contig_off = _dev(contig_off, torch.int64)
+    c = contig_off.numel() - 1
+    dev = dna.device
+    aa = torch.empty(max(2 * dna.numel(), 1), dtype=torch.int8, device=dev)  # 6 frames x n/3 codons
+    seq_off = torch.empty(6 * c + 1, dtype=torch.int64, device=dev)
+    meta = torch.empty(max(12 * c, 1), dtype=torch.int32, device=dev)
+    n = ctypes.c_int64()
+    rc = lib().plast_translate6(_ptr(dna), _ptr(contig_off), c, _ptr(aa), aa.numel(), _ptr(seq_off), _ptr(meta),
+                                ctypes.byref(n), _stream(stream))
+    if rc:
+        raise PlastError("plast_translate6", rc, n.value)
+    return aa[: n.value], seq_off, meta[: 12 * c].view(-1, 2)
+
+
+# ---------------------------------------------------------------------------
+# Host-side views of the records (copies).
+# ---------------------------------------------------------------------------
+def hits_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.contiguous().cpu().numpy().reshape(-1).view(HIT_DTYPE)
+
+
+def gapped_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.contiguous().cpu().numpy().reshape(-1).view(GAPPED_DTYPE)
+
+
+def hits_from_numpy(a: np.ndarray, device=None) -> torch.Tensor:
+    a = np.ascontiguousarray(a, dtype=HIT_DTYPE)
+    t = torch.from_numpy(a.view(np.uint8).reshape(-1, HIT_BYTES).copy())
+    return t.to(device or torch.device("cuda", torch.cuda.current_device()))
+
+
+@dataclass
+class DeviceBank:
+    """A bank's codes and offsets on the device, as plast_index_bank takes them."""
+    codes: torch.Tensor
+    seq_off: torch.Tensor
+
+    @staticmethod
+    def from_host(codes: np.ndarray, seq_off: np.ndarray, device=None) -> "DeviceBank":
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        return DeviceBank(torch.from_numpy(np.ascontiguousarray(codes).view(np.int8)).to(dev),
+                          torch.from_numpy(np.ascontiguousarray(seq_off, dtype=np.int64)).to(dev))

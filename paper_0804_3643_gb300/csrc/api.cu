@@ -1,0 +1,621 @@
+// api.cu -- the C ABI declared in include/plast.h.
+//
+// Host code only: argument checks, bank lifecycle, the stage-2 work list
+// (tiles of up to 64 bank-1 occurrences of one key, ordered largest first for
+// the persistent queue), stream-ordered scratch, and the launch sequences of
+// the calls.  Every step of the computation runs in the kernels of
+// index.cu, ungapped.cu, gapped.cu and prims.cu.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <stdio.h>
+#include <string.h>
+#include <vector>
+
+#include "common.cuh"
+#include "index.cuh"
+#include "ungapped.cuh"
+
+struct plast_bank {
+  int device = 0;
+  int32_t n_seqs = 0;
+  int64_t n_res = 0, n_pad = 0, n_idx = 0;
+  int8_t* pad = nullptr;       // [n_pad] padded codes
+  int64_t* pad_off = nullptr;  // [n_seqs + 1] padded start of each sequence; [n_seqs] = n_pad
+  int64_t* key_off = nullptr;  // [8801]
+  uint32_t* pos = nullptr;     // [n_idx] padded word starts in CSR order
+  int8_t* nb = nullptr;        // [n_idx][48] neighbourhoods
+  int pad_bits = 1;            // bits needed by a padded position
+  std::vector<int64_t> h_key_off;
+  std::vector<int64_t> h_pad_off;
+};
+
+namespace {
+
+using namespace plast;
+
+std::atomic<int> g_schedule{0};
+std::atomic<int> g_timing{0};
+
+// CUDA events recorded on the call's stream at the stage boundaries of the
+// last stage-2 / stage-3.1 call of this thread (when timing is on).
+struct StageTimer {
+  cudaEvent_t ev[PLAST_MAX_STAGES + 1] = {};
+  bool rec[PLAST_MAX_STAGES + 1] = {};
+  void reset() {
+    for (bool& r : rec) r = false;
+  }
+  void mark(int i, cudaStream_t st) {
+    if (!g_timing.load(std::memory_order_relaxed) || i > PLAST_MAX_STAGES) return;
+    if (!ev[i] && cudaEventCreate(&ev[i]) != cudaSuccess) return;
+    if (cudaEventRecord(ev[i], st) == cudaSuccess) rec[i] = true;
+  }
+};
+thread_local StageTimer t_timer;
+
+int rc_of(cudaError_t e) {
+  if (e == cudaSuccess) return PLAST_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return PLAST_E_OOM;
+  }
+  return PLAST_E_CUDA;
+}
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return rc_of(e_); \
+  } while (0)
+
+// Stream-ordered scratch that is returned when the call ends.
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <class T>
+  cudaError_t get(T** out, size_t count) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~(size_t)255, st);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return cudaSuccess;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(q, st);
+        q = nullptr;
+      }
+    ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), nullptr), ptrs.end());
+  }
+};
+
+bool params_ok(const plast_params* p) {
+  if (!p) return true;
+  return p->w == 4 && p->nl == LEFT && p->nr == RIGHT - 4 && p->lg == LG && p->band == BAND && p->gap_open >= 0 &&
+         p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 1000 && p->s1 >= -30000 &&
+         p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000;
+}
+
+plast_params resolve(const plast_params* p) {
+  plast_params d;
+  plast_default_params(&d);
+  return p ? *p : d;
+}
+
+int bits_for(int64_t v) {
+  int b = 1;
+  while (b < 62 && ((int64_t)1 << b) <= v) b++;
+  return b;
+}
+
+int num_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && sms[dev]) return sms[dev];
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (n <= 0) n = 1;
+  if (dev < 64) sms[dev] = n;
+  return n;
+}
+
+// Stage-2 work list: for every key present in both banks, tiles of up to
+// UNG_T1 consecutive bank-1 occurrences; work = rows * n2.
+struct TileList {
+  std::vector<int4> tiles;        // (key, first CSR index of bank 1, rows, 0)
+  std::vector<int32_t> key_first; // plain schedule: first tile of each key (key order)
+  int64_t pairs = 0;
+};
+
+void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl) {
+  tl->tiles.clear();
+  tl->pairs = 0;
+  std::vector<std::pair<int64_t, int4>> w;
+  for (int k = 0; k < NKEYS; k++) {
+    int64_t n1 = b1->h_key_off[k + 1] - b1->h_key_off[k];
+    int64_t n2 = b2->h_key_off[k + 1] - b2->h_key_off[k];
+    if (n1 == 0 || n2 == 0) continue;
+    tl->pairs += n1 * n2;
+    for (int64_t u = 0; u < n1; u += UNG_T1) {
+      int rows = (int)std::min<int64_t>(UNG_T1, n1 - u);
+      int4 t = make_int4(k, (int)(b1->h_key_off[k] + u), rows, 0);
+      w.push_back({(int64_t)rows * n2, t});
+    }
+  }
+  if (largest_first)
+    std::stable_sort(w.begin(), w.end(), [](const std::pair<int64_t, int4>& x, const std::pair<int64_t, int4>& y) {
+      return x.first > y.first;
+    });
+  tl->tiles.reserve(w.size());
+  for (auto& x : w) tl->tiles.push_back(x.second);
+}
+
+// Device state shared by the stage-2 calls: sorted survivor keys and values.
+struct Survivors {
+  uint64_t* key = nullptr;
+  uint32_t* val = nullptr;
+  int64_t n = 0;
+  int sh = 0;  // key = padded pos1 << sh | padded pos2
+};
+
+int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, cudaStream_t st, Scratch& sc,
+                 Survivors* sv) {
+  sv->n = 0;
+  sv->sh = b2->pad_bits;
+  TileList tl;
+  const int mode = g_schedule.load();
+  build_tiles(b1, b2, mode == 0, &tl);
+  t_timer.mark(0, st);
+  if (tl.tiles.empty()) return PLAST_OK;
+  const int64_t nt = (int64_t)tl.tiles.size();
+  if (nt > 0x7fffffff) return PLAST_E_INVALID;
+
+  int4* d_tiles;
+  int32_t* d_counter;
+  unsigned long long* d_count;
+  CK(sc.get(&d_tiles, nt));
+  CK(sc.get(&d_counter, 1));
+  CK(sc.get(&d_count, 1));
+  CK(cudaMemcpyAsync(d_tiles, tl.tiles.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
+
+  int64_t cap = tl.pairs / 128 + (1 << 20);
+  for (int attempt = 0; attempt < 2; attempt++) {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    CK(sc.get(&k0, cap));
+    CK(sc.get(&v0, cap));
+    CK(cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+    UngArgs a;
+    a.nb1 = b1->nb;
+    a.pos1 = b1->pos;
+    a.nb2 = b2->nb;
+    a.pos2 = b2->pos;
+    a.key_off2 = b2->key_off;
+    a.tiles = d_tiles;
+    a.tile_counter = d_counter;
+    a.s1 = prm.s1;
+    a.out_key = k0;
+    a.out_val = v0;
+    a.out_count = d_count;
+    a.cap = cap;
+    a.sh = sv->sh;
+    t_timer.mark(1, st);
+    if (mode == 0) {
+      a.persistent = 1;
+      a.tile_base = 0;
+      a.n_tiles = (int32_t)nt;
+      CK(launch_ungapped(a, (int)std::min<int64_t>(num_sms(), nt), st));
+    } else {
+      a.persistent = 0;
+      int64_t i = 0;
+      while (i < nt) {
+        int64_t j = i;
+        while (j < nt && tl.tiles[j].x == tl.tiles[i].x) j++;
+        a.tile_base = (int32_t)i;
+        a.n_tiles = (int32_t)(j - i);
+        CK(launch_ungapped(a, (int)(j - i), st));
+        i = j;
+      }
+    }
+    t_timer.mark(2, st);
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((int64_t)n > cap) {
+      sc.release(k0);
+      sc.release(v0);
+      cap = (int64_t)n + 1024;
+      continue;
+    }
+    sv->n = (int64_t)n;
+    if (n == 0) return PLAST_OK;
+    CK(sc.get(&k1, n));
+    CK(sc.get(&v1, n));
+    void* tmp;
+    size_t tb = radix_tmp_bytes((int64_t)n);
+    CK(sc.get((char**)&tmp, tb));
+    bool alt = false;
+    CK(radix_sort_pairs(k0, v0, k1, v1, (int64_t)n, b1->pad_bits + sv->sh, tmp, tb, st, &alt));
+    t_timer.mark(3, st);
+    sv->key = alt ? k1 : k0;
+    sv->val = alt ? v1 : v0;
+    return PLAST_OK;
+  }
+  return PLAST_E_CUDA;
+}
+
+int check_bad(int* d_bad, cudaStream_t st, int* h_bad) {
+  CK(cudaMemcpyAsync(h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void plast_default_params(plast_params* p) {
+  if (!p) return;
+  p->w = 4;
+  p->nl = 22;
+  p->nr = 22;
+  p->s1 = 38;
+  p->lg = 64;
+  p->band = 8;
+  p->gap_open = 11;
+  p->gap_extend = 1;
+  p->s2 = 47;
+}
+
+const char* plast_strerror(int code) {
+  switch (code) {
+    case PLAST_OK: return "ok";
+    case PLAST_E_INVALID: return "invalid argument";
+    case PLAST_E_OOM: return "device allocation failed";
+    case PLAST_E_CAPACITY: return "output capacity too small";
+    case PLAST_E_CUDA: return "CUDA error";
+    case PLAST_E_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+int plast_set_timing(int on) {
+  g_timing.store(on ? 1 : 0);
+  return PLAST_OK;
+}
+
+int plast_stage_times(double* ms, int n) {
+  if (!ms || n < 0) return PLAST_E_INVALID;
+  for (int i = 0; i < n; i++) {
+    ms[i] = -1.0;
+    if (i + 1 > PLAST_MAX_STAGES || !t_timer.rec[i] || !t_timer.rec[i + 1]) continue;
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, t_timer.ev[i], t_timer.ev[i + 1]) == cudaSuccess) ms[i] = f;
+  }
+  return PLAST_OK;
+}
+
+long long plast_kernel_launches(void) { return plast::launch_total(); }
+
+int plast_set_schedule(int mode) {
+  if (mode != 0 && mode != 1) return PLAST_E_INVALID;
+  g_schedule.store(mode);
+  return PLAST_OK;
+}
+
+void plast_bank_free(plast_bank* b) {
+  if (!b) return;
+  // pool memory, returned in order with the legacy default stream
+  for (void* p : {(void*)b->pad, (void*)b->pad_off, (void*)b->key_off, (void*)b->pos, (void*)b->nb})
+    if (p) cudaFreeAsync(p, 0);
+  delete b;
+}
+
+int plast_bank_stats(const plast_bank* b, int32_t* n_seqs, int64_t* n_residues, int64_t* n_positions) {
+  if (!b) return PLAST_E_INVALID;
+  if (n_seqs) *n_seqs = b->n_seqs;
+  if (n_residues) *n_residues = b->n_res;
+  if (n_positions) *n_positions = b->n_idx;
+  return PLAST_OK;
+}
+
+int64_t plast_pair_count(const plast_bank* b1, const plast_bank* b2) {
+  if (!b1 || !b2) return -1;
+  int64_t s = 0;
+  for (int k = 0; k < NKEYS; k++)
+    s += (b1->h_key_off[k + 1] - b1->h_key_off[k]) * (b2->h_key_off[k + 1] - b2->h_key_off[k]);
+  return s;
+}
+
+int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs, const plast_params* params,
+                     void* stream, plast_bank** out) {
+  if (!out || !seq_off || n_seqs < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(upload_tables_once());
+  std::vector<int64_t> h_off((size_t)n_seqs + 1);
+  CK(cudaMemcpyAsync(h_off.data(), seq_off, h_off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_off[0] != 0) return PLAST_E_INVALID;
+  for (int32_t s = 0; s < n_seqs; s++)
+    if (h_off[s + 1] < h_off[s]) return PLAST_E_INVALID;
+  const int64_t n_res = h_off[n_seqs];
+  const int64_t n_pad = n_res + (int64_t)GAP * (n_seqs + 1);
+  if (n_pad >= ((int64_t)1 << 31)) return PLAST_E_INVALID;
+  if (n_res > 0 && !codes) return PLAST_E_INVALID;
+
+  plast_bank* b = new (std::nothrow) plast_bank();
+  if (!b) return PLAST_E_OOM;
+  cudaGetDevice(&b->device);
+  b->n_seqs = n_seqs;
+  b->n_res = n_res;
+  b->n_pad = n_pad;
+  b->pad_bits = bits_for(n_pad);
+  b->h_pad_off.resize((size_t)n_seqs + 1);
+  for (int32_t s = 0; s <= n_seqs; s++) b->h_pad_off[s] = h_off[s] + (int64_t)GAP * (s + 1);
+
+  auto fail = [&](int rc) {
+    plast_bank_free(b);
+    return rc;
+  };
+  auto ck = [&](cudaError_t e) { return e == cudaSuccess ? PLAST_OK : rc_of(e); };
+  int rc;
+  {
+    Scratch sc(st);
+    int* d_bad;
+    int64_t* d_seq_off;
+    if ((rc = ck(sc.get(&d_bad, 1)))) return fail(rc);
+    if ((rc = ck(cudaMemsetAsync(d_bad, 0, sizeof(int), st)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->pad, (size_t)n_pad, st)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->pad_off, ((size_t)n_seqs + 1) * sizeof(int64_t), st)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->key_off, (NKEYS + 1) * sizeof(int64_t), st)))) return fail(rc);
+    if ((rc = ck(cudaMemcpyAsync(b->pad_off, b->h_pad_off.data(), b->h_pad_off.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st))))
+      return fail(rc);
+    if ((rc = ck(sc.get(&d_seq_off, (size_t)n_seqs + 1)))) return fail(rc);
+    if ((rc = ck(cudaMemcpyAsync(d_seq_off, seq_off, ((size_t)n_seqs + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToDevice, st))))
+      return fail(rc);
+    if ((rc = ck(launch_check_codes(codes, n_res, 0, 20, d_bad, st)))) return fail(rc);
+    if ((rc = ck(launch_build_pad(codes, d_seq_off, n_seqs, n_res, b->pad, n_pad, st)))) return fail(rc);
+    int32_t *d_key, *d_flag;
+    int64_t *d_at, *d_total;
+    if ((rc = ck(sc.get(&d_key, n_pad)))) return fail(rc);
+    if ((rc = ck(sc.get(&d_flag, n_pad)))) return fail(rc);
+    if ((rc = ck(sc.get(&d_at, n_pad)))) return fail(rc);
+    if ((rc = ck(sc.get(&d_total, 1)))) return fail(rc);
+    if ((rc = ck(launch_word_keys(b->pad, n_pad, d_key, d_flag, st)))) return fail(rc);
+    void* stmp;
+    size_t stb = scan_tmp_bytes(n_pad);
+    if ((rc = ck(sc.get((char**)&stmp, stb)))) return fail(rc);
+    if ((rc = ck(scan_exclusive(d_flag, d_at, n_pad, d_total, stmp, stb, st)))) return fail(rc);
+    int64_t n_idx = 0;
+    int h_bad = 0;
+    if ((rc = ck(cudaMemcpyAsync(&n_idx, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st)))) return fail(rc);
+    if ((rc = ck(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st)))) return fail(rc);
+    if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
+    if (h_bad) return fail(PLAST_E_INVALID);
+    b->n_idx = n_idx;
+    uint64_t *k0, *k1;
+    uint32_t* v1;
+    if ((rc = ck(sc.get(&k0, n_idx)))) return fail(rc);
+    if ((rc = ck(sc.get(&k1, n_idx)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->pos, (size_t)std::max<int64_t>(n_idx, 1) * sizeof(uint32_t), st))))
+      return fail(rc);
+    if ((rc = ck(sc.get(&v1, n_idx)))) return fail(rc);
+    if ((rc = ck(launch_compact_words(d_key, d_at, n_pad, k0, b->pos, st)))) return fail(rc);
+    sc.release(d_key);
+    sc.release(d_flag);
+    sc.release(d_at);
+    void* rtmp;
+    size_t rtb = radix_tmp_bytes(n_idx);
+    if ((rc = ck(sc.get((char**)&rtmp, rtb)))) return fail(rc);
+    bool alt = false;
+    if ((rc = ck(radix_sort_pairs(k0, b->pos, k1, v1, n_idx, 14, rtmp, rtb, st, &alt)))) return fail(rc);
+    uint64_t* skey = alt ? k1 : k0;
+    if (alt && n_idx > 0) {
+      if ((rc = ck(cudaMemcpyAsync(b->pos, v1, n_idx * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st))))
+        return fail(rc);
+    }
+    if ((rc = ck(launch_key_offsets(skey, n_idx, b->key_off, st)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->nb, (size_t)std::max<int64_t>(n_idx, 1) * WIN, st)))) return fail(rc);
+    if ((rc = ck(launch_neighbourhoods(b->pad, b->pos, n_idx, b->nb, st)))) return fail(rc);
+    b->h_key_off.resize(NKEYS + 1);
+    if ((rc = ck(cudaMemcpyAsync(b->h_key_off.data(), b->key_off, (NKEYS + 1) * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st))))
+      return fail(rc);
+  }
+  if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
+  *out = b;
+  return PLAST_OK;
+}
+
+int plast_bank_export_index(const plast_bank* b, int64_t* key_off, int32_t* pos, int64_t cap, int64_t* n_out,
+                            void* stream) {
+  if (!b || !n_out || !key_off) return PLAST_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  *n_out = b->n_idx;
+  if (cap < b->n_idx) return PLAST_E_CAPACITY;
+  if (b->n_idx > 0 && !pos) return PLAST_E_INVALID;
+  CK(cudaMemcpyAsync(key_off, b->key_off, (NKEYS + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  CK(launch_export_pos(b->pos, b->n_idx, b->pad_off, b->n_seqs, pos, st));
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
+}
+
+int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_hit* out,
+                   int64_t cap, int64_t* n_out, void* stream) {
+  if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  const plast_params prm = resolve(params);
+  cudaStream_t st = (cudaStream_t)stream;
+  *n_out = 0;
+  CK(upload_tables_once());
+  t_timer.reset();
+  Scratch sc(st);
+  Survivors sv;
+  int rc = run_ungapped(b1, b2, prm, st, sc, &sv);
+  if (rc) return rc;
+  *n_out = sv.n;
+  if (sv.n > cap) return PLAST_E_CAPACITY;
+  if (sv.n == 0) return PLAST_OK;
+  if (!out) return PLAST_E_INVALID;
+  int* d_bad;
+  CK(sc.get(&d_bad, 1));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  CK(launch_expand_hits(sv.key, sv.val, sv.n, sv.sh, b1->pad, b1->pad_off, b1->n_seqs, b2->pad, b2->pad_off,
+                        b2->n_seqs, out, d_bad, st));
+  int h_bad = 0;
+  if ((rc = check_bad(d_bad, st, &h_bad))) return rc;
+  return h_bad ? PLAST_E_CUDA : PLAST_OK;
+}
+
+namespace {
+
+int run_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, const uint64_t* key,
+               const uint32_t* val, int64_t n, int sh, plast_gapped* out, int64_t cap, int64_t* n_out,
+               cudaStream_t st, Scratch& sc) {
+  *n_out = 0;
+  if (n == 0) return PLAST_OK;
+  GapArgs g;
+  g.pad1 = b1->pad;
+  g.pad2 = b2->pad;
+  g.key = key;
+  g.val = val;
+  g.n = n;
+  g.sh = sh;
+  g.gap_open = prm.gap_open;
+  g.gap_extend = prm.gap_extend;
+  g.s2 = prm.s2;
+  int64_t *at, *total;
+  CK(sc.get(&g.score, n));
+  CK(sc.get(&g.ends, n));
+  CK(sc.get(&g.pass, n));
+  CK(sc.get(&at, n));
+  CK(sc.get(&total, 1));
+  CK(launch_small_gapped(g, st));
+  t_timer.mark(4, st);
+  void* stmp;
+  size_t stb = scan_tmp_bytes(n);
+  CK(sc.get((char**)&stmp, stb));
+  CK(scan_exclusive(g.pass, at, n, total, stmp, stb, st));
+  int64_t m = 0;
+  CK(cudaMemcpyAsync(&m, total, sizeof(m), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *n_out = m;
+  if (m > cap) return PLAST_E_CAPACITY;
+  if (m == 0) return PLAST_OK;
+  if (!out) return PLAST_E_INVALID;
+  CK(launch_gapped_compact(g, at, b1->pad_off, b1->n_seqs, b2->pad_off, b2->n_seqs, out, st));
+  t_timer.mark(5, st);
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
+}
+
+}  // namespace
+
+int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const plast_hit* in,
+                       int64_t n_in, plast_gapped* out, int64_t cap, int64_t* n_out, void* stream) {
+  if (!b1 || !b2 || !n_out || n_in < 0 || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  if (n_in > 0 && !in) return PLAST_E_INVALID;
+  const plast_params prm = resolve(params);
+  cudaStream_t st = (cudaStream_t)stream;
+  *n_out = 0;
+  CK(upload_tables_once());
+  t_timer.reset();
+  if (n_in == 0) return PLAST_OK;
+  if (b1->n_seqs == 0 || b2->n_seqs == 0) return PLAST_E_INVALID;
+  Scratch sc(st);
+  uint64_t* key;
+  uint32_t* val;
+  int* d_bad;
+  CK(sc.get(&key, n_in));
+  CK(sc.get(&val, n_in));
+  CK(sc.get(&d_bad, 1));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  const int sh = b2->pad_bits;
+  CK(launch_hits_to_keys(in, n_in, b1->pad_off, b1->n_seqs, b2->pad_off, b2->n_seqs, sh, key, val, d_bad, st));
+  int h_bad = 0;
+  int rc = check_bad(d_bad, st, &h_bad);
+  if (rc) return rc;
+  if (h_bad) return PLAST_E_INVALID;
+  return run_gapped(b1, b2, prm, key, val, n_in, sh, out, cap, n_out, st, sc);
+}
+
+int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
+                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream) {
+  if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  const plast_params prm = resolve(params);
+  cudaStream_t st = (cudaStream_t)stream;
+  *n_out = 0;
+  if (n_ungapped_out) *n_ungapped_out = 0;
+  CK(upload_tables_once());
+  t_timer.reset();
+  Scratch sc(st);
+  Survivors sv;
+  int rc = run_ungapped(b1, b2, prm, st, sc, &sv);
+  if (rc) return rc;
+  if (n_ungapped_out) *n_ungapped_out = sv.n;
+  return run_gapped(b1, b2, prm, sv.key, sv.val, sv.n, sv.sh, out, cap, n_out, st, sc);
+}
+
+int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,
+                     int64_t aa_cap, int64_t* seq_off_out, int32_t* frame_meta_out, int64_t* n_aa_out,
+                     void* stream) {
+  if (!contig_off || n_contigs < 0 || !n_aa_out) return PLAST_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  *n_aa_out = 0;
+  std::vector<int64_t> h_off((size_t)n_contigs + 1);
+  CK(cudaMemcpyAsync(h_off.data(), contig_off, h_off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_off[0] != 0) return PLAST_E_INVALID;
+  for (int32_t c = 0; c < n_contigs; c++)
+    if (h_off[c + 1] < h_off[c]) return PLAST_E_INVALID;
+  const int64_t n_nt = h_off[n_contigs];
+  if (n_nt > 0 && !dna) return PLAST_E_INVALID;
+  std::vector<int64_t> so((size_t)6 * n_contigs + 1);
+  std::vector<int32_t> meta((size_t)12 * n_contigs);
+  so[0] = 0;
+  for (int32_t c = 0; c < n_contigs; c++) {
+    const int64_t L = h_off[c + 1] - h_off[c];
+    for (int f = 0; f < 6; f++) {
+      const int64_t start = f % 3;
+      const int64_t len = L > start ? (L - start) / 3 : 0;
+      const size_t s = (size_t)6 * c + f;
+      so[s + 1] = so[s] + len;
+      meta[2 * s] = c;
+      meta[2 * s + 1] = f < 3 ? f + 1 : -(f - 2);
+    }
+  }
+  const int64_t n_aa = so.back();
+  *n_aa_out = n_aa;
+  if (n_aa > aa_cap) return PLAST_E_CAPACITY;
+  if (!seq_off_out || (n_contigs > 0 && !frame_meta_out) || (n_aa > 0 && !aa_out)) return PLAST_E_INVALID;
+  Scratch sc(st);
+  int* d_bad;
+  CK(sc.get(&d_bad, 1));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  CK(launch_check_codes((const int8_t*)dna, n_nt, 0, 3, d_bad, st));
+  int h_bad = 0;
+  int rc = check_bad(d_bad, st, &h_bad);
+  if (rc) return rc;
+  if (h_bad) return PLAST_E_INVALID;
+  CK(cudaMemcpyAsync(seq_off_out, so.data(), so.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (n_contigs > 0)
+    CK(cudaMemcpyAsync(frame_meta_out, meta.data(), meta.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(launch_translate6(dna, contig_off, n_contigs, seq_off_out, n_aa, aa_out, st));
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
+}
+
+}  // extern "C"

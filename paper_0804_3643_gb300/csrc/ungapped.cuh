@@ -1,0 +1,52 @@
+// ungapped.cuh -- arguments and launchers of the stage-2 kernels (ungapped.cu).
+#pragma once
+#include "common.cuh"
+
+namespace plast {
+
+struct UngArgs {
+  const int8_t* nb1;        // bank-1 windows [n_idx1][48]
+  const uint32_t* pos1;     // bank-1 padded positions, CSR order
+  const int8_t* nb2;        // bank-2 windows [n_idx2][48]
+  const uint32_t* pos2;     // bank-2 padded positions, CSR order
+  const int64_t* key_off2;  // bank-2 CSR offsets [8801]
+  const int4* tiles;        // (key, first bank-1 CSR index, rows <= 64, 0)
+  int32_t n_tiles;          // tiles handled by this launch
+  int32_t tile_base;        // first tile of this launch in `tiles`
+  int32_t* tile_counter;    // persistent schedule: next tile to take
+  int32_t persistent;       // 1: CTAs loop on the counter; 0: one tile per CTA
+  int32_t s1;               // ungapped threshold
+  uint64_t* out_key;        // hit (padded pos1 << sh | padded pos2)
+  uint32_t* out_val;        // hit score (int16 in the low half)
+  unsigned long long* out_count;
+  int64_t cap;              // capacity of out_key / out_val
+  int32_t sh;               // bits of a bank-2 padded position
+};
+
+size_t ungapped_smem_bytes();
+cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
+                               const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
+                               int32_t n2, plast_hit* out, int* bad, cudaStream_t st);
+
+// gapped.cu
+struct GapArgs {
+  const int8_t* pad1;
+  const int8_t* pad2;
+  const uint64_t* key;      // (padded pos1 << sh | padded pos2) per hit
+  const uint32_t* val;      // stage-2 score per hit in the low 16 bits
+  int64_t n;
+  int32_t sh;
+  int32_t gap_open, gap_extend, s2;
+  int32_t* score;           // out: small gapped score per hit
+  uint32_t* ends;           // out: r_i | r_j << 8 | l_i << 16 | l_j << 24
+  int32_t* pass;            // out: score >= s2
+};
+cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st);
+cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
+                                  const int64_t* pad_off2, int32_t n2, plast_gapped* out, cudaStream_t st);
+cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* pad_off1, int32_t n1,
+                                const int64_t* pad_off2, int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad,
+                                cudaStream_t st);
+
+}  // namespace plast

@@ -1,0 +1,232 @@
+"""CUDA path vs the CPU oracle, through the C ABI, element by element.
+
+Integer work throughout, so the bar is bit-exact: the same index, the same
+hit set with the same scores and extents, the same small gapped records in
+the same canonical order.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import bank_from
+from paper_0804_3643_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_0804_3643_gb300 import binding, build
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    build.build()
+    binding.lib()
+    binding.plast_set_schedule(0)
+    return binding
+
+
+def gpu_bank(B, codes, seq_off):
+    d = B.DeviceBank.from_host(codes, seq_off)
+    return B.plast_index_bank(d.codes, d.seq_off)
+
+
+def both(B, codes, seq_off):
+    return gpu_bank(B, codes, seq_off), oracle.make_bank(codes, seq_off)
+
+
+def same(a: np.ndarray, b: np.ndarray) -> bool:
+    return a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+def check_index(B, g, o):
+    key_off, pos = B.plast_bank_export_index(g)
+    assert np.array_equal(key_off.cpu().numpy(), o.idx.key_off)
+    assert np.array_equal(pos.cpu().numpy(), o.idx.pos)
+
+
+@pytest.fixture(scope="module")
+def plain(B):
+    b1, b2 = synth.workload("plastp_plain", seed=1)
+    g1, o1 = both(B, b1.codes, b1.seq_off)
+    g2, o2 = both(B, b2.codes, b2.seq_off)
+    return g1, o1, g2, o2
+
+
+def test_index_parity(B, plain):
+    g1, o1, g2, o2 = plain
+    check_index(B, g1, o1)
+    check_index(B, g2, o2)
+
+
+def test_index_edge_banks(B):
+    cases = [
+        ["AQAA"],                        # one word
+        ["AQA", "W", ""],                # no word at all
+        ["", "", "MKVLAAQAAWWW", ""],    # empty sequences around
+        ["A" * 300, "AQAASAAAPAAA" * 20],  # long lists of one key
+        ["MKV*LAQ*AAAA*", "**AQAA**"],  # stops are never inside an indexed word
+    ]
+    for seqs in cases:
+        c, o = bank_from(seqs)
+        g, ob = both(B, c, o)
+        check_index(B, g, ob)
+
+
+def test_ungapped_parity_plain(B, plain):
+    g1, o1, g2, o2 = plain
+    got = B.hits_numpy(B.plast_ungapped(g1, g2))
+    want = oracle.ungapped(o1, o2)
+    assert len(want) > 1000
+    assert same(got, want)
+
+
+def test_search_parity_plain(B, plain):
+    g1, o1, g2, o2 = plain
+    recs, n_ung = B.plast_search(g1, g2)
+    want_h = oracle.ungapped(o1, o2)
+    want = oracle.small_gapped(o1, o2, want_h)
+    assert n_ung == len(want_h)
+    assert len(want) > 100
+    assert same(B.gapped_numpy(recs), want)
+
+
+def test_small_gapped_on_given_hits(B, plain):
+    g1, o1, g2, o2 = plain
+    hits = oracle.ungapped(o1, o2, oracle.Params(s1=30))
+    prm = oracle.Params(s2=-10 ** 4)
+    want = oracle.small_gapped(o1, o2, hits, prm)
+    got = B.plast_small_gapped(g1, g2, B.hits_from_numpy(hits), B.plast_default_params(s2=-10 ** 4))
+    assert len(want) == len(hits)
+    assert same(B.gapped_numpy(got), want)
+
+
+def test_thresholds_and_gap_costs(B, plain):
+    g1, o1, g2, o2 = plain
+    for s1, s2, go, ge in [(25, 30, 11, 1), (45, 60, 10, 2), (38, 47, 5, 3)]:
+        prm = oracle.Params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
+        gp = B.plast_default_params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
+        recs, n_ung = B.plast_search(g1, g2, gp)
+        want_h = oracle.ungapped(o1, o2, prm)
+        assert n_ung == len(want_h)
+        assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h, prm))
+
+
+def test_plain_schedule_matches_persistent(B):
+    b1, b2 = synth.workload("plastp_plain", seed=2, scale=0.3)
+    g1, o1 = both(B, b1.codes, b1.seq_off)
+    g2, o2 = both(B, b2.codes, b2.seq_off)
+    want = oracle.ungapped(o1, o2)
+    try:
+        B.plast_set_schedule(1)
+        per_key = B.hits_numpy(B.plast_ungapped(g1, g2))
+    finally:
+        B.plast_set_schedule(0)
+    persistent = B.hits_numpy(B.plast_ungapped(g1, g2))
+    assert same(per_key, want) and same(persistent, want)
+
+
+def test_identical_banks_every_pair_passes(B):
+    # self comparison with S1 = 0: every pair passes, so per-warp buffers
+    # overflow and the direct-write path runs
+    rng = np.random.default_rng(3)
+    seqs = [rng.integers(0, 4, int(rng.integers(20, 200))).astype(np.int8) for _ in range(30)]
+    c, o = bank_from(seqs)
+    g, ob = both(B, c, o)
+    prm = oracle.Params(s1=0, s2=-10 ** 4)
+    want = oracle.ungapped(ob, ob, prm)
+    got = B.hits_numpy(B.plast_ungapped(g, g, B.plast_default_params(s1=0)))
+    assert len(want) == oracle.ungapped(ob, ob, prm, return_pairs=True)[1]
+    assert same(got, want)
+    recs, _ = B.plast_search(g, g, B.plast_default_params(s1=0, s2=-10 ** 4))
+    assert same(B.gapped_numpy(recs), oracle.small_gapped(ob, ob, want, prm))
+
+
+def test_low_complexity_workload(B):
+    b1, b2 = synth.workload("batching_stress", seed=4, scale=0.004)
+    g1, o1 = both(B, b1.codes, b1.seq_off)
+    g2, o2 = both(B, b2.codes, b2.seq_off)
+    want = oracle.ungapped(o1, o2, threads=8)
+    got = B.hits_numpy(B.plast_ungapped(g1, g2))
+    assert same(got, want)
+    recs, _ = B.plast_search(g1, g2)
+    assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want))
+
+
+def test_empty_and_tiny_banks(B):
+    c0, o0 = bank_from([])
+    c1, o1 = bank_from(["AQAA"])
+    c2, o2 = bank_from(["AQAAW", "SQAAC"])
+    e = gpu_bank(B, c0, o0)
+    a = gpu_bank(B, c1, o1)
+    b = gpu_bank(B, c2, o2)
+    assert B.plast_ungapped(e, a).shape[0] == 0
+    assert B.plast_ungapped(a, e).shape[0] == 0
+    h = B.hits_numpy(B.plast_ungapped(a, b, B.plast_default_params(s1=-100)))
+    want = oracle.ungapped(oracle.make_bank(c1, o1), oracle.make_bank(c2, o2), oracle.Params(s1=-100))
+    assert same(h, want) and len(want) == 1
+
+
+def test_translate6_parity(B):
+    rng = np.random.default_rng(9)
+    lens = [0, 1, 2, 3, 5, 7, 30, 301, 1000, 1001, 1002]
+    contigs = [rng.integers(0, 4, L).astype(np.uint8) for L in lens]
+    off = np.zeros(len(lens) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    dna = np.concatenate(contigs)
+    aa, so, meta = B.plast_translate6(torch.from_numpy(dna).cuda(), torch.from_numpy(off).cuda())
+    w_aa, w_so, w_meta = oracle.translate6(dna, off)
+    assert np.array_equal(aa.cpu().numpy(), w_aa)
+    assert np.array_equal(so.cpu().numpy(), w_so)
+    assert np.array_equal(meta.cpu().numpy(), w_meta)
+
+
+def test_tplastn_parity_small(B):
+    b1, dna = synth.tplastn_workload(seed=5, scale=0.01)
+    aa, so, _ = B.plast_translate6(torch.from_numpy(dna.codes).cuda(), torch.from_numpy(dna.seq_off).cuda())
+    w_aa, w_so, _ = oracle.translate6(dna.codes, dna.seq_off)
+    assert np.array_equal(aa.cpu().numpy(), w_aa)
+    g1, o1 = both(B, b1.codes, b1.seq_off)
+    g2 = B.plast_index_bank(aa, so)
+    o2 = oracle.make_bank(w_aa, w_so)
+    want = oracle.ungapped(o1, o2, threads=8)
+    got = B.hits_numpy(B.plast_ungapped(g1, g2))
+    assert len(want) > 0
+    assert same(got, want)
+    recs, _ = B.plast_search(g1, g2)
+    assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want))
+
+
+def test_errors(B):
+    c, o = bank_from(["AQAAW"])
+    bad = c.copy()
+    bad[2] = 22
+    d = B.DeviceBank.from_host(bad, o)
+    with pytest.raises(B.PlastError) as e:
+        B.plast_index_bank(d.codes, d.seq_off)
+    assert e.value.code == B.PLAST_E_INVALID
+    d = B.DeviceBank.from_host(c, np.array([0, 3, 2], dtype=np.int64))
+    with pytest.raises(B.PlastError) as e:
+        B.plast_index_bank(d.codes, d.seq_off)
+    assert e.value.code == B.PLAST_E_INVALID
+    g = gpu_bank(B, c, o)
+    with pytest.raises(B.PlastError) as e:
+        B.plast_ungapped(g, g, B.plast_default_params(nl=10))
+    assert e.value.code == B.PLAST_E_INVALID
+    # capacity: the call reports the needed count and writes nothing
+    h = B.plast_ungapped(g, g, B.plast_default_params(s1=-100))
+    assert h.shape[0] == 2
+    with pytest.raises(B.PlastError) as e:
+        B.plast_ungapped(g, g, B.plast_default_params(s1=-100), cap=1)
+    assert e.value.code == B.PLAST_E_CAPACITY and e.value.needed == 2
+    # small gapped on a hit outside the bank
+    hit = B.hits_numpy(h)[:1].copy()
+    hit["pos2"] = 99
+    with pytest.raises(B.PlastError) as e:
+        B.plast_small_gapped(g, g, B.hits_from_numpy(hit))
+    assert e.value.code == B.PLAST_E_INVALID
+    dna = torch.tensor([0, 1, 4], dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.PlastError) as e:
+        B.plast_translate6(dna, torch.tensor([0, 3], dtype=torch.int64, device="cuda"))
+    assert e.value.code == B.PLAST_E_INVALID
