@@ -1,7 +1,7 @@
 // api.cu -- the C ABI declared in include/plast.h.
 //
 // Host code only: argument checks, bank lifecycle, the stage-2 work list
-// (tiles of up to 64 bank-1 occurrences of one key, ordered largest first for
+// (tiles of up to UNG_T1 = 128 bank-1 occurrences of one key, largest first for
 // the persistent queue), stream-ordered scratch, and the launch sequences of
 // the calls.  Every step of the computation runs in the kernels of
 // index.cu, ungapped.cu, gapped.cu and prims.cu.

@@ -39,7 +39,7 @@ constexpr int BW = 2 * BAND + 1;
 constexpr int GAP = 80;
 
 // Launch geometry of the stage-2 kernel.
-constexpr int UNG_T1 = 64;         // bank-1 rows per profile tile
+constexpr int UNG_T1 = 128;        // bank-1 rows per profile tile
 constexpr int UNG_THREADS = 1024;  // 32 warps, one CTA per SM
 
 // BLOSUM62, upper triangle by rows, order A R N D C Q E G H I L K M F P S T W Y V
@@ -89,6 +89,16 @@ void build_tables(Tables* t);
 extern __constant__ int8_t c_score[NCODE * NCODE];
 extern __constant__ int8_t c_cls2[NAA];
 extern __constant__ int8_t c_cls3[NAA];
+
+// One byte from shared memory at a 32-bit shared address plus a constant
+// offset.  Issued as its own load so the byte goes through the load/store
+// unit rather than being carved out of a wider load on the integer ALU.
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u8(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1+%2];" : "=r"(v) : "r"(saddr), "n"(OFF));
+  return v;
+}
 
 __device__ __forceinline__ int seed_key(int a0, int a1, int a2, int a3) {
   // Key = ((c1 * 2 + c2) * 11 + c3) * 20 + c4; -1 when a letter is a stop or
