@@ -131,7 +131,7 @@ int32_t oracle_seed_key(const int8_t* w) {
 
 /* ------------------------------------------------------------------------
  * Stage 0, Section 3.3.1: index a bank.  Every overlapping word of length 4
- * inside one sequence (Section 2.2.1 splits a sequence into overlapping
+ * inside one sequence (Section 2.3.1 splits a sequence into overlapping
  * words) is mapped to its subset-seed key; positions sharing a key are
  * linked.  The linked lists plus the look-up table of the paper are held as
  * one CSR array: key_off[k] .. key_off[k+1] are the positions of key k in

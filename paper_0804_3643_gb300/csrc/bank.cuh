@@ -1,0 +1,20 @@
+// bank.cuh -- the device-resident indexed bank behind the opaque plast_bank
+// handle of include/plast.h (library-internal).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+struct plast_bank {
+  int device = 0;
+  int32_t n_seqs = 0;
+  int64_t n_res = 0, n_pad = 0, n_idx = 0;
+  int8_t* pad = nullptr;       // [n_pad] padded codes
+  int64_t* pad_off = nullptr;  // [n_seqs + 1] padded start of each sequence; [n_seqs] = n_pad
+  int64_t* key_off = nullptr;  // [8801]
+  uint32_t* pos = nullptr;     // [n_idx] padded word starts in CSR order
+  int8_t* nb = nullptr;        // [n_idx][48] neighbourhoods
+  int pad_bits = 1;            // bits needed by a padded position
+  std::vector<int64_t> h_key_off;
+  std::vector<int64_t> h_pad_off;
+};
