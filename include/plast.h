@@ -185,6 +185,31 @@ int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params*
                  int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream);
 
 /*
+ * plast_small_gapped without device allocation.  The paper has no
+ * counterpart to this call; it exists for callers that cannot let a library
+ * allocate device memory: a framework that reserved the GPU's memory for its
+ * own allocator, or a latency-bound loop that must not meet an allocation's
+ * implicit synchronisation or an out-of-memory failure mid-request.
+ * Same arguments, results and errors as plast_small_gapped, except:
+ *  - n_in must be at most PLAST_NOALLOC_MAX_HITS (otherwise PLAST_E_INVALID);
+ *  - the working buffers live in one static device array of
+ *    PLAST_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that
+ *    loads the library until the process exits; no cudaMalloc or cudaFree
+ *    is called;
+ *  - every call on a device uses that same array, which keeps the previous
+ *    call's contents: calls whose work overlaps on the GPU (other streams,
+ *    other threads) race and must be serialised by the caller;
+ *  - the first call on a device performs one-time set-up (it looks up the
+ *    array's device address and loads the score tables into constant
+ *    memory); make that first call before any stream capture.
+ */
+#define PLAST_NOALLOC_MAX_HITS 65536
+#define PLAST_NOALLOC_SCRATCH_BYTES (2 * 1024 * 1024 + 8192)
+int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+                               const plast_hit* in, int64_t n_in, plast_gapped* out, int64_t cap,
+                               int64_t* n_out, void* stream);
+
+/*
  * Scheduling of stage 2.  0 (default): one persistent launch, CTAs pull
  * profile tiles from a device work queue, largest first.  1: the plain
  * form, one launch per key.  Applies to later calls in this process.

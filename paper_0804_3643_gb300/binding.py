@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
         L.plast_small_gapped.restype = ctypes.c_int
         L.plast_search.argtypes = [P, P, pPrm, P, i64, pI64, pI64, P]
         L.plast_search.restype = ctypes.c_int
+        L.plast_small_gapped_noalloc.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
+        L.plast_small_gapped_noalloc.restype = ctypes.c_int
         L.plast_set_timing.argtypes = [ctypes.c_int]
         L.plast_set_timing.restype = ctypes.c_int
         L.plast_stage_times.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
@@ -246,6 +248,27 @@ def plast_small_gapped(b1: Bank, b2: Bank, hits: torch.Tensor, params: plast_par
     if rc:
         raise PlastError("plast_small_gapped", rc, n.value)
     return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES)
+
+
+NOALLOC_MAX_HITS = 65536
+
+
+def plast_small_gapped_noalloc(b1: Bank, b2: Bank, hits: torch.Tensor, out: torch.Tensor,
+                               params: plast_params | None = None, stream=None) -> torch.Tensor:
+    """plast_small_gapped for callers that cannot allocate: the library uses
+    its fixed device scratch area (at most NOALLOC_MAX_HITS hits; calls that
+    overlap on the GPU race).  ``out`` is the caller's preallocated uint8
+    device buffer; the records are returned as a view of it."""
+    hits = hits.contiguous()
+    m = hits.numel() // HIT_BYTES
+    cap = out.numel() // GAPPED_BYTES
+    n = ctypes.c_int64()
+    rc = lib().plast_small_gapped_noalloc(b1.handle, b2.handle,
+                                          ctypes.byref(params) if params is not None else None,
+                                          _ptr(hits), m, _ptr(out), cap, ctypes.byref(n), _stream(stream))
+    if rc:
+        raise PlastError("plast_small_gapped_noalloc", rc, n.value)
+    return out[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES)
 
 
 def plast_search(b1: Bank, b2: Bank, params: plast_params | None = None, cap: int | None = None,
