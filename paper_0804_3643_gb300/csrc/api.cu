@@ -304,7 +304,7 @@ int plast_set_schedule(int mode) {
 void plast_bank_free(plast_bank* b) {
   if (!b) return;
   // pool memory, returned in order with the legacy default stream
-  for (void* p : {(void*)b->pad, (void*)b->pad_off, (void*)b->key_off, (void*)b->pos, (void*)b->nb})
+  for (void* p : {(void*)b->pad_alloc, (void*)b->pad_off, (void*)b->key_off, (void*)b->pos, (void*)b->nb})
     if (p) cudaFreeAsync(p, 0);
   delete b;
 }
@@ -364,7 +364,9 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     int64_t* d_seq_off;
     if ((rc = ck(sc.get(&d_bad, 1)))) return fail(rc);
     if ((rc = ck(cudaMemsetAsync(d_bad, 0, sizeof(int), st)))) return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->pad, (size_t)n_pad, st)))) return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->pad_alloc, (size_t)(n_pad + 2 * PAD_SLACK), st)))) return fail(rc);
+    b->pad = b->pad_alloc + PAD_SLACK;
+    if ((rc = ck(cudaMemsetAsync(b->pad_alloc, SENTINEL, (size_t)(n_pad + 2 * PAD_SLACK), st)))) return fail(rc);
     if ((rc = ck(cudaMallocAsync((void**)&b->pad_off, ((size_t)n_seqs + 1) * sizeof(int64_t), st)))) return fail(rc);
     if ((rc = ck(cudaMallocAsync((void**)&b->key_off, (NKEYS + 1) * sizeof(int64_t), st)))) return fail(rc);
     if ((rc = ck(cudaMemcpyAsync(b->pad_off, b->h_pad_off.data(), b->h_pad_off.size() * sizeof(int64_t),

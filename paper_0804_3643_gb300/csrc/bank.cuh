@@ -5,11 +5,17 @@
 
 #include "common.cuh"
 
+// Sentinel bytes allocated before and after a bank's padded codes, beyond
+// GAP: kernels that read whole aligned words around a hit may touch a few
+// bytes outside [0, n_pad).
+constexpr int64_t PAD_SLACK = 256;
+
 struct plast_bank {
   int device = 0;
   int32_t n_seqs = 0;
   int64_t n_res = 0, n_pad = 0, n_idx = 0;
-  int8_t* pad = nullptr;       // [n_pad] padded codes
+  int8_t* pad = nullptr;       // [n_pad] padded codes (PAD_SLACK more sentinel bytes on both sides)
+  int8_t* pad_alloc = nullptr; // the allocation: pad - PAD_SLACK
   int64_t* pad_off = nullptr;  // [n_seqs + 1] padded start of each sequence; [n_seqs] = n_pad
   int64_t* key_off = nullptr;  // [8801]
   uint32_t* pos = nullptr;     // [n_idx] padded word starts in CSR order

@@ -1,159 +1,235 @@
 // gapped.cu -- stage 3.1 (Section 3.3.4; the two one-sided extensions per hit
 // of Section 5.2.2) on sm_103a.
 //
-// One thread computes one side of one hit: the banded affine dynamic
-// programme (Gotoh form, anchored at the seed start, free end, no clamp at
-// zero) over LG = 64 residues per sequence and the band |i - j| <= 8.  The
-// two threads of a hit are adjacent lanes and add their sides with a
-// shuffle.  CTAs stride over the hits.
+// One thread computes one side (right or left of the seed start) of TWO hits
+// at once, one per int16 half: the banded affine dynamic programme (Gotoh
+// form, anchored at the seed start, free end, no clamp at zero) over
+// LG = 64 residues per sequence and the band |i - j| <= 8.  The two threads
+// holding the two sides of the same hits are adjacent lanes and add their
+// sides with shuffles.  CTAs stride over the hits.
 //
-// The thread first copies its side's residues to its own shared segments
-// (A_1..A_64 and B_-8..B_74, in reading order, so the left side needs no
-// special case).  Per cell the work is then: a byte load of B_j (immediate
-// offset), an IMAD for the table address, a load of s(A_i, B_j) from a score
-// table replicated per lane (entry (a, b) of lane l at word
-// ((b * 23 + a) * 32 + l), so the 32 lanes of a warp never share a bank),
-// __viaddmax_s32 for E and F, one 3-input max for H, and a max over the row
-// of (33 H + 31 - jb), which keeps the first best cell of the row in
-// row-major order.  Adds and IMADs go to the FMA pipe, maxima to the ALU
-// pipe, which issues at half the FMA rate on sm_103.  Segment strides are odd
-// numbers of words, so the byte loads of a warp hit 32 different banks.  The
-// 17 band cells of the previous row (H, H - open - extend, F) live in
-// registers and are updated in place.
+// Per cell (two hits): two byte loads of B_j from the thread's shared
+// segments, two IMADs and two loads of s(A_i, B_j) from a lane-replicated
+// table (entry (a, b) of lane l at word (b * 23 + a) * 32 + l: the lanes of a
+// warp never share a bank), one IMAD packing the two scores, then
+//   F  = max(H_up - go - ge, F_up - ge)           __viaddmax_s16x2
+//   DF = max(H_diag + s, F)                       __viaddmax_s16x2
+//   H  = max(DF, E)                               __vmaxs2
+//   E' = max(E - ge, DF - go - ge)                __vsub2, __viaddmax_s16x2
+// (F is kept as F - ge, so F_up - ge needs no instruction.)
+// E' is E of the next cell: since go >= 0, H - go - ge is never above E - ge
+// when H = E, so only DF feeds the next E and the chain along the row is a
+// single instruction per cell.  Values are exact in int16 (|H| <= 64 * 11 on
+// the grid; cells off the grid stay above -16000 - 64 * 12).
+//
+// The end cell (first maximum in row-major order): after each row the row
+// maximum is compared with the best so far per half; the halves that improve
+// copy the row's H values into a best-row array (LOP3 masks) and record the
+// row.  At the end the first column of the best row holding the best value
+// is the end column.
 //
 // Reads past a sequence end meet the sentinel padding (score -32): no path
 // through a sentinel cell comes back above the best cell of the clipped
 // grid, so the fixed band over i <= LG equals the one clipped at the sequence
-// ends.  Columns j < 0 start at -2^20 and stay far below zero.  Columns
+// ends.  Columns j < 0 start at -16000 and stay far below zero.  Columns
 // j > LG (rows i > LG - BAND) lie outside the grid; they feed no cell of the
-// grid and are kept out of the maximum.
+// grid and are kept out of the maximum (compile-time column limits).
 #include "common.cuh"
 #include "ungapped.cuh"
 
 namespace plast {
 
-constexpr int NEG = -(1 << 20);
+constexpr int NEG16 = -16000;
 constexpr int GAP_THREADS = 256;
 constexpr int TAB_A = 23;                                   // padded entries per b
 constexpr int TAB_WORDS = NCODE * TAB_A * 32;               // lane-replicated
-constexpr int SEG_A = 68;                                   // 17 words: A_1 .. A_64
-constexpr int SEG_B = 84;                                   // 21 words: B_-8 .. B_74
-constexpr int GAP_SMEM = TAB_WORDS * 4 + GAP_THREADS * (SEG_A + SEG_B);  // 103680 bytes
+constexpr int SEG_W = 22;                                   // words staged per hit: B_-8 .. B_74 + slack
+constexpr int SEG_B = SEG_W * 4;                            // 88 bytes
+constexpr int SEG_T = 2 * SEG_B + 4;                        // 45 words per thread: odd, no bank conflict
+constexpr int GAP_SMEM = TAB_WORDS * 4 + GAP_THREADS * SEG_T;  // 110848 bytes
 
-// One band cell of row i: s from the lane's table, then E, F and H.
+__device__ __forceinline__ uint32_t x2(int v) { return ((uint32_t)(uint16_t)v << 16) | (uint16_t)v; }
+
+struct Band {
+  uint32_t H[BW], Fm[BW], bestH[BW];  // H and F - ge of the previous row, best row
+  uint32_t best, bi;                 // per half
+};
+
+// Cell JB of row i for both hits.
 template <int JB>
-__device__ __forceinline__ int band_cell(const unsigned char* rowbase, uint32_t segb, int (&H)[BW], int (&Hm)[BW],
-                                         int (&F)[BW], int& E, int& Hm_left, int goe, int ge) {
-  const uint32_t b = lds_u8<JB>(segb);  // B_{i - BAND + JB}
-  const int sc = *reinterpret_cast<const int*>(rowbase + b * (TAB_A * 128));
-  const int up_m = JB + 1 < BW ? Hm[JB + 1 < BW ? JB + 1 : 0] : NEG;
-  const int up_f = JB + 1 < BW ? F[JB + 1 < BW ? JB + 1 : 0] : NEG;
-  const int e = __viaddmax_s32(E, -ge, Hm_left);   // max(E - ge, H_left - open - ge)
-  const int f = __viaddmax_s32(up_f, -ge, up_m);   // max(F_up - ge, H_up - open - ge)
-  const int hv = __vimax3_s32(H[JB] + sc, e, f);
-  H[JB] = hv;
-  Hm_left = hv - goe;
-  Hm[JB] = Hm_left;
-  F[JB] = f;
-  E = e;
-  return hv;
+__device__ __forceinline__ uint32_t band_cell(Band& B, const unsigned char* row0, const unsigned char* row1,
+                                              uint32_t sb0, uint32_t sb1, uint32_t& E, uint32_t nge2,
+                                              uint32_t goe2) {
+  const uint32_t ngoe2 = __vsub2(0u, goe2);
+  const uint32_t b0 = lds_u8<JB>(sb0), b1 = lds_u8<JB>(sb1);  // B_{i - BAND + JB} of each hit
+  const uint32_t s0 = *reinterpret_cast<const uint32_t*>(row0 + b0 * (TAB_A * 128));
+  const uint32_t s1 = *reinterpret_cast<const uint32_t*>(row1 + b1 * (TAB_A * 128));
+  const uint32_t sc = s1 * 65536u + s0;  // entries are zero-extended int16
+  const uint32_t up_h = JB + 1 < BW ? B.H[JB + 1 < BW ? JB + 1 : 0] : x2(NEG16);
+  const uint32_t up_fm = JB + 1 < BW ? B.Fm[JB + 1 < BW ? JB + 1 : 0] : x2(NEG16);
+  const uint32_t f = __viaddmax_s16x2(up_h, ngoe2, up_fm);  // max(H_up - go - ge, F_up - ge)
+  const uint32_t df = __viaddmax_s16x2(B.H[JB], sc, f);     // max(H_diag + s, F)
+  const uint32_t h = __vmaxs2(df, E);
+  E = __viaddmax_s16x2(E, nge2, __vsub2(df, goe2));
+  B.H[JB] = h;
+  B.Fm[JB] = __vadd2(f, nge2);
+  return h;
 }
 
-// Row i of the band.  The first best cell of the row in row-major order is
-// the largest (H * 33 + 31 - jb): 33 > 31 keeps H's order, ties go to the
-// smaller jb.  Cells with j > LG (EDGE rows) stay out of the maximum.
-template <bool EDGE>
-__device__ __forceinline__ void gapped_row(int i, const unsigned char* rowbase, uint32_t segb, int (&H)[BW],
-                                           int (&Hm)[BW], int (&F)[BW], int goe, int ge, int& best, int& bi,
-                                           int& bj) {
-  int E = NEG, Hm_left = NEG;
-  const int jlim = LG + BAND - i;  // cells jb <= jlim have j <= LG
-  int enc[BW];
-#define PLAST_CELL(JB)                                                                   \
-  {                                                                                      \
-    const int hv = band_cell<JB>(rowbase, segb, H, Hm, F, E, Hm_left, goe, ge);          \
-    enc[JB] = (EDGE && JB > jlim) ? NEG * 33 : hv * 33 + (31 - JB);                      \
+template <int JB, int JLIM>
+__device__ __forceinline__ void band_cells(Band& B, const unsigned char* row0, const unsigned char* row1,
+                                           uint32_t sb0, uint32_t sb1, uint32_t& E, uint32_t nge2,
+                                           uint32_t goe2, uint32_t& rmax) {
+  if constexpr (JB < BW) {
+    const uint32_t h = band_cell<JB>(B, row0, row1, sb0, sb1, E, nge2, goe2);
+    if constexpr (JB <= JLIM) rmax = JB == 0 ? h : __vmaxs2(rmax, h);
+    band_cells<JB + 1, JLIM>(B, row0, row1, sb0, sb1, E, nge2, goe2, rmax);
   }
-  PLAST_CELL(0) PLAST_CELL(1) PLAST_CELL(2) PLAST_CELL(3) PLAST_CELL(4) PLAST_CELL(5) PLAST_CELL(6)
-  PLAST_CELL(7) PLAST_CELL(8) PLAST_CELL(9) PLAST_CELL(10) PLAST_CELL(11) PLAST_CELL(12) PLAST_CELL(13)
-  PLAST_CELL(14) PLAST_CELL(15) PLAST_CELL(16)
-#undef PLAST_CELL
-  int r = __vimax3_s32(enc[0], enc[1], enc[2]);
-  r = __vimax3_s32(r, enc[3], enc[4]);
-  r = __vimax3_s32(r, enc[5], enc[6]);
-  r = __vimax3_s32(r, enc[7], enc[8]);
-  r = __vimax3_s32(r, enc[9], enc[10]);
-  r = __vimax3_s32(r, enc[11], enc[12]);
-  r = __vimax3_s32(r, enc[13], enc[14]);
-  r = __vimax3_s32(r, enc[15], enc[16]);
-  if (r >= (best + 1) * 33) {  // a strictly larger H (r >= 0 here)
-    const int rb = r / 33;
-    best = rb;
-    bi = i;
-    bj = i - BAND + (31 - (r - rb * 33));
-  }
+}
+
+// Row i; columns jb > JLIM have j > LG and stay out of the maximum.
+template <int JLIM>
+__device__ __forceinline__ void gapped_row(Band& B, int i, const unsigned char* row0, const unsigned char* row1,
+                                           uint32_t sb0, uint32_t sb1, uint32_t nge2, uint32_t goe2) {
+  uint32_t E = x2(NEG16), rmax = 0;
+  band_cells<0, JLIM>(B, row0, row1, sb0 + i, sb1 + i, E, nge2, goe2, rmax);
+  const uint32_t up = __vcmpgts2(rmax, B.best);  // 0xffff in the halves that improve
+  B.best = __vmaxs2(B.best, rmax);
+  B.bi = (x2(i) & up) | (B.bi & ~up);
+#pragma unroll
+  for (int jb = 0; jb < BW; jb++) B.bestH[jb] = (B.H[jb] & up) | (B.bestH[jb] & ~up);
+}
+
+// First column of the best row holding the best value, for half q.
+__device__ __forceinline__ int end_column(const Band& B, int q) {
+  const int sh = 16 * q;
+  const int best = (int16_t)(B.best >> sh);
+  const int bi = (int16_t)(B.bi >> sh);
+  const int jlim = min(BW - 1, LG + BAND - bi);
+  int found = -1;
+#pragma unroll
+  for (int jb = BW - 1; jb >= 0; jb--)
+    if (jb <= jlim && (int16_t)(B.bestH[jb] >> sh) == best) found = jb;
+  return bi - BAND + found;
+}
+
+// Copy B_-8 .. B_74 of one hit side into a thread's segment in reading
+// order with aligned 32-bit loads, B_-8 landing on the segment's first byte
+// (so the byte loads of a warp stay conflict-free); returns its shared address.
+// Right side: B_j = pad2[p2 + j - 1], the bytes [p2 - 9, p2 + 73] forwards.
+// Left side:  B_j = pad2[p2 - j],     the bytes [p2 - 74, p2 + 8] backwards,
+// each word byte-reversed.
+__device__ __forceinline__ uint32_t stage_b(const int8_t* pad2, int64_t p2, int side, uint32_t* dst,
+                                            uint32_t dst_s) {
+  const int64_t lo = p2 - 9, hi = p2 + BAND;
+  const int64_t first = side ? ((hi | 3) - 3) : (lo & ~(int64_t)3);  // byte address of the first word
+  const uint32_t sel = side ? 0x0123u : 0x3210u;
+  const uint32_t sh = 8u * (side ? (uint32_t)(3 - (hi & 3)) : (uint32_t)(lo & 3));
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(pad2 + first);
+  uint32_t w[SEG_W + 1];
+#pragma unroll
+  for (int k = 0; k <= SEG_W; k++) w[k] = __byte_perm(__ldg(src + (side ? -k : k)), 0u, sel);
+#pragma unroll
+  for (int k = 0; k < SEG_W; k++) dst[k] = __funnelshift_r(w[k], w[k + 1], sh);
+  return dst_s;
 }
 
 __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   extern __shared__ __align__(16) unsigned char gsm[];
-  int* tab32 = reinterpret_cast<int*>(gsm);
-  unsigned char* sega = gsm + TAB_WORDS * 4 + threadIdx.x * SEG_A;
-  unsigned char* segb = gsm + TAB_WORDS * 4 + GAP_THREADS * SEG_A + threadIdx.x * SEG_B;
-  const uint32_t segb_s = (uint32_t)__cvta_generic_to_shared(segb);
+  uint32_t* tab32 = reinterpret_cast<uint32_t*>(gsm);
+  unsigned char* seg = gsm + TAB_WORDS * 4 + threadIdx.x * SEG_T;
+  const uint32_t seg_s = (uint32_t)__cvta_generic_to_shared(seg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int e = warp; e < NCODE * TAB_A; e += GAP_THREADS / 32) {
     const int b = e / TAB_A, aa = e - b * TAB_A;
-    tab32[e * 32 + lane] = aa < NCODE ? (int)c_score[aa * NCODE + b] : 0;
+    tab32[e * 32 + lane] = aa < NCODE ? (uint32_t)(uint16_t)(int16_t)c_score[aa * NCODE + b] : 0u;
   }
   __syncthreads();
   const unsigned char* tlane = reinterpret_cast<const unsigned char*>(tab32) + lane * 4;
   const int go = a.gap_open, ge = a.gap_extend, goe = go + ge;
-  const int64_t total = 2 * a.n;
+  const uint32_t nge2 = x2(-ge), goe2 = x2(goe);
+  const int64_t npairs = (a.n + 1) / 2;  // hits 2p and 2p+1 share a thread
+  const int64_t total = 2 * npairs;      // (pair, side) threads
   const int64_t stride = (int64_t)gridDim.x * GAP_THREADS;
   for (int64_t base = (int64_t)blockIdx.x * GAP_THREADS + warp * 32; base < total; base += stride) {
     const int64_t t = base + lane;
-    const int64_t h = t >> 1;
+    const int64_t pr = t >> 1;
     const int side = (int)(t & 1);  // 0: right of the seed start, 1: left of it
     const bool active = t < total;
-    int best = 0, bi = 0, bj = 0;
+    const int64_t h0 = 2 * pr, h1 = 2 * pr + 1 < a.n ? 2 * pr + 1 : 2 * pr;
+    Band B;
     if (active) {
-      const uint64_t key = a.key[h];
-      const int64_t p1 = (int64_t)(key >> a.sh), p2 = (int64_t)(key & ((1ull << a.sh) - 1));
-      // residue i (1-based) of each side: right A_i = pad1[p1 + i - 1],
-      // left A_i = pad1[p1 - i]; the same for B with p2
-      if (side == 0) {
-        for (int i = 0; i < LG; i++) sega[i] = (unsigned char)a.pad1[p1 + i];
-        for (int j = -BAND; j <= LG + BAND + 2; j++) segb[j + BAND] = (unsigned char)a.pad2[p2 + j - 1];
-      } else {
-        for (int i = 0; i < LG; i++) sega[i] = (unsigned char)a.pad1[p1 - 1 - i];
-        for (int j = -BAND; j <= LG + BAND + 2; j++) segb[j + BAND] = (unsigned char)a.pad2[p2 - j];
-      }
-      int H[BW], Hm[BW], F[BW];
+      const uint64_t k0 = a.key[h0], k1 = a.key[h1];
+      const uint64_t mask = (1ull << a.sh) - 1;
+      const int64_t p10 = (int64_t)(k0 >> a.sh), p20 = (int64_t)(k0 & mask);
+      const int64_t p11 = (int64_t)(k1 >> a.sh), p21 = (int64_t)(k1 & mask);
+      // residue i (1-based): right A_i = pad1[p1 + i - 1], B_j = pad2[p2 + j - 1];
+      // left A_i = pad1[p1 - i], B_j = pad2[p2 - j].
+      const int step = side ? -1 : 1;
+      const int8_t* A0 = a.pad1 + p10 - side;
+      const int8_t* A1 = a.pad1 + p11 - side;
+      // B_-8 .. B_74 of each hit in reading order: aligned words of pad2,
+      // taken backwards and byte-reversed for the left side; sbX points at B_-8
+      const uint32_t sb0 = stage_b(a.pad2, p20, side, reinterpret_cast<uint32_t*>(seg), seg_s);
+      const uint32_t sb1 = stage_b(a.pad2, p21, side, reinterpret_cast<uint32_t*>(seg + SEG_B), seg_s + SEG_B);
 #pragma unroll
       for (int jb = 0; jb < BW; jb++) {  // row 0
         const int j = jb - BAND;
-        H[jb] = j < 0 ? NEG : (j == 0 ? 0 : -(go + j * ge));
-        Hm[jb] = H[jb] - goe;
-        F[jb] = NEG;
+        const int v = j < 0 ? NEG16 : (j == 0 ? 0 : -(go + j * ge));
+        B.H[jb] = x2(v);
+        B.Fm[jb] = x2(NEG16);
+        B.bestH[jb] = B.H[jb];
       }
-      // row i reads B_{i - BAND + jb} = segb[i + jb]
-      for (int i = 1; i <= LG - BAND; i++) {
-        const unsigned char* rowbase = tlane + (uint32_t)sega[i - 1] * 128u;
-        gapped_row<false>(i, rowbase, segb_s + i, H, Hm, F, goe, ge, best, bi, bj);
-      }
-      for (int i = LG - BAND + 1; i <= LG; i++) {
-        const unsigned char* rowbase = tlane + (uint32_t)sega[i - 1] * 128u;
-        gapped_row<true>(i, rowbase, segb_s + i, H, Hm, F, goe, ge, best, bi, bj);
-      }
+      B.best = 0;
+      B.bi = 0;
+      // A_i of both hits, fetched one row ahead
+      uint32_t a0 = (uint8_t)A0[0], a1 = (uint8_t)A1[0];
+#define PLAST_ROW(JLIM)                                                                                 \
+  {                                                                                                    \
+    const unsigned char* r0 = tlane + a0 * 128u;                                                       \
+    const unsigned char* r1 = tlane + a1 * 128u;                                                       \
+    a0 = (uint8_t)A0[i * step];                                                                        \
+    a1 = (uint8_t)A1[i * step];                                                                        \
+    gapped_row<JLIM>(B, i, r0, r1, sb0, sb1, nge2, goe2);                                             \
+  }
+      for (int i = 1; i <= LG - BAND; i++) PLAST_ROW(BW - 1)
+      { int i = LG - BAND + 1; PLAST_ROW(15) }
+      { int i = LG - BAND + 2; PLAST_ROW(14) }
+      { int i = LG - BAND + 3; PLAST_ROW(13) }
+      { int i = LG - BAND + 4; PLAST_ROW(12) }
+      { int i = LG - BAND + 5; PLAST_ROW(11) }
+      { int i = LG - BAND + 6; PLAST_ROW(10) }
+      { int i = LG - BAND + 7; PLAST_ROW(9) }
+      { int i = LG - BAND + 8; PLAST_ROW(8) }
+#undef PLAST_ROW
+    } else {
+      B.best = 0;
+      B.bi = 0;
+#pragma unroll
+      for (int jb = 0; jb < BW; jb++) B.bestH[jb] = 0;
     }
-    const int other = __shfl_xor_sync(0xffffffffu, best, 1);
-    const int obi = __shfl_xor_sync(0xffffffffu, bi, 1);
-    const int obj = __shfl_xor_sync(0xffffffffu, bj, 1);
+    // per hit: this side's (score, end row, end column)
+    int bi0 = 0, bj0 = 0, bi1 = 0, bj1 = 0;
+    if (active) {
+      bi0 = (int16_t)(B.bi & 0xffff);
+      bj0 = end_column(B, 0);
+      bi1 = (int16_t)(B.bi >> 16);
+      bj1 = end_column(B, 1);
+    }
+    const uint32_t ob = __shfl_xor_sync(0xffffffffu, B.best, 1);
+    const int obi0 = __shfl_xor_sync(0xffffffffu, bi0, 1), obj0 = __shfl_xor_sync(0xffffffffu, bj0, 1);
+    const int obi1 = __shfl_xor_sync(0xffffffffu, bi1, 1), obj1 = __shfl_xor_sync(0xffffffffu, bj1, 1);
     if (active && side == 0) {
-      const int g = best + other;
-      a.score[h] = g;
-      a.ends[h] = (uint32_t)bi | ((uint32_t)bj << 8) | ((uint32_t)obi << 16) | ((uint32_t)obj << 24);
-      a.pass[h] = g >= a.s2;
+      const int g0 = (int16_t)(B.best & 0xffff) + (int16_t)(ob & 0xffff);
+      a.score[h0] = g0;
+      a.ends[h0] = (uint32_t)bi0 | ((uint32_t)bj0 << 8) | ((uint32_t)obi0 << 16) | ((uint32_t)obj0 << 24);
+      a.pass[h0] = g0 >= a.s2;
+      if (2 * pr + 1 < a.n) {
+        const int g1 = (int16_t)(B.best >> 16) + (int16_t)(ob >> 16);
+        a.score[h1] = g1;
+        a.ends[h1] = (uint32_t)bi1 | ((uint32_t)bj1 << 8) | ((uint32_t)obi1 << 16) | ((uint32_t)obj1 << 24);
+        a.pass[h1] = g1 >= a.s2;
+      }
     }
   }
 }
@@ -170,7 +246,7 @@ cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t blocks = (2 * a.n + GAP_THREADS - 1) / GAP_THREADS;
+  int64_t blocks = (2 * ((a.n + 1) / 2) + GAP_THREADS - 1) / GAP_THREADS;
   const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 2 * 16;
   if (blocks > cap) blocks = cap;
   note_launch();
