@@ -171,6 +171,29 @@ def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def reduce_max(x: float, world: int, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank processes the same amount)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
+def shard_seed(rank: int) -> int:
+    """Seed of a rank's bank-2 shard: rank 0 draws the single-GPU workload."""
+    return 1 + rank
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("ungapped.cu", "ungapped.cuh", "common.cuh"):
@@ -205,11 +228,9 @@ def run_gpu(args, rank, world, local_rank):
     B.plast_set_schedule(1 if args.schedule == "per_key" else 0)
 
     t0 = time.time()
-    b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale)
-    if rank == 0:
-        _, b2 = synth.workload(WORKLOAD, seed=1, scale=args.scale)
-    else:  # weak scaling: each rank its own bank-2 shard of the same size
-        _, b2 = synth.workload(WORKLOAD, seed=1 + rank, scale=args.scale)
+    b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale, n2=2)
+    # weak scaling: each rank its own bank-2 shard of the same size
+    _, b2 = synth.workload(WORKLOAD, seed=shard_seed(rank), scale=args.scale, n2=args.bank2_proteins)
     log(f"[rank {rank}] banks generated in {time.time() - t0:.1f}s: {b1.n_seqs} x {b2.n_seqs} proteins, "
         f"{len(b1.codes)} / {len(b2.codes)} residues")
 
@@ -252,12 +273,7 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, dev)
 
     # ---- device-resident arm
     B.plast_set_timing(True)
@@ -317,7 +333,7 @@ def run_gpu(args, rank, world, local_rank):
         traffic = tr["dram_bytes_per_pair"] * pairs
     result = {
         "metric": METRIC,
-        "value": world * pairs / (ms_step / 1e3),
+        "value": whole_job_rate(pairs, world, ms_step),
         "unit": "pairs/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -365,6 +381,141 @@ def run_gpu(args, rank, world, local_rank):
     }
     return result, (b1, b2)
 
+# --------------------------------------------------------------------------
+# Other workloads (not the headline line): the batching stress test, the
+# TPLAST-N chain and the serving loop.  Each prints one JSON line.
+# --------------------------------------------------------------------------
+def _time_steps(fn, steps, warmup):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_stress(args):
+    """50,000 x 50,000 proteins, 20 % with low-complexity runs: heavy-tailed
+    key lists; the persistent work-queue launch against one launch per key."""
+    import torch
+
+    from paper_0804_3643_gb300 import binding as B
+
+    b1, b2 = synth.workload("batching_stress", seed=1, scale=args.scale)
+    d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
+    d2 = B.DeviceBank.from_host(b2.codes, b2.seq_off)
+    g1 = B.plast_index_bank(d1.codes, d1.seq_off)
+    g2 = B.plast_index_bank(d2.codes, d2.seq_off)
+    pairs = B.plast_pair_count(g1, g2)
+    recs, n_ung = B.plast_search(g1, g2)
+    cap = int(recs.shape[0] * 1.05) + 1024
+    out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
+    res = {}
+    B.plast_set_timing(True)
+    for name, mode in (("persistent", 0), ("per_key", 1)):
+        B.plast_set_schedule(mode)
+        st = []
+
+        def step():
+            B.plast_search(g1, g2, out=out, cap=cap)
+            st.append(B.plast_stage_times())
+
+        ms = _time_steps(step, args.steps, args.warmup)
+        res[name] = {"ms_per_search": ms, "pairs_per_s": pairs / (ms / 1e3),
+                     "stage2_ms": statistics.mean(x["stage2_kernel"] for x in st[args.warmup:])}
+    B.plast_set_schedule(0)
+    B.plast_set_timing(False)
+    n1 = np.diff(np.array(B.plast_bank_export_index(g1)[0].cpu()))
+    n2 = np.diff(np.array(B.plast_bank_export_index(g2)[0].cpu()))
+    per_key = n1 * n2
+    return {
+        "metric": "search time, persistent work queue vs one launch per key", "unit": "ms",
+        "workload": f"batching stress: {b1.n_seqs} x {b2.n_seqs} proteins, 20% with low-complexity runs, seed 1",
+        "pairs": pairs, "stage2_hits": n_ung, "records": int(recs.shape[0]),
+        "pairs_per_key": {"max": int(per_key.max()), "p50": float(np.median(per_key[per_key > 0])),
+                          "keys_over_1e6": int((per_key > 1e6).sum())},
+        "schedules": res,
+        "speedup_persistent_over_per_key": res["per_key"]["ms_per_search"] / res["persistent"]["ms_per_search"],
+    }
+
+
+def run_tplastn(args):
+    """5,000 proteins vs a 50 Mbp nucleotide bank: six-frame translation on
+    the device, then stage 0 of both banks and the search, per step."""
+    import torch
+
+    from paper_0804_3643_gb300 import binding as B
+
+    b1, dna = synth.tplastn_workload(seed=1, scale=args.scale)
+    d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
+    hd = torch.from_numpy(dna.codes).cuda()
+    ho = torch.from_numpy(dna.seq_off).cuda()
+    aa, so, _ = B.plast_translate6(hd, ho)
+    g1 = B.plast_index_bank(d1.codes, d1.seq_off)
+    g2 = B.plast_index_bank(aa, so)
+    pairs = B.plast_pair_count(g1, g2)
+    recs, n_ung = B.plast_search(g1, g2)
+    cap = int(recs.shape[0] * 1.05) + 1024
+    out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
+    n_rec = int(recs.shape[0])
+    del g2
+
+    def step():
+        a, s_, _ = B.plast_translate6(hd, ho)
+        x = B.plast_index_bank(d1.codes, d1.seq_off)
+        y = B.plast_index_bank(a, s_)
+        B.plast_search(x, y, out=out, cap=cap)
+        x.free()
+        y.free()
+
+    ms = _time_steps(step, args.steps, args.warmup)
+    return {
+        "metric": "ungapped pairs/s, TPLAST-N chain (translate6 + index + search)", "unit": "pairs/s",
+        "value": pairs / (ms / 1e3), "ms_per_step": ms,
+        "workload": f"TPLAST-N: {b1.n_seqs} proteins vs {len(dna.codes) / 1e6:.1f} Mbp in {dna.n_seqs} contigs "
+                    f"({len(aa)} translated residues), {len(dna.planted['regions'])} planted regions, seed 1",
+        "pairs": pairs, "stage2_hits": n_ung, "records": n_rec,
+    }
+
+
+def run_serving(args):
+    """A resident bank of 1,000,000 proteins; query banks of 1-500 proteins
+    arriving as Poisson processes; continuous batching."""
+    from paper_0804_3643_gb300 import serve
+
+    rng = np.random.default_rng(1)
+    n_res = max(1000, int(1_000_000 * args.scale))
+    t0 = time.time()
+    bank = synth.random_protein_bank(rng, n_res)
+    ex = serve.GpuExecutor(bank.codes, bank.seq_off)
+    log(f"resident bank {n_res} proteins ({len(bank.codes)} residues) generated and indexed in "
+        f"{time.time() - t0:.1f}s")
+    rows = []
+    for rate in (5.0, 20.0, 50.0, 100.0, 200.0):
+        reqs = [serve.Request(i, t, b.codes, b.seq_off) for i, (t, b) in
+                enumerate(synth.serving_requests(seed=int(rate), n=args.requests, rate_per_s=rate))]
+        srv = serve.Server(ex.execute, ex.mem_of, slots=2, mem_budget=120 << 30, max_batch_seqs=3000)
+        t1 = time.perf_counter()
+        srv.run(reqs, realtime=True, timeout=900)
+        wall = time.perf_counter() - t1
+        pairs = sum(b.pairs for b in srv.batches)
+        row = {"rate_per_s": rate, **serve.latency_summary(reqs, pairs, wall),
+               "batches": len(srv.batches), "mean_batch_requests": len(reqs) / len(srv.batches),
+               "peak_concurrent_batches": srv.peak_busy, "wall_s": wall}
+        log(json.dumps(row))
+        rows.append(row)
+    return {"metric": "serving latency p50/p99 and pairs/s under continuous batching", "unit": "ms",
+            "workload": f"resident bank of {n_res} synthetic proteins ({len(bank.codes)} residues); "
+                        f"{args.requests} query banks of U(1..500) proteins per rate, Poisson arrivals",
+            "slots": 2, "rows": rows}
+
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -376,6 +527,12 @@ def main():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_key"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batching_stress", "tplastn", "serving"],
+                    help="the headline line is plastp_full; the others print their own lines")
+    ap.add_argument("--requests", type=int, default=60, help="serving: requests per arrival rate")
+    ap.add_argument("--bank2-proteins", type=int, default=None,
+                    help="bank-2 size of the headline workload (profiling captures use 10000)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -399,6 +556,12 @@ def main():
             "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
         print(json.dumps(line), flush=True)
+        return
+
+    if args.workload != WORKLOAD:
+        if rank == 0:
+            fn = {"batching_stress": run_stress, "tplastn": run_tplastn, "serving": run_serving}[args.workload]
+            print(json.dumps(fn(args)), flush=True)
         return
 
     if world > 1:

@@ -1,0 +1,27 @@
+"""Build and run the instruction issue-rate probe (probe/pipes.cu) on the
+current GPU; prints one JSON line per instruction kind.
+
+    python -m paper_0804_3643_gb300.peak
+
+Under ncu, with --metrics sm__inst_executed_pipe_alu.sum,
+sm__inst_executed_pipe_fmaheavy.sum,smsp__inst_executed.sum, it shows on which
+pipe each kind issues; the stage-2 roofline in the design doc rests on that split.
+"""
+import os
+import subprocess
+import sys
+
+from .build import ARCH, nvcc
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def main() -> int:
+    src = os.path.join(HERE, "probe", "pipes.cu")
+    exe = os.path.join(HERE, "probe", "pipes")
+    subprocess.check_call([nvcc()] + ARCH + ["-O3", "-o", exe, src])
+    return subprocess.call([exe])
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -270,12 +270,13 @@ WORKLOADS = {
 }
 
 
-def workload(name: str, seed: int = 1, scale: float = 1.0):
-    """(bank1, bank2) of a named protein-vs-protein workload."""
+def workload(name: str, seed: int = 1, scale: float = 1.0, n2: int | None = None):
+    """(bank1, bank2) of a named protein-vs-protein workload; ``n2`` overrides
+    the number of bank-2 proteins (bank 1 is drawn first, so it is unchanged)."""
     rng = np.random.default_rng(seed)
     cfg = WORKLOADS[name]
     n1 = max(2, int(round(cfg["n1"] * scale)))
-    n2 = max(2, int(round(cfg["n2"] * scale)))
+    n2 = max(2, int(round(cfg["n2"] * scale))) if n2 is None else int(n2)
     b1 = protein_bank(rng, n1, lowcomplex_frac=cfg["lowc"])
     b2 = protein_bank(rng, n2, homolog_source=b1, planted_frac=cfg["planted"], lowcomplex_frac=cfg["lowc"])
     return b1, b2
