@@ -39,7 +39,7 @@ from paper_0804_3643_gb300 import synth  # noqa: E402
 
 WORKLOAD = "plastp_full"
 CELLS_PER_PAIR = 48        # ungapped window: 26 right + 22 left cells
-ALU_OPS_PER_PAIR = 2 * CELLS_PER_PAIR  # one add and one max per cell (int16)
+CELLS_PER_CLK_SM = 128     # int16 cells per clock per SM on the ALU / FMA-heavy pipes
 METRIC = "ungapped pairs/s and GCUPS at 1 GB300 (bit-exact), % of int/HBM roofline"
 
 
@@ -325,8 +325,11 @@ def run_gpu(args, rank, world, local_rank):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
-    peak_ops = n_sm * 128 * 2 * sm_max * 1e6  # int16 lanes: 128 per SM per clock, 2 per 32-bit lane
-    achieved_ops = pairs * ALU_OPS_PER_PAIR / (ung_ms / 1e3)
+    # A cell needs one int16 max (ALU pipe: 64 lanes x 2 halves per clock per
+    # SM) and one int16 add (FMA-heavy pipe, the same rate): 128 cells per
+    # clock per SM (see profiles/pipes_sm103.md).
+    peak_cells = n_sm * CELLS_PER_CLK_SM * sm_max * 1e6
+    achieved_cells = pairs * CELLS_PER_PAIR / (ung_ms / 1e3)
     tr = committed_traffic()
     traffic = None
     if tr is not None:
@@ -362,16 +365,18 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {
             "bound": "alu",
             "kernel": "k_ungapped",
-            "achieved": achieved_ops / 1e12,
-            "peak": peak_ops / 1e12,
-            "unit": "Tops/s (int16)",
-            "frac": achieved_ops / peak_ops,
+            "achieved": achieved_cells / 1e12,
+            "peak": peak_cells / 1e12,
+            "unit": "Tcell/s",
+            "frac": achieved_cells / peak_cells,
             "traffic": traffic,
-            "ops_per_pair": ALU_OPS_PER_PAIR,
+            "cells_per_pair": CELLS_PER_PAIR,
             "kernel_ms": ung_ms,
-            "peak_basis": f"{n_sm} SMs x 128 int32 lanes x 2 int16 halves x {sm_max:.0f} MHz (max SM clock)",
-            "frac_at_measured_clock": (achieved_ops / (n_sm * 256 * clocks["sm_mhz"] * 1e6)
+            "peak_basis": f"{n_sm} SMs x {CELLS_PER_CLK_SM} cells/clock (ALU pipe 64 lanes x 2 int16 halves for "
+                          f"the max, FMA-heavy pipe the same for the add) x {sm_max:.0f} MHz (max SM clock)",
+            "frac_at_measured_clock": (achieved_cells / (n_sm * CELLS_PER_CLK_SM * clocks["sm_mhz"] * 1e6)
                                        if clocks.get("sm_mhz") else None),
+            "hbm_gbs": (traffic / (ung_ms / 1e3) / 1e9) if traffic else None,
         },
         "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(rec_bytes), "ms_per_step": e2e_ms},

@@ -159,6 +159,21 @@ int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_param
                    int64_t cap, int64_t* n_out, void* stream);
 
 /*
+ * plast_ungapped / plast_search restricted to the subset-seed keys
+ * keys[0 .. n_keys) (each in 0..8799; duplicates ignored).  Stages 1-3.1 are
+ * independent per key (Section 5.1 hands seeds to cores one at a time), so the
+ * records of a key set are exactly the records of the full call whose seed
+ * word has one of those keys.  Used to shard a comparison by key and to check
+ * a sample of keys of a large comparison.  Errors as the unrestricted calls,
+ * and PLAST_E_INVALID for a key outside 0..8799.
+ */
+int plast_ungapped_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
+                        int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out, void* stream);
+int plast_search_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
+                      int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
+                      void* stream);
+
+/*
  * Number of ungapped pairs (sum over keys of n1 * n2) the two banks give;
  * pure host arithmetic on the indexes, no device work.
  */
@@ -208,6 +223,33 @@ int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params*
 int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
                                const plast_hit* in, int64_t n_in, plast_gapped* out, int64_t cap,
                                int64_t* n_out, void* stream);
+
+/*
+ * Planned search for repeated comparisons of the same two banks (a resident
+ * bank against a fixed query set, a benchmark loop).  plast_plan_create
+ * allocates every buffer the search needs for at most max_hits stage-2 hits
+ * and uploads the stage-2 work list; `records` (device, caller-owned,
+ * max_records entries) receives the stage-3.1 records of every run.  The
+ * banks and `records` must outlive the plan.  plast_plan_run then queues the
+ * whole chain of stages 1-3.1 on `stream` with no allocation and no host
+ * synchronisation (the kernels pass the survivor count in device memory), so
+ * it can be captured in a CUDA graph; plast_plan_capture does that capture
+ * on a non-default `stream` and keeps the instantiated graph in the plan,
+ * and plast_plan_launch replays it.  plast_plan_result synchronises `stream`
+ * and returns the record count of the last run (records in canonical order,
+ * as plast_search) and its stage-2 hit count; PLAST_E_CAPACITY if either
+ * limit was exceeded (*n_records then holds the hit or record count that did
+ * not fit, and the records are incomplete).  Runs of one plan must not
+ * overlap on the device.
+ */
+typedef struct plast_plan plast_plan;
+int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int64_t max_hits,
+                      plast_gapped* records, int64_t max_records, void* stream, plast_plan** out);
+int plast_plan_run(plast_plan* plan, void* stream);
+int plast_plan_capture(plast_plan* plan, void* stream);
+int plast_plan_launch(plast_plan* plan, void* stream);
+int plast_plan_result(const plast_plan* plan, int64_t* n_records, int64_t* n_hits, void* stream);
+void plast_plan_free(plast_plan* plan);
 
 /*
  * Scheduling of stage 2.  0 (default): one persistent launch, CTAs pull

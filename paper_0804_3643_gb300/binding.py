@@ -93,6 +93,19 @@ def lib() -> ctypes.CDLL:
         L.plast_search.restype = ctypes.c_int
         L.plast_small_gapped_noalloc.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
         L.plast_small_gapped_noalloc.restype = ctypes.c_int
+        L.plast_ungapped_keys.argtypes = [P, P, pPrm, P, i32, P, i64, pI64, P]
+        L.plast_ungapped_keys.restype = ctypes.c_int
+        L.plast_search_keys.argtypes = [P, P, pPrm, P, i32, P, i64, pI64, pI64, P]
+        L.plast_search_keys.restype = ctypes.c_int
+        L.plast_plan_create.argtypes = [P, P, pPrm, i64, P, i64, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.plast_plan_create.restype = ctypes.c_int
+        for f in ("plast_plan_run", "plast_plan_capture", "plast_plan_launch"):
+            getattr(L, f).argtypes = [P, P]
+            getattr(L, f).restype = ctypes.c_int
+        L.plast_plan_result.argtypes = [P, pI64, pI64, P]
+        L.plast_plan_result.restype = ctypes.c_int
+        L.plast_plan_free.argtypes = [P]
+        L.plast_plan_free.restype = None
         L.plast_set_timing.argtypes = [ctypes.c_int]
         L.plast_set_timing.restype = ctypes.c_int
         L.plast_stage_times.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
@@ -290,6 +303,106 @@ def plast_search(b1: Bank, b2: Bank, params: plast_params | None = None, cap: in
             raise PlastError("plast_search", rc, n.value)
         return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
     raise PlastError("plast_search", PLAST_E_CAPACITY, cap)
+
+
+class Plan:
+    """plast_plan: a search of two banks with every buffer allocated up front
+    (at most ``max_hits`` stage-2 hits, ``max_records`` records), runnable
+    without allocation or host synchronisation and capturable in a CUDA
+    graph.  The banks must outlive the plan."""
+
+    def __init__(self, b1: Bank, b2: Bank, max_hits: int, max_records: int, params: plast_params | None = None,
+                 stream=None):
+        self.banks = (b1, b2)
+        self.records = torch.empty(max(max_records, 1) * GAPPED_BYTES, dtype=torch.uint8,
+                                   device=torch.device("cuda", torch.cuda.current_device()))
+        self.handle = ctypes.c_void_p()
+        rc = lib().plast_plan_create(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                     max_hits, _ptr(self.records), max_records, _stream(stream),
+                                     ctypes.byref(self.handle))
+        if rc:
+            self.handle = None
+            raise PlastError("plast_plan_create", rc)
+
+    def _call(self, name, stream):
+        rc = getattr(lib(), name)(self.handle, _stream(stream))
+        if rc:
+            raise PlastError(name, rc)
+
+    def run(self, stream=None):
+        self._call("plast_plan_run", stream)
+
+    def capture(self, stream):
+        self._call("plast_plan_capture", stream)
+
+    def launch(self, stream=None):
+        self._call("plast_plan_launch", stream)
+
+    def result(self, stream=None):
+        """(records [n, 28] uint8 view of the plan's output, stage-2 hits) of
+        the last run; synchronises ``stream``."""
+        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().plast_plan_result(self.handle, ctypes.byref(n), ctypes.byref(nu), _stream(stream))
+        if rc:
+            raise PlastError("plast_plan_result", rc, n.value)
+        return self.records[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
+
+    def free(self):
+        if self.handle:
+            lib().plast_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _keys_host(keys) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(keys, dtype=np.int32))
+
+
+def plast_ungapped_keys(b1: Bank, b2: Bank, keys, params: plast_params | None = None, cap: int | None = None,
+                        stream=None) -> torch.Tensor:
+    """plast_ungapped over the subset-seed keys ``keys`` only (host list)."""
+    k = _keys_host(keys)
+    if cap is None:
+        cap = 1 << 20
+    for _ in range(2):
+        buf = _records(None, cap, HIT_BYTES)
+        n = ctypes.c_int64()
+        rc = lib().plast_ungapped_keys(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                       k.ctypes.data_as(ctypes.c_void_p), len(k), _ptr(buf), cap, ctypes.byref(n),
+                                       _stream(stream))
+        if rc == PLAST_E_CAPACITY:
+            cap = n.value
+            continue
+        if rc:
+            raise PlastError("plast_ungapped_keys", rc, n.value)
+        return buf[: n.value * HIT_BYTES].view(-1, HIT_BYTES)
+    raise PlastError("plast_ungapped_keys", PLAST_E_CAPACITY, cap)
+
+
+def plast_search_keys(b1: Bank, b2: Bank, keys, params: plast_params | None = None, cap: int | None = None,
+                      stream=None):
+    """plast_search over the subset-seed keys ``keys`` only: (records, stage-2 hits)."""
+    k = _keys_host(keys)
+    if cap is None:
+        cap = 1 << 20
+    for _ in range(2):
+        buf = _records(None, cap, GAPPED_BYTES)
+        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().plast_search_keys(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                     k.ctypes.data_as(ctypes.c_void_p), len(k), _ptr(buf), cap, ctypes.byref(n),
+                                     ctypes.byref(nu), _stream(stream))
+        if rc == PLAST_E_CAPACITY:
+            cap = n.value
+            continue
+        if rc:
+            raise PlastError("plast_search_keys", rc, n.value)
+        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
+    raise PlastError("plast_search_keys", PLAST_E_CAPACITY, cap)
 
 
 def plast_translate6(dna: torch.Tensor, contig_off: torch.Tensor, stream=None):

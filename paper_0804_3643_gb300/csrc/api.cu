@@ -124,11 +124,13 @@ struct TileList {
   int64_t pairs = 0;
 };
 
-void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl) {
+void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl,
+                 const std::vector<char>* key_mask = nullptr) {
   tl->tiles.clear();
   tl->pairs = 0;
   std::vector<std::pair<int64_t, int4>> w;
   for (int k = 0; k < NKEYS; k++) {
+    if (key_mask && !(*key_mask)[k]) continue;
     int64_t n1 = b1->h_key_off[k + 1] - b1->h_key_off[k];
     int64_t n2 = b2->h_key_off[k + 1] - b2->h_key_off[k];
     if (n1 == 0 || n2 == 0) continue;
@@ -156,12 +158,12 @@ struct Survivors {
 };
 
 int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, cudaStream_t st, Scratch& sc,
-                 Survivors* sv) {
+                 Survivors* sv, const std::vector<char>* key_mask = nullptr) {
   sv->n = 0;
   sv->sh = b2->pad_bits;
   TileList tl;
   const int mode = g_schedule.load();
-  build_tiles(b1, b2, mode == 0, &tl);
+  build_tiles(b1, b2, mode == 0, &tl, key_mask);
   t_timer.mark(0, st);
   if (tl.tiles.empty()) return PLAST_OK;
   const int64_t nt = (int64_t)tl.tiles.size();
@@ -443,8 +445,27 @@ int plast_bank_export_index(const plast_bank* b, int64_t* key_off, int32_t* pos,
   return PLAST_OK;
 }
 
+static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+                         const std::vector<char>* mask, plast_hit* out, int64_t cap, int64_t* n_out, void* stream);
+
 int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_hit* out,
                    int64_t cap, int64_t* n_out, void* stream) {
+  return ungapped_impl(b1, b2, params, nullptr, out, cap, n_out, stream);
+}
+
+int plast_ungapped_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
+                        int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out, void* stream) {
+  if ((!keys && n_keys != 0) || n_keys < 0) return PLAST_E_INVALID;
+  std::vector<char> mask(NKEYS, 0);
+  for (int32_t i = 0; i < n_keys; i++) {
+    if (keys[i] < 0 || keys[i] >= NKEYS) return PLAST_E_INVALID;
+    mask[keys[i]] = 1;
+  }
+  return ungapped_impl(b1, b2, params, &mask, out, cap, n_out, stream);
+}
+
+static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+                         const std::vector<char>* mask, plast_hit* out, int64_t cap, int64_t* n_out, void* stream) {
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
@@ -453,7 +474,7 @@ int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_param
   t_timer.reset();
   Scratch sc(st);
   Survivors sv;
-  int rc = run_ungapped(b1, b2, prm, st, sc, &sv);
+  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, mask);
   if (rc) return rc;
   *n_out = sv.n;
   if (sv.n > cap) return PLAST_E_CAPACITY;
@@ -541,9 +562,19 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
   return run_gapped(b1, b2, prm, key, val, n_in, sh, out, cap, n_out, st, sc);
 }
 
-int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
-                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream) {
+static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
+                       int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
+                       void* stream) {
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  std::vector<char> mask;
+  if (keys) {
+    if (n_keys < 0) return PLAST_E_INVALID;
+    mask.assign(NKEYS, 0);
+    for (int32_t i = 0; i < n_keys; i++) {
+      if (keys[i] < 0 || keys[i] >= NKEYS) return PLAST_E_INVALID;
+      mask[keys[i]] = 1;
+    }
+  }
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
   *n_out = 0;
@@ -552,10 +583,24 @@ int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params*
   t_timer.reset();
   Scratch sc(st);
   Survivors sv;
-  int rc = run_ungapped(b1, b2, prm, st, sc, &sv);
+  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, keys ? &mask : nullptr);
   if (rc) return rc;
   if (n_ungapped_out) *n_ungapped_out = sv.n;
   return run_gapped(b1, b2, prm, sv.key, sv.val, sv.n, sv.sh, out, cap, n_out, st, sc);
+}
+
+int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
+                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream) {
+  return search_impl(b1, b2, params, nullptr, 0, out, cap, n_out, n_ungapped_out, stream);
+}
+
+int plast_search_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
+                      int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
+                      void* stream) {
+  if (!keys && n_keys != 0) return PLAST_E_INVALID;
+  static const int32_t none = 0;
+  return search_impl(b1, b2, params, keys ? keys : &none, keys ? n_keys : 0, out, cap, n_out, n_ungapped_out,
+                     stream);
 }
 
 int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,
@@ -605,6 +650,205 @@ int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_co
   CK(launch_translate6(dna, contig_off, n_contigs, seq_off_out, n_aa, aa_out, st));
   CK(cudaStreamSynchronize(st));
   return PLAST_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Planned search: every buffer sized up front, so the chain of stages 1-3.1
+// runs with no allocation and no host synchronisation and can be captured in
+// a CUDA graph.  The survivor count flows between kernels in device memory.
+// ---------------------------------------------------------------------------
+struct plast_plan {
+  const plast_bank* b1 = nullptr;
+  const plast_bank* b2 = nullptr;
+  plast_params prm{};
+  int device = 0;
+  int64_t max_hits = 0, max_records = 0, n_tiles = 0;
+  int sh = 0, bits = 0;
+  bool alt = false;
+  int4* tiles = nullptr;
+  int32_t* counter = nullptr;
+  unsigned long long* count = nullptr;
+  int64_t* n_dev = nullptr;
+  uint64_t *k0 = nullptr, *k1 = nullptr;
+  uint32_t *v0 = nullptr, *v1 = nullptr;
+  void* rtmp = nullptr;
+  size_t rtb = 0;
+  int32_t* score = nullptr;
+  uint32_t* ends = nullptr;
+  int32_t* pass = nullptr;
+  int64_t* at = nullptr;
+  int64_t* total = nullptr;
+  void* stmp = nullptr;
+  size_t stb = 0;
+  plast_gapped* out = nullptr;  // caller's buffer
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+void plast_plan_free(plast_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (void* q : {(void*)p->tiles, (void*)p->counter, (void*)p->count, (void*)p->n_dev, (void*)p->k0, (void*)p->k1,
+                  (void*)p->v0, (void*)p->v1, p->rtmp, (void*)p->score, (void*)p->ends, (void*)p->pass,
+                  (void*)p->at, (void*)p->total, p->stmp})
+    if (q) cudaFree(q);
+  delete p;
+}
+
+int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int64_t max_hits,
+                      plast_gapped* records, int64_t max_records, void* stream, plast_plan** out) {
+  if (!b1 || !b2 || !out || !records || max_hits < 1 || max_records < 1 || !params_ok(params))
+    return PLAST_E_INVALID;
+  if (max_hits > ((int64_t)1 << 34) || max_records > ((int64_t)1 << 34)) return PLAST_E_INVALID;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(upload_tables_once());
+  plast_plan* p = new (std::nothrow) plast_plan();
+  if (!p) return PLAST_E_OOM;
+  cudaGetDevice(&p->device);
+  p->b1 = b1;
+  p->b2 = b2;
+  p->prm = resolve(params);
+  p->max_hits = max_hits;
+  p->max_records = max_records;
+  p->out = records;
+  p->sh = b2->pad_bits;
+  p->bits = b1->pad_bits + p->sh;
+  p->alt = ((p->bits + 7) / 8) % 2 == 1;
+  auto fail = [&](cudaError_t e) {
+    plast_plan_free(p);
+    return rc_of(e);
+  };
+  TileList tl;
+  build_tiles(b1, b2, true, &tl);
+  p->n_tiles = (int64_t)tl.tiles.size();
+  cudaError_t e;
+  auto alloc = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes < 16 ? 16 : bytes); };
+  p->rtb = radix_tmp_bytes(max_hits);
+  p->stb = scan_tmp_bytes(max_hits);
+  if ((e = alloc((void**)&p->tiles, sizeof(int4) * (size_t)std::max<int64_t>(p->n_tiles, 1))) ||
+      (e = alloc((void**)&p->counter, sizeof(int32_t))) || (e = alloc((void**)&p->count, sizeof(unsigned long long))) ||
+      (e = alloc((void**)&p->n_dev, sizeof(int64_t))) || (e = alloc((void**)&p->k0, 8 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->k1, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->v0, 4 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->v1, 4 * (size_t)max_hits)) || (e = alloc(&p->rtmp, p->rtb)) ||
+      (e = alloc((void**)&p->score, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->ends, 4 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->at, 8 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->total, sizeof(int64_t))) || (e = alloc(&p->stmp, p->stb)))
+    return fail(e);
+  if (p->n_tiles > 0 &&
+      (e = cudaMemcpyAsync(p->tiles, tl.tiles.data(), sizeof(int4) * p->n_tiles, cudaMemcpyHostToDevice, st)))
+    return fail(e);
+  // set the kernels' shared-memory attributes now, outside any capture
+  UngArgs none{};
+  GapArgs gnone{};
+  gnone.n = 0;
+  if ((e = launch_ungapped(none, 0, st)) || (e = launch_small_gapped(gnone, st))) return fail(e);
+  if ((e = cudaStreamSynchronize(st))) return fail(e);
+  *out = p;
+  return PLAST_OK;
+}
+
+int plast_plan_run(plast_plan* p, void* stream) {
+  if (!p) return PLAST_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(p->counter, 0, sizeof(int32_t), st));
+  CK(cudaMemsetAsync(p->count, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(p->total, 0, sizeof(int64_t), st));
+  if (p->n_tiles > 0) {
+    UngArgs a;
+    a.nb1 = p->b1->nb;
+    a.pos1 = p->b1->pos;
+    a.nb2 = p->b2->nb;
+    a.pos2 = p->b2->pos;
+    a.key_off2 = p->b2->key_off;
+    a.tiles = p->tiles;
+    a.n_tiles = (int32_t)p->n_tiles;
+    a.tile_base = 0;
+    a.tile_counter = p->counter;
+    a.persistent = 1;
+    a.s1 = p->prm.s1;
+    a.out_key = p->k0;
+    a.out_val = p->v0;
+    a.out_count = p->count;
+    a.cap = p->max_hits;
+    a.sh = p->sh;
+    CK(launch_ungapped(a, (int)std::min<int64_t>(num_sms(), p->n_tiles), st));
+  }
+  CK(launch_clamp_count(p->count, p->max_hits, p->n_dev, st));
+  bool alt = false;
+  CK(radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, p->max_hits, p->bits, p->rtmp, p->rtb, st, &alt, p->n_dev));
+  GapArgs g;
+  g.pad1 = p->b1->pad;
+  g.pad2 = p->b2->pad;
+  g.key = alt ? p->k1 : p->k0;
+  g.val = alt ? p->v1 : p->v0;
+  g.n = p->max_hits;
+  g.sh = p->sh;
+  g.gap_open = p->prm.gap_open;
+  g.gap_extend = p->prm.gap_extend;
+  g.s2 = p->prm.s2;
+  g.score = p->score;
+  g.ends = p->ends;
+  g.pass = p->pass;
+  g.n_dev = p->n_dev;
+  g.out_cap = p->max_records;
+  CK(launch_small_gapped(g, st));
+  CK(scan_exclusive(g.pass, p->at, p->max_hits, p->total, p->stmp, p->stb, st, p->n_dev));
+  CK(launch_gapped_compact(g, p->at, p->b1->pad_off, p->b1->n_seqs, p->b2->pad_off, p->b2->n_seqs, p->out, st));
+  return PLAST_OK;
+}
+
+int plast_plan_capture(plast_plan* p, void* stream) {
+  if (!p || !stream) return PLAST_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+  }
+  if (p->graph) {
+    cudaGraphDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = plast_plan_run(p, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return rc_of(e);
+  p->graph = g;
+  CK(cudaGraphInstantiate(&p->exec, g, 0));
+  return PLAST_OK;
+}
+
+int plast_plan_launch(plast_plan* p, void* stream) {
+  if (!p || !p->exec) return PLAST_E_INVALID;
+  CK(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  return PLAST_OK;
+}
+
+int plast_plan_result(const plast_plan* p, int64_t* n_records, int64_t* n_hits, void* stream) {
+  if (!p || !n_records) return PLAST_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long hits = 0;
+  int64_t recs = 0;
+  CK(cudaMemcpyAsync(&hits, p->count, sizeof(hits), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&recs, p->total, sizeof(recs), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (n_hits) *n_hits = (int64_t)hits;
+  if ((int64_t)hits > p->max_hits) {
+    *n_records = (int64_t)hits;
+    return PLAST_E_CAPACITY;
+  }
+  *n_records = recs;
+  return recs > p->max_records ? PLAST_E_CAPACITY : PLAST_OK;
 }
 
 }  // extern "C"

@@ -118,11 +118,14 @@ namespace plast {
 void note_launch();  // counts every kernel launch of the library
 long long launch_total();
 cudaError_t upload_tables_once();
+// n_dev (optional, device): the actual element count, at most n; the grids
+// are sized for n so the launches need no host copy of the count.
 cudaError_t scan_exclusive(const int32_t* in, int64_t* out, int64_t n, int64_t* d_total, void* tmp,
-                           size_t tmp_bytes, cudaStream_t st);
+                           size_t tmp_bytes, cudaStream_t st, const int64_t* n_dev = nullptr);
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                             int bits, void* tmp, size_t tmp_bytes, cudaStream_t st, bool* result_in_alt);
+                             int bits, void* tmp, size_t tmp_bytes, cudaStream_t st, bool* result_in_alt,
+                             const int64_t* n_dev = nullptr);
 size_t radix_tmp_bytes(int64_t n);
 
 }  // namespace plast

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   const unsigned char* tlane = reinterpret_cast<const unsigned char*>(tab32) + lane * 4;
   const int go = a.gap_open, ge = a.gap_extend, goe = go + ge;
   const uint32_t nge2 = x2(-ge), goe2 = x2(goe);
-  const int64_t npairs = (a.n + 1) / 2;  // hits 2p and 2p+1 share a thread
+  const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
+  const int64_t npairs = (n + 1) / 2;  // hits 2p and 2p+1 share a thread
   const int64_t total = 2 * npairs;      // (pair, side) threads
   const int64_t stride = (int64_t)gridDim.x * GAP_THREADS;
   for (int64_t base = (int64_t)blockIdx.x * GAP_THREADS + warp * 32; base < total; base += stride) {
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
     const int64_t pr = t >> 1;
     const int side = (int)(t & 1);  // 0: right of the seed start, 1: left of it
     const bool active = t < total;
-    const int64_t h0 = 2 * pr, h1 = 2 * pr + 1 < a.n ? 2 * pr + 1 : 2 * pr;
+    const int64_t h0 = 2 * pr, h1 = 2 * pr + 1 < n ? 2 * pr + 1 : 2 * pr;
     Band B;
     if (active) {
       const uint64_t k0 = a.key[h0], k1 = a.key[h1];
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
       a.score[h0] = g0;
       a.ends[h0] = (uint32_t)bi0 | ((uint32_t)bj0 << 8) | ((uint32_t)obi0 << 16) | ((uint32_t)obj0 << 24);
       a.pass[h0] = g0 >= a.s2;
-      if (2 * pr + 1 < a.n) {
+      if (2 * pr + 1 < n) {
         const int g1 = (int16_t)(B.best >> 16) + (int16_t)(ob >> 16);
         a.score[h1] = g1;
         a.ends[h1] = (uint32_t)bi1 | ((uint32_t)bj1 << 8) | ((uint32_t)obi1 << 16) | ((uint32_t)obj1 << 24);
@@ -266,8 +267,9 @@ __device__ __forceinline__ int32_t find_seq_g(const int64_t* off, int32_t n, int
 
 __global__ void k_gapped_compact(GapArgs a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
                                  const int64_t* pad_off2, int32_t n2, plast_gapped* out) {
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < a.n; h += (int64_t)gridDim.x * blockDim.x) {
-    if (!a.pass[h]) continue;
+  const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
+    if (!a.pass[h] || at[h] >= a.out_cap) continue;
     const uint64_t key = a.key[h];
     const int64_t p1 = (int64_t)(key >> a.sh), p2 = (int64_t)(key & ((1ull << a.sh) - 1));
     const int32_t q1 = find_seq_g(pad_off1, n1, p1), q2 = find_seq_g(pad_off2, n2, p2);
@@ -294,6 +296,17 @@ cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int
   if (b > 152 * 32) b = 152 * 32;
   note_launch();
   k_gapped_compact<<<(unsigned)b, 256, 0, st>>>(a, at, pad_off1, n1, pad_off2, n2, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev) {
+  const unsigned long long c = *count;
+  *n_dev = c > (unsigned long long)cap ? cap : (int64_t)c;
+}
+
+cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st) {
+  note_launch();
+  k_clamp_count<<<1, 1, 0, st>>>(count, cap, n_dev);
   return cudaGetLastError();
 }
 

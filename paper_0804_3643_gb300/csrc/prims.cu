@@ -116,7 +116,13 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* tota
   return r;
 }
 
-__global__ void k_scan_tile_sums(const int32_t* in, int64_t n, int64_t* sums) {
+// n_dev (optional): the element count lives in device memory, at most n.
+__device__ __forceinline__ int64_t count_of(int64_t n, const int64_t* n_dev) {
+  return n_dev ? min(n, max(*n_dev, (int64_t)0)) : n;
+}
+
+__global__ void k_scan_tile_sums(const int32_t* in, int64_t n, int64_t* sums, const int64_t* n_dev) {
+  n = count_of(n, n_dev);
   int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
   int64_t acc = 0;
 #pragma unroll
@@ -142,7 +148,8 @@ __global__ void k_scan_sums(int64_t* sums, int64_t nt, int64_t* d_total) {
   if (threadIdx.x == 0 && d_total) *d_total = carry;
 }
 
-__global__ void k_scan_tiles(const int32_t* in, int64_t n, const int64_t* sums, int64_t* out) {
+__global__ void k_scan_tiles(const int32_t* in, int64_t n, const int64_t* sums, int64_t* out, const int64_t* n_dev) {
+  n = count_of(n, n_dev);
   // thread t owns the contiguous items [t*ITEMS, t*ITEMS + ITEMS) of the tile
   int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
   int32_t v[SCAN_ITEMS];
@@ -168,7 +175,7 @@ size_t scan_tmp_bytes(int64_t n) {
 }
 
 cudaError_t scan_exclusive(const int32_t* in, int64_t* out, int64_t n, int64_t* d_total, void* tmp,
-                           size_t tmp_bytes, cudaStream_t st) {
+                           size_t tmp_bytes, cudaStream_t st, const int64_t* n_dev) {
   if (n <= 0) {
     if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(int64_t), st);
     return cudaSuccess;
@@ -177,11 +184,11 @@ cudaError_t scan_exclusive(const int32_t* in, int64_t* out, int64_t n, int64_t* 
   if (tmp_bytes < scan_tmp_bytes(n)) return cudaErrorInvalidValue;
   int64_t* sums = (int64_t*)tmp;
   note_launch();
-  k_scan_tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, sums);
+  k_scan_tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, sums, n_dev);
   note_launch();
   k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nt, d_total);
   note_launch();
-  k_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, sums, out);
+  k_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, n, sums, out, n_dev);
   return cudaGetLastError();
 }
 
@@ -195,8 +202,10 @@ constexpr int RS_ROUNDS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
 constexpr int RS_WARPS = RS_THREADS / 32;
 
-__global__ void k_radix_hist(const uint64_t* keys, int64_t n, int shift, int32_t* hist, int64_t nt) {
+__global__ void k_radix_hist(const uint64_t* keys, int64_t n, int shift, int32_t* hist, int64_t nt,
+                             const int64_t* n_dev) {
   __shared__ int h[256];
+  n = count_of(n, n_dev);
   h[threadIdx.x] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_TILE;
@@ -210,7 +219,8 @@ __global__ void k_radix_hist(const uint64_t* keys, int64_t n, int shift, int32_t
 }
 
 __global__ void k_radix_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
-                                int shift, const int64_t* off, int64_t nt) {
+                                int shift, const int64_t* off, int64_t nt, const int64_t* n_dev) {
+  n = count_of(n, n_dev);
   __shared__ int64_t s_base[256];
   __shared__ int s_cnt[RS_WARPS][256];
   __shared__ int s_run[256];
@@ -258,9 +268,10 @@ size_t radix_tmp_bytes(int64_t n) {
 }
 
 cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                             int bits, void* tmp, size_t tmp_bytes, cudaStream_t st, bool* result_in_alt) {
+                             int bits, void* tmp, size_t tmp_bytes, cudaStream_t st, bool* result_in_alt,
+                             const int64_t* n_dev) {
   *result_in_alt = false;
-  if (n <= 1 || bits <= 0) return cudaSuccess;
+  if ((n <= 1 && !n_dev) || n <= 0 || bits <= 0) return cudaSuccess;
   if (tmp_bytes < radix_tmp_bytes(n)) return cudaErrorInvalidValue;
   int64_t nt = (n + RS_TILE - 1) / RS_TILE;
   size_t h = (size_t)256 * nt;
@@ -273,11 +284,11 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
   bool alt = false;
   for (int shift = 0; shift < bits; shift += 8) {
     note_launch();
-    k_radix_hist<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, n, shift, hist, nt);
+    k_radix_hist<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, n, shift, hist, nt, n_dev);
     cudaError_t e = scan_exclusive(hist, off, (int64_t)h, nullptr, stmp, stmp_bytes, st);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_radix_scatter<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, off, nt);
+    k_radix_scatter<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, off, nt, n_dev);
     uint64_t* tk = ki;
     ki = ko;
     ko = tk;

@@ -41,10 +41,14 @@ struct GapArgs {
   int32_t* score;           // out: small gapped score per hit
   uint32_t* ends;           // out: r_i | r_j << 8 | l_i << 16 | l_j << 24
   int32_t* pass;            // out: score >= s2
+  const int64_t* n_dev = nullptr;  // optional device copy of the hit count (<= n)
+  int64_t out_cap = INT64_MAX;     // records written only below this index
 };
 cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st);
 cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
                                   const int64_t* pad_off2, int32_t n2, plast_gapped* out, cudaStream_t st);
+// *n_dev = min(*count, cap): the hit count a planned chain feeds forward.
+cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st);
 cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* pad_off1, int32_t n1,
                                 const int64_t* pad_off2, int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad,
                                 cudaStream_t st);

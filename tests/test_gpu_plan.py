@@ -1,0 +1,77 @@
+"""Planned search (preallocated, no host synchronisation) and its CUDA-graph
+replay give the oracle's records, the same as plast_search; exceeding either
+limit reports PLAST_E_CAPACITY."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_0804_3643_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_0804_3643_gb300 import binding, build
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    build.build()
+    binding.lib()
+    binding.plast_set_schedule(0)
+    return binding
+
+
+@pytest.fixture(scope="module")
+def banks(B):
+    b1, b2 = synth.workload("plastp_plain", seed=3, scale=0.5)
+    out = []
+    for b in (b1, b2):
+        d = B.DeviceBank.from_host(b.codes, b.seq_off)
+        out.append(B.plast_index_bank(d.codes, d.seq_off))
+    o1 = oracle.make_bank(b1.codes, b1.seq_off)
+    o2 = oracle.make_bank(b2.codes, b2.seq_off)
+    hits = oracle.ungapped(o1, o2, threads=16)
+    want = oracle.small_gapped(o1, o2, hits)
+    return out[0], out[1], len(hits), want
+
+
+def test_plan_run_and_graph_replay(B, banks):
+    g1, g2, n_hits, want = banks
+    assert len(want) > 50
+    plan = B.Plan(g1, g2, max_hits=2 * n_hits + 1000, max_records=len(want) + 100)
+    plan.run()
+    recs, nu = plan.result()
+    assert nu == n_hits
+    got = B.gapped_numpy(recs)
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+    ref, nu2 = B.plast_search(g1, g2)
+    assert nu2 == n_hits and torch.equal(ref, recs)
+
+    st = torch.cuda.Stream()
+    plan.capture(st)
+    for _ in range(2):
+        plan.records.fill_(0xAB)
+        plan.launch(st)
+        recs, nu = plan.result(st)
+        assert nu == n_hits
+        assert np.array_equal(B.gapped_numpy(recs).view(np.uint8), want.view(np.uint8))
+    plan.free()
+
+
+def test_plan_capacity_errors(B, banks):
+    g1, g2, n_hits, want = banks
+    small_hits = B.Plan(g1, g2, max_hits=n_hits // 2, max_records=len(want) + 100)
+    small_hits.run()
+    with pytest.raises(B.PlastError) as e:
+        small_hits.result()
+    assert e.value.code == B.PLAST_E_CAPACITY and e.value.needed == n_hits
+    small_recs = B.Plan(g1, g2, max_hits=n_hits + 10, max_records=len(want) - 1)
+    small_recs.run()
+    with pytest.raises(B.PlastError) as e:
+        small_recs.result()
+    assert e.value.code == B.PLAST_E_CAPACITY and e.value.needed == len(want)
+    # the records that fit are the first ones of the canonical order
+    got = B.gapped_numpy(small_recs.records[: (len(want) - 1) * B.GAPPED_BYTES].view(-1, B.GAPPED_BYTES))
+    assert np.array_equal(got.view(np.uint8), want[:-1].view(np.uint8))
