@@ -214,6 +214,19 @@ def committed_traffic():
     return t
 
 
+def setup_tiles(args, B) -> dict:
+    """Stage-2 tile shape policy and its cost constants (measured on this
+    device by the library's calibration unless --no-autotune)."""
+    B.plast_set_tile_shape({"auto": 0, "wide": 1, "narrow": 2}[args.tile_shape])
+    if args.no_autotune:
+        c = dict(B.plast_get_tile_costs(), source="defaults")
+    else:
+        t0 = time.time()
+        c = B.autotune()
+        log(f"tile costs ({c['source']}, {time.time() - t0:.2f}s): {c}")
+    return dict(c, shape=args.tile_shape)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -226,6 +239,7 @@ def run_gpu(args, rank, world, local_rank):
         build.build()
     B.lib()
     B.plast_set_schedule(1 if args.schedule == "per_key" else 0)
+    tiles = setup_tiles(args, B)
 
     t0 = time.time()
     b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale, n2=2)
@@ -356,6 +370,7 @@ def run_gpu(args, rank, world, local_rank):
             "records_per_step": n_recs,
             "params": B.plast_default_params().as_dict(),
             "schedule": args.schedule,
+            "stage2_tiles": tiles,
             "l2": f"inputs larger than L2 (129 MB): {nb_gb:.2f} GB of neighbourhood arrays rebuilt and "
                   "read every step, no explicit flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -412,6 +427,7 @@ def run_stress(args):
 
     from paper_0804_3643_gb300 import binding as B
 
+    tiles = setup_tiles(args, B)
     b1, b2 = synth.workload("batching_stress", seed=1, scale=args.scale)
     d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
     d2 = B.DeviceBank.from_host(b2.codes, b2.seq_off)
@@ -445,7 +461,7 @@ def run_stress(args):
         "pairs": pairs, "stage2_hits": n_ung, "records": int(recs.shape[0]),
         "pairs_per_key": {"max": int(per_key.max()), "p50": float(np.median(per_key[per_key > 0])),
                           "keys_over_1e6": int((per_key > 1e6).sum())},
-        "schedules": res,
+        "schedules": res, "stage2_tiles": tiles,
         "speedup_persistent_over_per_key": res["per_key"]["ms_per_search"] / res["persistent"]["ms_per_search"],
     }
 
@@ -457,6 +473,7 @@ def run_tplastn(args):
 
     from paper_0804_3643_gb300 import binding as B
 
+    tiles = setup_tiles(args, B)
     b1, dna = synth.tplastn_workload(seed=1, scale=args.scale)
     d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
     hd = torch.from_numpy(dna.codes).cuda()
@@ -485,15 +502,74 @@ def run_tplastn(args):
         "value": pairs / (ms / 1e3), "ms_per_step": ms,
         "workload": f"TPLAST-N: {b1.n_seqs} proteins vs {len(dna.codes) / 1e6:.1f} Mbp in {dna.n_seqs} contigs "
                     f"({len(aa)} translated residues), {len(dna.planted['regions'])} planted regions, seed 1",
-        "pairs": pairs, "stage2_hits": n_ung, "records": n_rec,
+        "pairs": pairs, "stage2_hits": n_ung, "records": n_rec, "stage2_tiles": tiles,
+    }
+
+
+def run_query(args):
+    """One query bank of --query-proteins proteins against a resident bank of
+    --bank2-proteins (default 1,000,000): the search a serving request runs,
+    timed three ways: the plain call (plast_search: work list, allocation and
+    the survivor-count read on the host), the planned search (buffers
+    allocated once, no host synchronisation inside) and its CUDA-graph
+    replay."""
+    import torch
+
+    from paper_0804_3643_gb300 import binding as B
+
+    B.lib()
+    tiles = setup_tiles(args, B)
+    n_bank = args.bank2_proteins or 1_000_000
+    t0 = time.time()
+    bank = synth.random_protein_bank(np.random.default_rng(1), max(2, int(n_bank * args.scale)))
+    q = synth.random_protein_bank(np.random.default_rng(2), args.query_proteins)
+    db = B.DeviceBank.from_host(bank.codes, bank.seq_off)
+    dq = B.DeviceBank.from_host(q.codes, q.seq_off)
+    gb = B.plast_index_bank(db.codes, db.seq_off)
+    gq = B.plast_index_bank(dq.codes, dq.seq_off)
+    log(f"banks ready in {time.time() - t0:.1f}s")
+    pairs = B.plast_pair_count(gq, gb)
+    ref, n_ung = B.plast_search(gq, gb)
+    st = torch.cuda.Stream()
+    plan = B.Plan(gq, gb, max_hits=2 * n_ung + 4096, max_records=2 * ref.shape[0] + 1024, stream=st)
+    plan.capture(st)
+    res = {}
+    with torch.cuda.stream(st):
+        res["search_ms"] = _time_steps(lambda: B.plast_search(gq, gb, stream=st), args.steps, args.warmup)
+        res["plan_ms"] = _time_steps(lambda: (plan.run(st), plan.result(st)), args.steps, args.warmup)
+        res["graph_ms"] = _time_steps(lambda: (plan.launch(st), plan.result(st)), args.steps, args.warmup)
+    recs, nu = plan.result(st)
+    if not (torch.equal(recs, ref) and nu == n_ung):
+        raise RuntimeError("planned search differs from plast_search")
+    B.plast_set_timing(True)
+    stages = []
+    for _ in range(3):
+        B.plast_search(gq, gb, stream=st)
+        stages.append(B.plast_stage_times())
+    B.plast_set_timing(False)
+    res["stage_ms"] = {k: round(statistics.median(x[k] for x in stages), 3) for k in stages[0]}
+    t1 = time.perf_counter()
+    gq2 = B.plast_index_bank(dq.codes, dq.seq_off, stream=st)
+    st.synchronize()
+    res["query_index_ms"] = (time.perf_counter() - t1) * 1e3
+    del gq2
+    return {
+        "metric": "query search latency against a resident bank (plain call / planned / CUDA graph)", "unit": "ms",
+        "workload": f"{q.n_seqs} random proteins ({len(q.codes)} residues) vs a resident bank of {bank.n_seqs} "
+                    f"random proteins ({len(bank.codes)} residues)",
+        "pairs": pairs, "stage2_hits": n_ung, "records": int(ref.shape[0]),
+        **res, "pairs_per_s_graph": pairs / (res["graph_ms"] / 1e3), "stage2_tiles": tiles,
     }
 
 
 def run_serving(args):
     """A resident bank of 1,000,000 proteins; query banks of 1-500 proteins
     arriving as Poisson processes; continuous batching."""
+    from paper_0804_3643_gb300 import binding as B
     from paper_0804_3643_gb300 import serve
 
+    B.lib()
+    tiles = setup_tiles(args, B)
     rng = np.random.default_rng(1)
     n_res = max(1000, int(1_000_000 * args.scale))
     t0 = time.time()
@@ -518,7 +594,7 @@ def run_serving(args):
     return {"metric": "serving latency p50/p99 and pairs/s under continuous batching", "unit": "ms",
             "workload": f"resident bank of {n_res} synthetic proteins ({len(bank.codes)} residues); "
                         f"{args.requests} query banks of U(1..500) proteins per rate, Poisson arrivals",
-            "slots": 2, "rows": rows}
+            "slots": 2, "stage2_tiles": tiles, "rows": rows}
 
 
 
@@ -532,10 +608,14 @@ def main():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_key"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow"],
+                    help="stage-2 tile shapes: by measured cost (default) or forced")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile costs")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batching_stress", "tplastn", "serving"],
+                    choices=[WORKLOAD, "batching_stress", "tplastn", "serving", "query"],
                     help="the headline line is plastp_full; the others print their own lines")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per arrival rate")
+    ap.add_argument("--query-proteins", type=int, default=250, help="query: proteins of the query bank")
     ap.add_argument("--bank2-proteins", type=int, default=None,
                     help="bank-2 size of the headline workload (profiling captures use 10000)")
     args = ap.parse_args()
@@ -565,7 +645,8 @@ def main():
 
     if args.workload != WORKLOAD:
         if rank == 0:
-            fn = {"batching_stress": run_stress, "tplastn": run_tplastn, "serving": run_serving}[args.workload]
+            fn = {"batching_stress": run_stress, "tplastn": run_tplastn, "serving": run_serving,
+                  "query": run_query}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 

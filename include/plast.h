@@ -194,7 +194,8 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
  * ungapped extension of every pair, small gapped extension of the hits
  * scoring >= s1, and the records scoring >= s2 written to out sorted by
  * (seq1, pos1, seq2, pos2).  *n_ungapped_out (host, may be NULL) receives
- * the number of stage-2 hits.  Errors as plast_ungapped.
+ * the number of stage-2 hits (at most 2^32 - 1 per call, else
+ * PLAST_E_CAPACITY).  Errors as plast_ungapped.
  */
 int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
                  int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream);
@@ -239,8 +240,9 @@ int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank* b2, const
  * and returns the record count of the last run (records in canonical order,
  * as plast_search) and its stage-2 hit count; PLAST_E_CAPACITY if either
  * limit was exceeded (*n_records then holds the hit or record count that did
- * not fit, and the records are incomplete).  Runs of one plan must not
- * overlap on the device.
+ * not fit, and the records are an incomplete subset).  PLAST_E_INVALID at
+ * creation unless max_records >= 1 and 1 <= max_hits < 2^32.  Runs of one
+ * plan must not overlap on the device.
  */
 typedef struct plast_plan plast_plan;
 int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int64_t max_hits,
@@ -259,14 +261,52 @@ void plast_plan_free(plast_plan* plan);
 int plast_set_schedule(int mode);
 
 /*
+ * Stage-2 tile shapes.  The work of a key is cut into tiles of consecutive
+ * bank-1 occurrences: wide tiles of 128 rows, whose profile serves 4 bank-2
+ * windows per warp, and narrow tiles of 8 rows, one bank-2 window per lane,
+ * for short lists (a small query bank against a large one, the end of a long
+ * list).  The library picks, per key, the shape of the remainder after the
+ * full wide tiles from a cost model: a tile of shape S costs
+ * S_slot x (rows of S) x ceil(n2 / P_S) x P_S + S_tile SM-nanoseconds, n2 the
+ * key's bank-2 occurrences, P_S the bank-2 windows a CTA scores per pass
+ * (128 wide, 1024 narrow).  plast_autotune measures the four constants on
+ * the current device (random banks, the stage-2 kernel timed with every tile
+ * wide, then every tile narrow, against a long and a short bank 2; about a
+ * second),
+ * installs them and copies them to *out (may be NULL); plast_get_tile_costs /
+ * plast_set_tile_costs read and install them (for a cached calibration;
+ * PLAST_E_INVALID unless the slot costs are positive and the tile costs
+ * non-negative).  plast_set_tile_shape forces the shape of every tile
+ * (1 wide, 2 narrow; 0, the default, by cost).  Shapes change the schedule,
+ * never the results.  Settings are process-wide and apply to later calls.
+ */
+typedef struct plast_tile_costs {
+  double wide_slot, wide_tile, narrow_slot, narrow_tile;
+} plast_tile_costs;
+int plast_autotune(void* stream, plast_tile_costs* out);
+int plast_get_tile_costs(plast_tile_costs* out);
+int plast_set_tile_costs(const plast_tile_costs* costs);
+int plast_set_tile_shape(int mode);
+/*
+ * The stage-2 work list the library would run for two banks with the given
+ * CSR key offsets (host arrays of PLAST_NKEYS + 1 entries each, as
+ * plast_bank_export_index returns): host-only, no device needed.  Fills
+ * tiles[4 * t ..] with (key, first bank-1 CSR index, rows, shape: 0 wide,
+ * 1 narrow) in launch order for t < *n_tiles; PLAST_E_CAPACITY if more than
+ * `cap` tiles (then *n_tiles = needed), PLAST_E_INVALID on decreasing offsets.
+ */
+int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t* tiles, int64_t cap,
+                       int64_t* n_tiles);
+
+/*
  * Instrumentation (no effect on results).
  * plast_set_timing(1) makes later plast_ungapped / plast_small_gapped /
  * plast_search calls of the calling thread record CUDA events on their stream
  * at the stage boundaries; plast_stage_times then fills ms[0 .. n) with the
  * device time of the last call's intervals (-1 where not recorded):
  *   ms[0] work list upload   ms[1] stage-2 kernel   ms[2] survivor count read
- *   and sort                 ms[3] stage-3.1 kernel ms[4] threshold scan and
- *   record write-out.
+ *   (and, for plast_ungapped, the survivor sort)   ms[3] stage-3.1 kernel
+ *   ms[4] threshold scan, record sort (plast_search) and write-out.
  * plast_kernel_launches returns how many kernels the library has launched in
  * this process so far.
  */

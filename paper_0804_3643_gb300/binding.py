@@ -43,6 +43,13 @@ class plast_params(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class plast_tile_costs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class PlastError(RuntimeError):
     def __init__(self, call: str, code: int, needed: int | None = None):
         self.code = code
@@ -106,6 +113,17 @@ def lib() -> ctypes.CDLL:
         L.plast_plan_result.restype = ctypes.c_int
         L.plast_plan_free.argtypes = [P]
         L.plast_plan_free.restype = None
+        pCost = ctypes.POINTER(plast_tile_costs)
+        L.plast_autotune.argtypes = [P, pCost]
+        L.plast_autotune.restype = ctypes.c_int
+        L.plast_get_tile_costs.argtypes = [pCost]
+        L.plast_get_tile_costs.restype = ctypes.c_int
+        L.plast_set_tile_costs.argtypes = [pCost]
+        L.plast_set_tile_costs.restype = ctypes.c_int
+        L.plast_stage2_tiles.argtypes = [P, P, P, i64, pI64]
+        L.plast_stage2_tiles.restype = ctypes.c_int
+        L.plast_set_tile_shape.argtypes = [ctypes.c_int]
+        L.plast_set_tile_shape.restype = ctypes.c_int
         L.plast_set_timing.argtypes = [ctypes.c_int]
         L.plast_set_timing.restype = ctypes.c_int
         L.plast_stage_times.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int]
@@ -167,6 +185,94 @@ def plast_stage_times() -> dict:
 
 def plast_kernel_launches() -> int:
     return int(lib().plast_kernel_launches())
+
+
+def plast_autotune(stream=None) -> dict:
+    c = plast_tile_costs()
+    rc = lib().plast_autotune(_stream(stream), ctypes.byref(c))
+    if rc:
+        raise PlastError("plast_autotune", rc)
+    return c.as_dict()
+
+
+def plast_get_tile_costs() -> dict:
+    c = plast_tile_costs()
+    lib().plast_get_tile_costs(ctypes.byref(c))
+    return c.as_dict()
+
+
+def plast_set_tile_costs(costs: dict) -> None:
+    c = plast_tile_costs(**{k: float(costs[k]) for k, _ in plast_tile_costs._fields_})
+    rc = lib().plast_set_tile_costs(ctypes.byref(c))
+    if rc:
+        raise PlastError("plast_set_tile_costs", rc)
+
+
+def plast_set_tile_shape(mode: int) -> None:
+    """0: by cost (default), 1: every tile wide, 2: every tile narrow."""
+    rc = lib().plast_set_tile_shape(int(mode))
+    if rc:
+        raise PlastError("plast_set_tile_shape", rc)
+
+
+def plast_stage2_tiles(key_off1: np.ndarray, key_off2: np.ndarray) -> np.ndarray:
+    """Host-only: the stage-2 tiles [t, 4] = (key, first bank-1 CSR index,
+    rows, shape) for two banks' CSR key offsets."""
+    k1 = np.ascontiguousarray(key_off1, dtype=np.int64)
+    k2 = np.ascontiguousarray(key_off2, dtype=np.int64)
+    if len(k1) != NKEYS + 1 or len(k2) != NKEYS + 1:
+        raise ValueError("key offsets need NKEYS + 1 entries")
+    n = ctypes.c_int64()
+    cap = 0
+    for _ in range(2):
+        out = np.zeros((max(cap, 1), 4), dtype=np.int32)
+        rc = lib().plast_stage2_tiles(k1.ctypes.data, k2.ctypes.data, out.ctypes.data, cap, ctypes.byref(n))
+        if rc == PLAST_E_CAPACITY:
+            cap = n.value
+            continue
+        if rc:
+            raise PlastError("plast_stage2_tiles", rc)
+        return out[: n.value]
+    raise PlastError("plast_stage2_tiles", PLAST_E_CAPACITY, n.value)
+
+
+def _cost_cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "plast_gb300", "tile_costs.json")
+
+
+def autotune(cache: bool = True, stream=None) -> dict:
+    """Tile costs of the current device: from the cache file when it holds an
+    entry for this device and library build, else measured with
+    plast_autotune (and stored).  Installs them and returns them."""
+    import hashlib
+    import json
+
+    with open(LIB_PATH, "rb") as f:
+        build_id = hashlib.sha256(f.read()).hexdigest()[:16]
+    dev = torch.cuda.get_device_properties(torch.cuda.current_device())
+    entry = f"{dev.name}|{dev.multi_processor_count}|{build_id}"
+    path = _cost_cache_path()
+    table = {}
+    if cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+        if entry in table:
+            plast_set_tile_costs(table[entry])
+            return dict(table[entry], source="cache")
+    costs = plast_autotune(stream)
+    if cache:
+        table[entry] = costs
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(table, f, indent=1)
+        except OSError:
+            pass
+    return dict(costs, source="measured")
 
 
 class Bank:

@@ -1,10 +1,11 @@
 // api.cu -- the C ABI declared in include/plast.h.
 //
 // Host code only: argument checks, bank lifecycle, the stage-2 work list
-// (tiles of up to UNG_T1 = 128 bank-1 occurrences of one key, largest first for
-// the persistent queue), stream-ordered scratch, and the launch sequences of
-// the calls.  Every step of the computation runs in the kernels of
-// index.cu, ungapped.cu, gapped.cu and prims.cu.
+// (tiles of bank-1 occurrences of one key, wide or narrow by measured cost,
+// costliest first for the persistent queue), the tile-cost calibration,
+// stream-ordered scratch, and the launch sequences of the calls.  Every step
+// of the computation runs in the kernels of index.cu, ungapped.cu, gapped.cu
+// and prims.cu.
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -116,37 +117,74 @@ int num_sms() {
   return n;
 }
 
-// Stage-2 work list: for every key present in both banks, tiles of up to
-// UNG_T1 consecutive bank-1 occurrences; work = rows * n2.
+// Stage-2 tile costs in SM-nanoseconds: per slot (a bank-1 row of the tile's
+// shape against a bank-2 window: 48 cells, whatever the tile's fill) and per
+// tile.  A CTA moves through a key's bank-2 windows WINDOWS_PER_PASS at a
+// time (32 warps x 4 windows wide, x 32 narrow), so a tile is charged its
+// shape's rows x n2 rounded up to that granularity.  Defaults from a GB300;
+// plast_autotune measures them on the current device.
+std::mutex g_cost_mu;
+plast_tile_costs g_costs = {0.40, 6800.0, 0.71, 2500.0};
+std::atomic<int> g_shape{0};  // 0: by cost, 1: wide only, 2: narrow only
+constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
+constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tile
+int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) / g * g; }
+
+// Stage-2 work list: for every key present in both banks, tiles of
+// consecutive bank-1 occurrences.  Full wide tiles of UNG_T1 rows; the
+// remainder (or a short list) goes to one wide tile or to narrow tiles of
+// UNG_NT1 rows, whichever the cost model says is cheaper.
 struct TileList {
-  std::vector<int4> tiles;        // (key, first CSR index of bank 1, rows, 0)
-  std::vector<int32_t> key_first; // plain schedule: first tile of each key (key order)
+  std::vector<int4> tiles;        // (key, first CSR index of bank 1, rows, shape)
   int64_t pairs = 0;
 };
 
-void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl,
-                 const std::vector<char>* key_mask = nullptr) {
+void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first, TileList* tl,
+                      const std::vector<char>* key_mask, int shape_override) {
   tl->tiles.clear();
   tl->pairs = 0;
-  std::vector<std::pair<int64_t, int4>> w;
+  plast_tile_costs c;
+  {
+    std::lock_guard<std::mutex> lk(g_cost_mu);
+    c = g_costs;
+  }
+  const int shape = shape_override >= 0 ? shape_override : g_shape.load();
+  std::vector<std::pair<double, int4>> w;
   for (int k = 0; k < NKEYS; k++) {
     if (key_mask && !(*key_mask)[k]) continue;
-    int64_t n1 = b1->h_key_off[k + 1] - b1->h_key_off[k];
-    int64_t n2 = b2->h_key_off[k + 1] - b2->h_key_off[k];
+    const int64_t n1 = ko1[k + 1] - ko1[k];
+    const int64_t n2 = ko2[k + 1] - ko2[k];
     if (n1 == 0 || n2 == 0) continue;
     tl->pairs += n1 * n2;
-    for (int64_t u = 0; u < n1; u += UNG_T1) {
-      int rows = (int)std::min<int64_t>(UNG_T1, n1 - u);
-      int4 t = make_int4(k, (int)(b1->h_key_off[k] + u), rows, 0);
-      w.push_back({(int64_t)rows * n2, t});
+    const int64_t first = ko1[k];
+    const double cost_w = c.wide_slot * UNG_T1 * (double)round_up(n2, WIDE_PASS) + c.wide_tile;
+    const double cost_n = c.narrow_slot * UNG_NT1 * (double)round_up(n2, NARROW_PASS) + c.narrow_tile;
+    int64_t u = 0;
+    if (shape != 2)
+      for (; n1 - u >= UNG_T1; u += UNG_T1) w.push_back({cost_w, make_int4(k, (int)(first + u), UNG_T1, UNG_WIDE)});
+    const int64_t rem = n1 - u;
+    if (rem <= 0) continue;
+    const int64_t n_narrow = (rem + UNG_NT1 - 1) / UNG_NT1;
+    const bool narrow = shape == 2 || (shape == 0 && (double)n_narrow * cost_n < cost_w);
+    if (!narrow) {
+      for (; u < n1; u += UNG_T1)
+        w.push_back({cost_w, make_int4(k, (int)(first + u), (int)std::min<int64_t>(UNG_T1, n1 - u), UNG_WIDE)});
+    } else {
+      for (; u < n1; u += UNG_NT1)
+        w.push_back({cost_n, make_int4(k, (int)(first + u), (int)std::min<int64_t>(UNG_NT1, n1 - u), UNG_NARROW)});
     }
   }
   if (largest_first)
-    std::stable_sort(w.begin(), w.end(), [](const std::pair<int64_t, int4>& x, const std::pair<int64_t, int4>& y) {
+    std::stable_sort(w.begin(), w.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
       return x.first > y.first;
     });
   tl->tiles.reserve(w.size());
   for (auto& x : w) tl->tiles.push_back(x.second);
+}
+
+void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl,
+                 const std::vector<char>* key_mask = nullptr, int shape_override = -1) {
+  build_tiles_from(b1->h_key_off.data(), b2->h_key_off.data(), largest_first, tl, key_mask, shape_override);
 }
 
 // Device state shared by the stage-2 calls: sorted survivor keys and values.
@@ -157,8 +195,10 @@ struct Survivors {
   int sh = 0;  // key = padded pos1 << sh | padded pos2
 };
 
+// Stage 2 into scratch; the survivors come back in canonical (key) order
+// when `sort`, else in the order the kernel wrote them.
 int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, cudaStream_t st, Scratch& sc,
-                 Survivors* sv, const std::vector<char>* key_mask = nullptr) {
+                 Survivors* sv, const std::vector<char>* key_mask = nullptr, bool sort = true) {
   sv->n = 0;
   sv->sh = b2->pad_bits;
   TileList tl;
@@ -229,6 +269,12 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
     }
     sv->n = (int64_t)n;
     if (n == 0) return PLAST_OK;
+    if (!sort) {
+      t_timer.mark(3, st);
+      sv->key = k0;
+      sv->val = v0;
+      return PLAST_OK;
+    }
     CK(sc.get(&k1, n));
     CK(sc.get(&v1, n));
     void* tmp;
@@ -532,6 +578,63 @@ int run_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params& p
   return PLAST_OK;
 }
 
+// Stage 3.1 of a search: the survivors in any order; the passing ones are
+// gathered, sorted by key (fewer than the survivors) and written as records
+// in canonical order.
+int run_gapped_search(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, const Survivors& sv,
+                      plast_gapped* out, int64_t cap, int64_t* n_out, cudaStream_t st, Scratch& sc) {
+  *n_out = 0;
+  const int64_t n = sv.n;
+  if (n == 0) return PLAST_OK;
+  if (n > (int64_t)UINT32_MAX) return PLAST_E_CAPACITY;
+  GapArgs g;
+  g.pad1 = b1->pad;
+  g.pad2 = b2->pad;
+  g.key = sv.key;
+  g.val = sv.val;
+  g.n = n;
+  g.sh = sv.sh;
+  g.gap_open = prm.gap_open;
+  g.gap_extend = prm.gap_extend;
+  g.s2 = prm.s2;
+  int64_t *at, *total;
+  CK(sc.get(&g.score, n));
+  CK(sc.get(&g.ends, n));
+  CK(sc.get(&g.pass, n));
+  CK(sc.get(&at, n));
+  CK(sc.get(&total, 1));
+  CK(launch_small_gapped(g, st));
+  t_timer.mark(4, st);
+  void* stmp;
+  size_t stb = scan_tmp_bytes(n);
+  CK(sc.get((char**)&stmp, stb));
+  CK(scan_exclusive(g.pass, at, n, total, stmp, stb, st));
+  int64_t m = 0;
+  CK(cudaMemcpyAsync(&m, total, sizeof(m), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *n_out = m;
+  if (m > cap) return PLAST_E_CAPACITY;
+  if (m == 0) return PLAST_OK;
+  if (!out) return PLAST_E_INVALID;
+  uint64_t *rk0, *rk1;
+  uint32_t *ri0, *ri1;
+  CK(sc.get(&rk0, m));
+  CK(sc.get(&rk1, m));
+  CK(sc.get(&ri0, m));
+  CK(sc.get(&ri1, m));
+  void* rtmp;
+  size_t rtb = radix_tmp_bytes(m);
+  CK(sc.get((char**)&rtmp, rtb));
+  CK(launch_gather_pass(g, at, rk0, ri0, st));
+  bool alt = false;
+  CK(radix_sort_pairs(rk0, ri0, rk1, ri1, m, b1->pad_bits + sv.sh, rtmp, rtb, st, &alt));
+  CK(launch_write_sorted(g, alt ? rk1 : rk0, alt ? ri1 : ri0, m, nullptr, b1->pad_off, b1->n_seqs, b2->pad_off,
+                         b2->n_seqs, out, st));
+  t_timer.mark(5, st);
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
+}
+
 }  // namespace
 
 int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const plast_hit* in,
@@ -583,10 +686,10 @@ static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_p
   t_timer.reset();
   Scratch sc(st);
   Survivors sv;
-  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, keys ? &mask : nullptr);
+  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, keys ? &mask : nullptr, false);
   if (rc) return rc;
   if (n_ungapped_out) *n_ungapped_out = sv.n;
-  return run_gapped(b1, b2, prm, sv.key, sv.val, sv.n, sv.sh, out, cap, n_out, st, sc);
+  return run_gapped_search(b1, b2, prm, sv, out, cap, n_out, st, sc);
 }
 
 int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
@@ -666,13 +769,15 @@ struct plast_plan {
   int device = 0;
   int64_t max_hits = 0, max_records = 0, n_tiles = 0;
   int sh = 0, bits = 0;
-  bool alt = false;
   int4* tiles = nullptr;
   int32_t* counter = nullptr;
   unsigned long long* count = nullptr;
-  int64_t* n_dev = nullptr;
-  uint64_t *k0 = nullptr, *k1 = nullptr;
-  uint32_t *v0 = nullptr, *v1 = nullptr;
+  int64_t* n_dev = nullptr;   // survivors, clamped to max_hits
+  int64_t* m_dev = nullptr;   // records, clamped to max_records
+  uint64_t* k0 = nullptr;     // survivors (kernel order)
+  uint32_t* v0 = nullptr;
+  uint64_t *rk0 = nullptr, *rk1 = nullptr;  // record keys and hit indexes, sorted
+  uint32_t *ri0 = nullptr, *ri1 = nullptr;
   void* rtmp = nullptr;
   size_t rtb = 0;
   int32_t* score = nullptr;
@@ -693,9 +798,9 @@ void plast_plan_free(plast_plan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  for (void* q : {(void*)p->tiles, (void*)p->counter, (void*)p->count, (void*)p->n_dev, (void*)p->k0, (void*)p->k1,
-                  (void*)p->v0, (void*)p->v1, p->rtmp, (void*)p->score, (void*)p->ends, (void*)p->pass,
-                  (void*)p->at, (void*)p->total, p->stmp})
+  for (void* q : {(void*)p->tiles, (void*)p->counter, (void*)p->count, (void*)p->n_dev, (void*)p->m_dev,
+                  (void*)p->k0, (void*)p->v0, (void*)p->rk0, (void*)p->rk1, (void*)p->ri0, (void*)p->ri1, p->rtmp,
+                  (void*)p->score, (void*)p->ends, (void*)p->pass, (void*)p->at, (void*)p->total, p->stmp})
     if (q) cudaFree(q);
   delete p;
 }
@@ -704,7 +809,8 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
                       plast_gapped* records, int64_t max_records, void* stream, plast_plan** out) {
   if (!b1 || !b2 || !out || !records || max_hits < 1 || max_records < 1 || !params_ok(params))
     return PLAST_E_INVALID;
-  if (max_hits > ((int64_t)1 << 34) || max_records > ((int64_t)1 << 34)) return PLAST_E_INVALID;
+  if (max_hits > (int64_t)UINT32_MAX) return PLAST_E_INVALID;
+  max_records = std::min(max_records, max_hits);  // a search never has more records than hits
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   CK(upload_tables_once());
@@ -719,7 +825,6 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   p->out = records;
   p->sh = b2->pad_bits;
   p->bits = b1->pad_bits + p->sh;
-  p->alt = ((p->bits + 7) / 8) % 2 == 1;
   auto fail = [&](cudaError_t e) {
     plast_plan_free(p);
     return rc_of(e);
@@ -729,13 +834,15 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   p->n_tiles = (int64_t)tl.tiles.size();
   cudaError_t e;
   auto alloc = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes < 16 ? 16 : bytes); };
-  p->rtb = radix_tmp_bytes(max_hits);
+  p->rtb = radix_tmp_bytes(max_records);
   p->stb = scan_tmp_bytes(max_hits);
   if ((e = alloc((void**)&p->tiles, sizeof(int4) * (size_t)std::max<int64_t>(p->n_tiles, 1))) ||
       (e = alloc((void**)&p->counter, sizeof(int32_t))) || (e = alloc((void**)&p->count, sizeof(unsigned long long))) ||
-      (e = alloc((void**)&p->n_dev, sizeof(int64_t))) || (e = alloc((void**)&p->k0, 8 * (size_t)max_hits)) ||
-      (e = alloc((void**)&p->k1, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->v0, 4 * (size_t)max_hits)) ||
-      (e = alloc((void**)&p->v1, 4 * (size_t)max_hits)) || (e = alloc(&p->rtmp, p->rtb)) ||
+      (e = alloc((void**)&p->n_dev, sizeof(int64_t))) || (e = alloc((void**)&p->m_dev, sizeof(int64_t))) ||
+      (e = alloc((void**)&p->k0, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->v0, 4 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->rk0, 8 * (size_t)max_records)) || (e = alloc((void**)&p->rk1, 8 * (size_t)max_records)) ||
+      (e = alloc((void**)&p->ri0, 4 * (size_t)max_records)) || (e = alloc((void**)&p->ri1, 4 * (size_t)max_records)) ||
+      (e = alloc(&p->rtmp, p->rtb)) ||
       (e = alloc((void**)&p->score, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->ends, 4 * (size_t)max_hits)) ||
       (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->at, 8 * (size_t)max_hits)) ||
       (e = alloc((void**)&p->total, sizeof(int64_t))) || (e = alloc(&p->stmp, p->stb)))
@@ -780,13 +887,11 @@ int plast_plan_run(plast_plan* p, void* stream) {
     CK(launch_ungapped(a, (int)std::min<int64_t>(num_sms(), p->n_tiles), st));
   }
   CK(launch_clamp_count(p->count, p->max_hits, p->n_dev, st));
-  bool alt = false;
-  CK(radix_sort_pairs(p->k0, p->v0, p->k1, p->v1, p->max_hits, p->bits, p->rtmp, p->rtb, st, &alt, p->n_dev));
   GapArgs g;
   g.pad1 = p->b1->pad;
   g.pad2 = p->b2->pad;
-  g.key = alt ? p->k1 : p->k0;
-  g.val = alt ? p->v1 : p->v0;
+  g.key = p->k0;
+  g.val = p->v0;
   g.n = p->max_hits;
   g.sh = p->sh;
   g.gap_open = p->prm.gap_open;
@@ -799,7 +904,12 @@ int plast_plan_run(plast_plan* p, void* stream) {
   g.out_cap = p->max_records;
   CK(launch_small_gapped(g, st));
   CK(scan_exclusive(g.pass, p->at, p->max_hits, p->total, p->stmp, p->stb, st, p->n_dev));
-  CK(launch_gapped_compact(g, p->at, p->b1->pad_off, p->b1->n_seqs, p->b2->pad_off, p->b2->n_seqs, p->out, st));
+  CK(launch_clamp_total(p->total, p->max_records, p->m_dev, st));
+  CK(launch_gather_pass(g, p->at, p->rk0, p->ri0, st));
+  bool alt = false;
+  CK(radix_sort_pairs(p->rk0, p->ri0, p->rk1, p->ri1, p->max_records, p->bits, p->rtmp, p->rtb, st, &alt, p->m_dev));
+  CK(launch_write_sorted(g, alt ? p->rk1 : p->rk0, alt ? p->ri1 : p->ri0, p->max_records, p->m_dev, p->b1->pad_off,
+                         p->b1->n_seqs, p->b2->pad_off, p->b2->n_seqs, p->out, st));
   return PLAST_OK;
 }
 
@@ -849,6 +959,207 @@ int plast_plan_result(const plast_plan* p, int64_t* n_records, int64_t* n_hits, 
   }
   *n_records = recs;
   return recs > p->max_records ? PLAST_E_CAPACITY : PLAST_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tile-cost calibration: the stage-2 kernel timed on random banks with every
+// tile wide, then every tile narrow, against a long and a short bank 2; a
+// two-point fit per shape gives the cost per row slot x window and per tile.
+// ---------------------------------------------------------------------------
+namespace {
+
+uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// n_seqs random proteins of `len` residues (codes 0..19 uniform), indexed
+int random_bank(int32_t n_seqs, int len, uint64_t seed, cudaStream_t st, plast_bank** out) {
+  std::vector<int8_t> codes((size_t)n_seqs * len);
+  std::vector<int64_t> off((size_t)n_seqs + 1);
+  uint64_t x = seed;
+  for (auto& c : codes) c = (int8_t)(splitmix(x) % 20);
+  for (int32_t i = 0; i <= n_seqs; i++) off[i] = (int64_t)i * len;
+  int8_t* d_codes = nullptr;
+  int64_t* d_off = nullptr;
+  CK(cudaMalloc(&d_codes, codes.size()));
+  cudaError_t e = cudaMalloc(&d_off, off.size() * sizeof(int64_t));
+  int rc = PLAST_OK;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_codes, codes.data(), codes.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) rc = plast_index_bank(d_codes, d_off, n_seqs, nullptr, st, out);
+  else rc = rc_of(e);
+  cudaStreamSynchronize(st);
+  cudaFree(d_codes);
+  if (d_off) cudaFree(d_off);
+  return rc;
+}
+
+// median device time (ms) of the stage-2 kernel over `reps` runs of the
+// given shape; *slots = sum over tiles of the charged slots, *tiles = count
+int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStream_t st, int reps, double* ms,
+                double* slots, double* tiles) {
+  TileList tl;
+  build_tiles(b1, b2, true, &tl, nullptr, shape);
+  *slots = 0;
+  for (const int4& t : tl.tiles) {
+    const int64_t n2 = b2->h_key_off[t.x + 1] - b2->h_key_off[t.x];
+    *slots += t.w == UNG_WIDE ? (double)UNG_T1 * (double)round_up(n2, WIDE_PASS)
+                              : (double)UNG_NT1 * (double)round_up(n2, NARROW_PASS);
+  }
+  *tiles = (double)tl.tiles.size();
+  *ms = 0;
+  if (tl.tiles.empty()) return PLAST_OK;
+  Scratch sc(st);
+  int4* d_tiles;
+  int32_t* d_counter;
+  unsigned long long* d_count;
+  uint64_t* k0;
+  uint32_t* v0;
+  const int64_t cap = tl.pairs / 64 + (1 << 16);
+  CK(sc.get(&d_tiles, tl.tiles.size()));
+  CK(sc.get(&d_counter, 1));
+  CK(sc.get(&d_count, 1));
+  CK(sc.get(&k0, cap));
+  CK(sc.get(&v0, cap));
+  CK(cudaMemcpyAsync(d_tiles, tl.tiles.data(), tl.tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  UngArgs a;
+  a.nb1 = b1->nb;
+  a.pos1 = b1->pos;
+  a.nb2 = b2->nb;
+  a.pos2 = b2->pos;
+  a.key_off2 = b2->key_off;
+  a.tiles = d_tiles;
+  a.n_tiles = (int32_t)tl.tiles.size();
+  a.tile_base = 0;
+  a.tile_counter = d_counter;
+  a.persistent = 1;
+  plast_params dp;
+  plast_default_params(&dp);
+  a.s1 = dp.s1;
+  a.out_key = k0;
+  a.out_val = v0;
+  a.out_count = d_count;
+  a.cap = cap;
+  a.sh = b2->pad_bits;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PLAST_E_CUDA;
+  }
+  std::vector<float> t;
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r <= reps && e == cudaSuccess; r++) {
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_ungapped(a, (int)std::min<int64_t>(num_sms(), tl.tiles.size()), st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float x = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, e0, e1);
+    if (r > 0) t.push_back(x);  // run 0 warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return rc_of(e);
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return PLAST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int plast_get_tile_costs(plast_tile_costs* out) {
+  if (!out) return PLAST_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_cost_mu);
+  *out = g_costs;
+  return PLAST_OK;
+}
+
+int plast_set_tile_costs(const plast_tile_costs* c) {
+  if (!c || !(c->wide_slot > 0) || !(c->narrow_slot > 0) || !(c->wide_tile >= 0) || !(c->narrow_tile >= 0) ||
+      c->wide_slot > 1e6 || c->narrow_slot > 1e6 || c->wide_tile > 1e12 || c->narrow_tile > 1e12)
+    return PLAST_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_cost_mu);
+  g_costs = *c;
+  return PLAST_OK;
+}
+
+int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t* tiles, int64_t cap,
+                       int64_t* n_tiles) {
+  if (!key_off1 || !key_off2 || !n_tiles || cap < 0 || (cap > 0 && !tiles)) return PLAST_E_INVALID;
+  for (int k = 0; k < NKEYS; k++)
+    if (key_off1[k + 1] < key_off1[k] || key_off2[k + 1] < key_off2[k] || key_off1[k + 1] > INT32_MAX)
+      return PLAST_E_INVALID;
+  TileList tl;
+  build_tiles_from(key_off1, key_off2, g_schedule.load() == 0, &tl, nullptr, -1);
+  *n_tiles = (int64_t)tl.tiles.size();
+  if (*n_tiles > cap) return PLAST_E_CAPACITY;
+  for (size_t i = 0; i < tl.tiles.size(); i++) {
+    tiles[4 * i] = tl.tiles[i].x;
+    tiles[4 * i + 1] = tl.tiles[i].y;
+    tiles[4 * i + 2] = tl.tiles[i].z;
+    tiles[4 * i + 3] = tl.tiles[i].w;
+  }
+  return PLAST_OK;
+}
+
+int plast_set_tile_shape(int mode) {
+  if (mode < 0 || mode > 2) return PLAST_E_INVALID;
+  g_shape.store(mode);
+  return PLAST_OK;
+}
+
+int plast_autotune(void* stream, plast_tile_costs* out) {
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(upload_tables_once());
+  plast_bank *b1 = nullptr, *b2l = nullptr, *b2s = nullptr;
+  // bank 1: ~10 occurrences per key; bank 2: ~4,100 (four narrow passes)
+  // and ~300 (two wide passes, a fraction of a narrow one) per key
+  int rc = random_bank(300, 300, 11, st, &b1);
+  if (rc == PLAST_OK) rc = random_bank(120000, 300, 12, st, &b2l);
+  if (rc == PLAST_OK) rc = random_bank(9000, 300, 13, st, &b2s);
+  plast_tile_costs c;
+  plast_get_tile_costs(&c);
+  const double sms = (double)num_sms();
+  for (int shape = 1; shape <= 2 && rc == PLAST_OK; shape++) {
+    double t_l, s_l, n_l, t_s, s_s, n_s;
+    rc = time_stage2(b1, b2l, shape, st, 3, &t_l, &s_l, &n_l);
+    if (rc == PLAST_OK) rc = time_stage2(b1, b2s, shape, st, 3, &t_s, &s_s, &n_s);
+    if (rc != PLAST_OK) break;
+    // SM-nanoseconds = slot cost x slots + tile cost x tiles, for both banks
+    const double y_l = t_l * 1e6 * sms, y_s = t_s * 1e6 * sms;
+    const double det = s_l * n_s - s_s * n_l;
+    double slot = det != 0 ? (y_l * n_s - y_s * n_l) / det : 0;
+    double tile = det != 0 ? (s_l * y_s - s_s * y_l) / det : 0;
+    if (!(slot > 0) || !(tile >= 0)) {
+      slot = y_l / std::max(s_l, 1.0);
+      tile = 0;
+    }
+    if (shape == 1) {
+      c.wide_slot = slot;
+      c.wide_tile = tile;
+    } else {
+      c.narrow_slot = slot;
+      c.narrow_tile = tile;
+    }
+  }
+  plast_bank_free(b1);
+  plast_bank_free(b2l);
+  plast_bank_free(b2s);
+  if (rc != PLAST_OK) return rc;
+  rc = plast_set_tile_costs(&c);
+  if (rc == PLAST_OK && out) *out = c;
+  return rc;
 }
 
 }  // extern "C"

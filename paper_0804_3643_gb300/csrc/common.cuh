@@ -39,7 +39,8 @@ constexpr int BW = 2 * BAND + 1;
 constexpr int GAP = 80;
 
 // Launch geometry of the stage-2 kernel.
-constexpr int UNG_T1 = 128;        // bank-1 rows per profile tile
+constexpr int UNG_T1 = 128;        // bank-1 rows per wide profile tile
+constexpr int UNG_NT1 = 8;         // bank-1 rows per narrow profile tile
 constexpr int UNG_THREADS = 1024;  // 32 warps, one CTA per SM
 
 // BLOSUM62, upper triangle by rows, order A R N D C Q E G H I L K M F P S T W Y V

@@ -22,6 +22,13 @@
 // single instruction per cell.  Values are exact in int16 (|H| <= 64 * 11 on
 // the grid; cells off the grid stay above -16000 - 64 * 12).
 //
+// The A residues of a side reach the thread four rows at a time: aligned
+// 32-bit loads of pad1 (byte-reversed for the left side) funnel-shifted into
+// place, one word per hit per four rows, fetched a group ahead; each row
+// takes its byte with one prmt.  (Byte loads, one per row, cost a memory
+// transaction per lane when the hits of a warp are scattered over bank 1, as
+// they are in the order stage 2 writes them.)
+//
 // The end cell (first maximum in row-major order): after each row the row
 // maximum is compared with the best so far per half; the halves that improve
 // copy the row's H values into a best-row array (LOP3 masks) and record the
@@ -134,6 +141,30 @@ __device__ __forceinline__ uint32_t stage_b(const int8_t* pad2, int64_t p2, int 
   return dst_s;
 }
 
+// Consecutive bytes of pad1 from address `start`, forwards (dir 0) or
+// backwards (dir 1), delivered four per call in reading order (byte 0 first).
+struct ByteRun {
+  const uint32_t* src;
+  uint32_t prev, sel, sh;
+  int dir, k;
+  __device__ __forceinline__ void init(const int8_t* base, int64_t start, int d) {
+    dir = d;
+    const int64_t first = start & ~(int64_t)3;
+    sel = d ? 0x0123u : 0x3210u;
+    sh = 8u * (d ? (uint32_t)(3 - (start & 3)) : (uint32_t)(start & 3));
+    src = reinterpret_cast<const uint32_t*>(base + first);
+    prev = __byte_perm(__ldg(src), 0u, sel);
+    k = 1;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    const uint32_t nxt = __byte_perm(__ldg(src + (dir ? -k : k)), 0u, sel);
+    const uint32_t out = __funnelshift_r(prev, nxt, sh);
+    prev = nxt;
+    k++;
+    return out;
+  }
+};
+
 __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   extern __shared__ __align__(16) unsigned char gsm[];
   uint32_t* tab32 = reinterpret_cast<uint32_t*>(gsm);
@@ -166,9 +197,6 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
       const int64_t p11 = (int64_t)(k1 >> a.sh), p21 = (int64_t)(k1 & mask);
       // residue i (1-based): right A_i = pad1[p1 + i - 1], B_j = pad2[p2 + j - 1];
       // left A_i = pad1[p1 - i], B_j = pad2[p2 - j].
-      const int step = side ? -1 : 1;
-      const int8_t* A0 = a.pad1 + p10 - side;
-      const int8_t* A1 = a.pad1 + p11 - side;
       // B_-8 .. B_74 of each hit in reading order: aligned words of pad2,
       // taken backwards and byte-reversed for the left side; sbX points at B_-8
       const uint32_t sb0 = stage_b(a.pad2, p20, side, reinterpret_cast<uint32_t*>(seg), seg_s);
@@ -183,25 +211,45 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
       }
       B.best = 0;
       B.bi = 0;
-      // A_i of both hits, fetched one row ahead
-      uint32_t a0 = (uint8_t)A0[0], a1 = (uint8_t)A1[0];
-#define PLAST_ROW(JLIM)                                                                                 \
+      // A_i of both hits, four rows per word (byte r = row 4g + 1 + r),
+      // fetched a group ahead; right: A_i = pad1[p1 + i - 1] forwards from
+      // p1, left: A_i = pad1[p1 - i] backwards from p1 - 1
+      ByteRun ra0, ra1;
+      ra0.init(a.pad1, p10 - side, side);
+      ra1.init(a.pad1, p11 - side, side);
+      uint32_t aw0 = ra0.next(), aw1 = ra1.next();
+#define PLAST_ROW(I, R, JLIM)                                                                          \
   {                                                                                                    \
-    const unsigned char* r0 = tlane + a0 * 128u;                                                       \
-    const unsigned char* r1 = tlane + a1 * 128u;                                                       \
-    a0 = (uint8_t)A0[i * step];                                                                        \
-    a1 = (uint8_t)A1[i * step];                                                                        \
-    gapped_row<JLIM>(B, i, r0, r1, sb0, sb1, nge2, goe2);                                             \
+    const unsigned char* r0 = tlane + __byte_perm(c0, 0u, 0x4440u + (R)) * 128u;                       \
+    const unsigned char* r1 = tlane + __byte_perm(c1, 0u, 0x4440u + (R)) * 128u;                       \
+    gapped_row<JLIM>(B, (I), r0, r1, sb0, sb1, nge2, goe2);                                            \
   }
-      for (int i = 1; i <= LG - BAND; i++) PLAST_ROW(BW - 1)
-      { int i = LG - BAND + 1; PLAST_ROW(15) }
-      { int i = LG - BAND + 2; PLAST_ROW(14) }
-      { int i = LG - BAND + 3; PLAST_ROW(13) }
-      { int i = LG - BAND + 4; PLAST_ROW(12) }
-      { int i = LG - BAND + 5; PLAST_ROW(11) }
-      { int i = LG - BAND + 6; PLAST_ROW(10) }
-      { int i = LG - BAND + 7; PLAST_ROW(9) }
-      { int i = LG - BAND + 8; PLAST_ROW(8) }
+      for (int g = 0; g < (LG - BAND) / 4; g++) {  // rows 1 .. 56: the whole band on the grid
+        const uint32_t c0 = aw0, c1 = aw1;
+        aw0 = ra0.next();
+        aw1 = ra1.next();
+        const int i = 4 * g + 1;
+        PLAST_ROW(i, 0, BW - 1)
+        PLAST_ROW(i + 1, 1, BW - 1)
+        PLAST_ROW(i + 2, 2, BW - 1)
+        PLAST_ROW(i + 3, 3, BW - 1)
+      }
+      {  // rows 57 .. 60
+        const uint32_t c0 = aw0, c1 = aw1;
+        aw0 = ra0.next();
+        aw1 = ra1.next();
+        PLAST_ROW(LG - BAND + 1, 0, 15)
+        PLAST_ROW(LG - BAND + 2, 1, 14)
+        PLAST_ROW(LG - BAND + 3, 2, 13)
+        PLAST_ROW(LG - BAND + 4, 3, 12)
+      }
+      {  // rows 61 .. 64
+        const uint32_t c0 = aw0, c1 = aw1;
+        PLAST_ROW(LG - BAND + 5, 0, 11)
+        PLAST_ROW(LG - BAND + 6, 1, 10)
+        PLAST_ROW(LG - BAND + 7, 2, 9)
+        PLAST_ROW(LG - BAND + 8, 3, 8)
+      }
 #undef PLAST_ROW
     } else {
       B.best = 0;
@@ -265,28 +313,54 @@ __device__ __forceinline__ int32_t find_seq_g(const int64_t* off, int32_t n, int
   return lo;
 }
 
+__device__ __forceinline__ plast_gapped make_record(const GapArgs& a, int64_t h, uint64_t key,
+                                                    const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
+                                                    int32_t n2) {
+  const int64_t p1 = (int64_t)(key >> a.sh), p2 = (int64_t)(key & ((1ull << a.sh) - 1));
+  const int32_t q1 = find_seq_g(pad_off1, n1, p1), q2 = find_seq_g(pad_off2, n2, p2);
+  const uint32_t e = a.ends[h];
+  plast_gapped r;
+  r.seq1 = q1;
+  r.pos1 = (int32_t)(p1 - pad_off1[q1]);
+  r.seq2 = q2;
+  r.pos2 = (int32_t)(p2 - pad_off2[q2]);
+  r.score = (int16_t)a.score[h];
+  r.ungapped = (int16_t)(a.val[h] & 0xffffu);
+  r.r_i = (int16_t)(e & 0xff);
+  r.r_j = (int16_t)((e >> 8) & 0xff);
+  r.l_i = (int16_t)((e >> 16) & 0xff);
+  r.l_j = (int16_t)((e >> 24) & 0xff);
+  return r;
+}
+
 __global__ void k_gapped_compact(GapArgs a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
                                  const int64_t* pad_off2, int32_t n2, plast_gapped* out) {
   const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
     if (!a.pass[h] || at[h] >= a.out_cap) continue;
-    const uint64_t key = a.key[h];
-    const int64_t p1 = (int64_t)(key >> a.sh), p2 = (int64_t)(key & ((1ull << a.sh) - 1));
-    const int32_t q1 = find_seq_g(pad_off1, n1, p1), q2 = find_seq_g(pad_off2, n2, p2);
-    const uint32_t e = a.ends[h];
-    plast_gapped r;
-    r.seq1 = q1;
-    r.pos1 = (int32_t)(p1 - pad_off1[q1]);
-    r.seq2 = q2;
-    r.pos2 = (int32_t)(p2 - pad_off2[q2]);
-    r.score = (int16_t)a.score[h];
-    r.ungapped = (int16_t)(a.val[h] & 0xffffu);
-    r.r_i = (int16_t)(e & 0xff);
-    r.r_j = (int16_t)((e >> 8) & 0xff);
-    r.l_i = (int16_t)((e >> 16) & 0xff);
-    r.l_j = (int16_t)((e >> 24) & 0xff);
-    out[at[h]] = r;
+    out[at[h]] = make_record(a, h, a.key[h], pad_off1, n1, pad_off2, n2);
   }
+}
+
+// Passing hits h (record slot at[h] below out_cap): rkey[at[h]] = key[h],
+// ridx[at[h]] = h, for the record sort.
+__global__ void k_gather_pass(GapArgs a, const int64_t* at, uint64_t* rkey, uint32_t* ridx) {
+  const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
+    if (!a.pass[h] || at[h] >= a.out_cap) continue;
+    rkey[at[h]] = a.key[h];
+    ridx[at[h]] = (uint32_t)h;
+  }
+}
+
+// Records in key order: out[r] from hit sidx[r] (key skey[r]), r < m (or
+// < *m_dev, at most m).
+__global__ void k_write_sorted(GapArgs a, const uint64_t* skey, const uint32_t* sidx, int64_t m, const int64_t* m_dev,
+                               const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2, int32_t n2,
+                               plast_gapped* out) {
+  if (m_dev) m = min(m, max(*m_dev, (int64_t)0));
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
+    out[r] = make_record(a, sidx[r], skey[r], pad_off1, n1, pad_off2, n2);
 }
 
 cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
@@ -307,6 +381,37 @@ __global__ void k_clamp_count(const unsigned long long* count, int64_t cap, int6
 cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st) {
   note_launch();
   k_clamp_count<<<1, 1, 0, st>>>(count, cap, n_dev);
+  return cudaGetLastError();
+}
+
+__global__ void k_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev) {
+  const int64_t c = *total;
+  *n_dev = c > cap ? cap : (c < 0 ? 0 : c);
+}
+
+cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev, cudaStream_t st) {
+  note_launch();
+  k_clamp_total<<<1, 1, 0, st>>>(total, cap, n_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pass(const GapArgs& a, const int64_t* at, uint64_t* rkey, uint32_t* ridx, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  int64_t b = (a.n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  note_launch();
+  k_gather_pass<<<(unsigned)b, 256, 0, st>>>(a, at, rkey, ridx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_sorted(const GapArgs& a, const uint64_t* skey, const uint32_t* sidx, int64_t m,
+                                const int64_t* m_dev, const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
+                                int32_t n2, plast_gapped* out, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  int64_t b = (m + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  note_launch();
+  k_write_sorted<<<(unsigned)b, 256, 0, st>>>(a, skey, sidx, m, m_dev, pad_off1, n1, pad_off2, n2, out);
   return cudaGetLastError();
 }
 

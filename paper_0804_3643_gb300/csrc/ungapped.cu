@@ -1,29 +1,39 @@
 // ungapped.cu -- stage 2 (Section 3.3.3, the loop of Annex 4) on sm_103a.
 //
-// Work unit: a TILE = (key, up to 128 consecutive bank-1 occurrences of that
-// key).  A CTA builds, in shared memory, the score profile of its bank-1
-// windows: prof[k][b][r] = score(nb1[r][k], b) for cell k < 48, residue code
-// b < 22 and row r < 128, one signed byte each, rows of one (k, b) 144 bytes
-// apart (128 used).  It then streams every bank-2 occurrence of the key
-// through the profile.  Lane (g, js) of a warp scores bank-2 row js (4 per
-// warp, staged in the warp's shared buffer) against bank-1 rows
-// 16g .. 16g+15.  Per cell: one byte load fetches the bank-2 residue, one
-// IMAD forms the profile address, one 16-byte load fetches the 16 row scores,
-// prmt sign-extends them into eight int16x2 words, and per pair of cells two
-// __vadd2 and one __vimax3_s16x2 update each word's running sums and maxima
-// (exact: |sum| <= 48 * 32 < 2^15).  After cell 25 the sums restart from the
-// maxima (the reset of Annex 4).
+// Work unit: a TILE = (key, consecutive bank-1 occurrences of that key, shape).
+// A CTA builds, in shared memory, the score profile of its bank-1 windows:
+// prof[k][b][r] = score(nb1[r][k], b) for cell k < 48, residue code b < 22 and
+// tile row r, one signed byte each.  It then streams every bank-2 occurrence
+// of the key through the profile.  Per cell a lane loads the bank-2 residue
+// (one byte), forms the profile address (one IMAD) and loads its rows' scores
+// (one vector load); prmt sign-extends them into int16x2 words, and per pair
+// of cells two __vadd2 and one __vimax3_s16x2 update each word's running sums
+// and maxima (exact: |sum| <= 48 * 32 < 2^15).  After cell 25 the sums restart
+// from the maxima (the reset of Annex 4).
 //
-// Pipe balance on sm_103: byte loads and 16-byte loads go to the LSU, IMAD and
+// Two tile shapes share the kernel:
+//  * wide: up to 128 rows, profile rows of one (k, b) 144 bytes apart.  Lane
+//    (g, js) of a warp scores bank-2 window js (4 per warp) against rows
+//    16g .. 16g+15 with one 16-byte load per cell; the 8 lanes of a window
+//    read one 128-byte profile row, so a warp's 512 bytes come out of shared
+//    memory in the minimum 4 wavefronts.
+//  * narrow: up to 8 rows, the profile in two planes of 4 rows, one 32-bit
+//    word per (k, b).  Every lane scores its own bank-2 window (32 per warp)
+//    against the 8 rows with two word loads per cell; the 22 words of a cell
+//    lie in 22 distinct banks, so 32 lanes with any residues read them in one
+//    wavefront.  It serves keys with few bank-1 occurrences (a small query
+//    bank against a large one, the remainder of a long list), where a wide
+//    tile would mostly score padding rows.
+// The host picks the shape per key from measured per-cell and per-tile costs.
+//
+// Pipe balance on sm_103: byte and vector loads go to the LSU, IMAD and
 // __vadd2 to the FMA pipe, prmt and the 3-input maxima to the ALU pipe, which
-// issues at half the FMA rate and is the bound.  The 8 lanes sharing a bank-2
-// row read one 128-byte profile row, so a warp's 512 bytes come out of shared
-// memory in the minimum 4 wavefronts; each byte read serves one pair-cell.
+// is the bound.
 //
 // Hits (score >= s1) are staged in a per-warp shared buffer and flushed with
 // one global atomic per 64 records, as (padded pos1 << sh | padded pos2,
-// score).  Tiles come from a device counter (persistent launch, largest tile
-// first) or, in the plain schedule, one launch per key.
+// score).  Tiles come from a device counter (persistent launch, costliest
+// tile first) or, in the plain schedule, one launch per key.
 #include "common.cuh"
 #include "ungapped.cuh"
 
@@ -40,6 +50,15 @@ constexpr int WKEY_BYTES = NWARPS * WBUF * 8;              // 16384
 constexpr int WVAL_BYTES = NWARPS * WBUF * 4;              // 8192
 constexpr int UNG_SMEM = PROF_BYTES + TAB_BYTES + ROWS_BYTES + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 16;
 constexpr int ROWS_PER_LANE = UNG_T1 / 8;                  // 16
+
+// narrow tiles overlay the wide profile
+constexpr int NSTRIDE = 52;                                // staged window stride: 13 words, conflict-free bytes
+constexpr int NPLANE = WIN * NCODE * 4;                     // 4224: one plane of 4 rows
+constexpr int NPROF_BYTES = 2 * NPLANE;                     // 8448
+constexpr int NROWS_BYTES = WIN * UNG_NT1;                 // 384, cell-major
+constexpr int NSTAGE_BYTES = NWARPS * 32 * NSTRIDE;        // 53248: one window per lane
+static_assert(NPROF_BYTES + NROWS_BYTES + NSTAGE_BYTES <= PROF_BYTES, "narrow tile fits the wide profile area");
+static_assert(NPROF_BYTES % 16 == 0 && NROWS_BYTES % 16 == 0 && (32 * NSTRIDE) % 16 == 0, "alignment");
 
 size_t ungapped_smem_bytes() { return (size_t)UNG_SMEM; }
 
@@ -62,6 +81,13 @@ __device__ __forceinline__ void unpack16(const uint4& p, uint32_t (&u)[8]) {
   u[7] = sext_pair(p.w, 1);
 }
 
+__device__ __forceinline__ void unpack8(uint32_t lo, uint32_t hi, uint32_t (&u)[4]) {
+  u[0] = sext_pair(lo, 0);
+  u[1] = sext_pair(lo, 1);
+  u[2] = sext_pair(hi, 0);
+  u[3] = sext_pair(hi, 1);
+}
+
 __device__ __forceinline__ void flush_warp(const uint64_t* wk, const uint32_t* wv, int n, int lane,
                                            unsigned long long* out_count, uint64_t* out_key, uint32_t* out_val,
                                            int64_t cap) {
@@ -77,28 +103,108 @@ __device__ __forceinline__ void flush_warp(const uint64_t* wk, const uint32_t* w
   }
 }
 
-// Cells K and K+1 of one bank-2 window against this lane's 16 bank-1 rows,
+// Cells K and K+1 of one bank-2 window against this lane's 2 * NW bank-1 rows,
 // then the following pairs (compile-time recursion over K = 0, 2, .., 46).
-template <int K>
-__device__ __forceinline__ void cell_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[8],
-                                           uint32_t (&m)[8]) {
+// Wide (NW = 8): the lane's 16 row scores for (k, b) are the 16 bytes at
+// plane + (k * NCODE + b) * STRIDE.  Narrow (NW = 4): rows 0-3 are the word at
+// plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE bytes further.
+template <int K, int NW, int STRIDE>
+__device__ __forceinline__ void cell_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[NW],
+                                           uint32_t (&m)[NW]) {
   if constexpr (K < WIN) {
     const uint32_t b0 = lds_u8<K>(row), b1 = lds_u8<K + 1>(row);
-    uint32_t u0[8], u1[8];
-    unpack16(*reinterpret_cast<const uint4*>(plane + (K * NCODE + b0) * PROF_STRIDE), u0);
-    unpack16(*reinterpret_cast<const uint4*>(plane + ((K + 1) * NCODE + b1) * PROF_STRIDE), u1);
+    uint32_t u0[NW], u1[NW];
+    if constexpr (NW == 8) {
+      unpack16(*reinterpret_cast<const uint4*>(plane + (K * NCODE + b0) * STRIDE), u0);
+      unpack16(*reinterpret_cast<const uint4*>(plane + ((K + 1) * NCODE + b1) * STRIDE), u1);
+    } else {
+      const unsigned char* e0 = plane + (K * NCODE + b0) * 4;
+      const unsigned char* e1 = plane + ((K + 1) * NCODE + b1) * 4;
+      unpack8(*reinterpret_cast<const uint32_t*>(e0), *reinterpret_cast<const uint32_t*>(e0 + NPLANE), u0);
+      unpack8(*reinterpret_cast<const uint32_t*>(e1), *reinterpret_cast<const uint32_t*>(e1 + NPLANE), u1);
+    }
 #pragma unroll
-    for (int w = 0; w < 8; w++) {
+    for (int w = 0; w < NW; w++) {
       const uint32_t t0 = __vadd2(s[w], u0[w]);
       s[w] = __vadd2(t0, u1[w]);
       m[w] = __vimax3_s16x2(m[w], t0, s[w]);
     }
     if constexpr (K + 1 == RIGHT - 1) {  // the reset of Annex 4
 #pragma unroll
-      for (int w = 0; w < 8; w++) s[w] = m[w];
+      for (int w = 0; w < NW; w++) s[w] = m[w];
     }
-    cell_pairs<K + 2>(row, plane, s, m);
+    cell_pairs<K + 2, NW, STRIDE>(row, plane, s, m);
   }
+}
+
+// Records the rows of this lane whose score reaches s1 against bank-2
+// occurrence v: rows r0 + i for i < 2 * NW (row 2w in the low half of m[w],
+// row 2w + 1 in the high half), of which the first valid_rows exist.
+template <int NW>
+__device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int valid_rows, int64_t r0, int64_t v,
+                                          const UngArgs& a, uint32_t s1x2, int lane, uint64_t* my_wk,
+                                          uint32_t* my_wv, int& wcnt) {
+  uint32_t mx = __vimax3_s16x2(m[0], m[1], m[2]);
+  if constexpr (NW == 8) {
+    mx = __vimax3_s16x2(mx, m[3], m[4]);
+    mx = __vimax3_s16x2(mx, m[5], m[6]);
+    mx = __vmaxs2(mx, m[7]);
+  } else {
+    mx = __vmaxs2(mx, m[3]);
+  }
+  const bool maybe = vok && __vcmpges2(mx, s1x2) != 0u;
+  if (!__any_sync(0xffffffffu, maybe)) return;
+  unsigned mask = 0;
+  if (maybe) {
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+      const uint32_t c = __vcmpges2(m[w], s1x2);
+      mask |= ((c & 1u) | ((c >> 15) & 2u)) << (2 * w);
+    }
+    if (valid_rows < 2 * NW) mask &= valid_rows <= 0 ? 0u : ((1u << valid_rows) - 1u);
+  }
+  const int cnt = __popc(mask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (wcnt + total > WBUF) {
+    __syncwarp();
+    flush_warp(my_wk, my_wv, wcnt, lane, a.out_count, a.out_key, a.out_val, a.cap);
+    __syncwarp();
+    wcnt = 0;
+  }
+  const uint64_t p2 = vok ? (uint64_t)a.pos2[v] : 0;
+  if (total > WBUF) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.out_count, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 0) + (incl - cnt);
+#pragma unroll
+    for (int i = 0; i < 2 * NW; i++)
+      if (mask & (1u << i)) {
+        const uint64_t p1 = a.pos1[r0 + i];
+        if ((int64_t)base < a.cap) {
+          a.out_key[base] = (p1 << a.sh) | p2;
+          a.out_val[base] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+        }
+        base++;
+      }
+  } else {
+    int at = wcnt + incl - cnt;
+#pragma unroll
+    for (int i = 0; i < 2 * NW; i++)
+      if (mask & (1u << i)) {
+        const uint64_t p1 = a.pos1[r0 + i];
+        my_wk[at] = (p1 << a.sh) | p2;
+        my_wv[at] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+        at++;
+      }
+    wcnt += total;
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
@@ -110,6 +216,10 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   uint64_t* wkey = reinterpret_cast<uint64_t*>(stage + STAGE_BYTES);
   uint32_t* wval = reinterpret_cast<uint32_t*>(stage + STAGE_BYTES + WKEY_BYTES);
   int* s_tile = reinterpret_cast<int*>(stage + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
+  // narrow-tile areas (inside the wide profile)
+  unsigned char* nprof = smem;
+  uint8_t* nrows = smem + NPROF_BYTES;
+  unsigned char* nstage = smem + NPROF_BYTES + NROWS_BYTES;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane & 7, js = lane >> 3;
@@ -117,7 +227,10 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   uint32_t* my_wv = wval + warp * WBUF;
   uint4* my_stage = reinterpret_cast<uint4*>(stage + warp * 4 * WIN);  // 12 x 16 bytes
   const uint32_t my_row = (uint32_t)__cvta_generic_to_shared(stage + warp * 4 * WIN + js * WIN);  // lane's window
+  unsigned char* my_nstage = nstage + warp * 32 * NSTRIDE;
+  const uint32_t my_nrow = (uint32_t)__cvta_generic_to_shared(my_nstage + lane * NSTRIDE);
   int wcnt = 0;  // warp-uniform fill of this warp's buffer
+  const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
 
   for (int i = tid; i < NCODE * NCODE; i += UNG_THREADS) tab[i] = c_score[i];
   const uint32_t s1x2 = ((uint32_t)(uint16_t)a.s1 << 16) | (uint16_t)a.s1;
@@ -137,119 +250,128 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
     const int4 tile = a.tiles[a.tile_base + t];
     const int key = tile.x, rows = tile.z;
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
-
-    // bank-1 windows of the tile, transposed to cell-major (rowsT[k][r])
-    for (int i = tid; i < ROWS_BYTES; i += UNG_THREADS) {
-      const int r = i & (UNG_T1 - 1), k = i / UNG_T1;
-      rowsT[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
-    }
-    __syncthreads();
-    // score profile prof[k][b][r], 16 rows per 16-byte item
-    for (int e = tid; e < WIN * NCODE * 8; e += UNG_THREADS) {
-      const int k = e / (NCODE * 8);
-      const int rem = e - k * (NCODE * 8);
-      const int b = rem >> 3, gg = rem & 7;
-      const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
-      const uint32_t src[4] = {c16.x, c16.y, c16.z, c16.w};
-      uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        uint32_t x = 0;
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-          const int ar = (src[q] >> (8 * r)) & 0xff;
-          x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
-        }
-        w[q] = x;
-      }
-      *reinterpret_cast<uint4*>(prof + (k * NCODE + b) * PROF_STRIDE + gg * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __syncthreads();
-
     const int64_t v0 = a.key_off2[key], v1 = a.key_off2[key + 1];
-    const unsigned char* plane = prof + g * 16;
-    // lanes 0..11 fetch the warp's next 4 windows (12 x 16 bytes) one
-    // iteration ahead; sentinel windows past the end of the key
-    uint4 pre = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
-    if (lane < 12) {
-      const int64_t v = v0 + warp * 4 + lane / 3;
-      if (v < v1) pre = __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + lane % 3);
-    }
-    for (int64_t vb = v0 + warp * 4; vb < v1; vb += NWARPS * 4) {
-      const int64_t v = vb + js;
-      const bool vok = v < v1;
-      __syncwarp();
-      if (lane < 12) my_stage[lane] = pre;
-      __syncwarp();
-      if (lane < 12) {
-        const int64_t vn = vb + NWARPS * 4 + lane / 3;
-        pre = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + lane % 3)
-                      : make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
+
+    if (tile.w == UNG_WIDE) {
+      // bank-1 windows of the tile, transposed to cell-major (rowsT[k][r])
+      for (int i = tid; i < ROWS_BYTES; i += UNG_THREADS) {
+        const int r = i & (UNG_T1 - 1), k = i / UNG_T1;
+        rowsT[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
       }
-      uint32_t s[8], m[8];
+      __syncthreads();
+      // score profile prof[k][b][r], 16 rows per 16-byte item
+      for (int e = tid; e < WIN * NCODE * 8; e += UNG_THREADS) {
+        const int k = e / (NCODE * 8);
+        const int rem = e - k * (NCODE * 8);
+        const int b = rem >> 3, gg = rem & 7;
+        const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
+        const uint32_t src[4] = {c16.x, c16.y, c16.z, c16.w};
+        uint32_t w[4];
 #pragma unroll
-      for (int w = 0; w < 8; w++) s[w] = m[w] = 0;
-      cell_pairs<0>(my_row, plane, s, m);
-      // any row of this lane at or above s1?
-      uint32_t mx = __vimax3_s16x2(m[0], m[1], m[2]);
-      mx = __vimax3_s16x2(mx, m[3], m[4]);
-      mx = __vimax3_s16x2(mx, m[5], m[6]);
-      mx = __vmaxs2(mx, m[7]);
-      const bool maybe = vok && __vcmpges2(mx, s1x2) != 0u;
-      if (__any_sync(0xffffffffu, maybe)) {
-        // rows 16g + 2w (low half of m[w]) and 16g + 2w + 1 (high half)
-        unsigned mask = 0;
-        if (maybe) {
+        for (int q = 0; q < 4; q++) {
+          uint32_t x = 0;
 #pragma unroll
-          for (int w = 0; w < 8; w++) {
-            const uint32_t c = __vcmpges2(m[w], s1x2);
-            mask |= ((c & 1u) | ((c >> 15) & 2u)) << (2 * w);
+          for (int r = 0; r < 4; r++) {
+            const int ar = (src[q] >> (8 * r)) & 0xff;
+            x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
           }
-          const int valid_rows = rows - g * ROWS_PER_LANE;
-          if (valid_rows < ROWS_PER_LANE) mask &= valid_rows <= 0 ? 0u : ((1u << valid_rows) - 1u);
+          w[q] = x;
         }
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
+        *reinterpret_cast<uint4*>(prof + (k * NCODE + b) * PROF_STRIDE + gg * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      __syncthreads();
+
+      const unsigned char* plane = prof + g * 16;
+      // lanes 0..11 fetch the warp's next 4 windows (12 x 16 bytes) one
+      // iteration ahead; sentinel windows past the end of the key
+      uint4 pre = sent16;
+      if (lane < 12) {
+        const int64_t v = v0 + warp * 4 + lane / 3;
+        if (v < v1) pre = __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + lane % 3);
+      }
+      for (int64_t vb = v0 + warp * 4; vb < v1; vb += NWARPS * 4) {
+        const int64_t v = vb + js;
+        const bool vok = v < v1;
+        __syncwarp();
+        if (lane < 12) my_stage[lane] = pre;
+        __syncwarp();
+        if (lane < 12) {
+          const int64_t vn = vb + NWARPS * 4 + lane / 3;
+          pre = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + lane % 3) : sent16;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (wcnt + total > WBUF) {
-          __syncwarp();
-          flush_warp(my_wk, my_wv, wcnt, lane, a.out_count, a.out_key, a.out_val, a.cap);
-          __syncwarp();
-          wcnt = 0;
+        uint32_t s[8], m[8];
+#pragma unroll
+        for (int w = 0; w < 8; w++) s[w] = m[w] = 0;
+        cell_pairs<0, 8, PROF_STRIDE>(my_row, plane, s, m);
+        emit_hits<8>(m, vok, rows - g * ROWS_PER_LANE, u0 + g * ROWS_PER_LANE, v, a, s1x2, lane, my_wk, my_wv,
+                     wcnt);
+      }
+    } else {
+      // narrow tile: rows cell-major (nrows[k][r]), profile planes
+      // nprof[p][k][b][r'] for rows 4p + r'
+      for (int i = tid; i < NROWS_BYTES; i += UNG_THREADS) {
+        const int r = i & (UNG_NT1 - 1), k = i / UNG_NT1;
+        nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
+      }
+      __syncthreads();
+      for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
+        const int k = e / NCODE, b = e - k * NCODE;
+        const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + k * UNG_NT1);
+        const uint32_t src[2] = {c8.x, c8.y};
+        uint32_t w[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          uint32_t x = 0;
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const int ar = (src[q] >> (8 * r)) & 0xff;
+            x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
+          }
+          w[q] = x;
         }
-        const uint64_t p2 = vok ? (uint64_t)a.pos2[v] : 0;
-        if (total > WBUF) {
-          unsigned long long base = 0;
-          if (lane == 0) base = atomicAdd(a.out_count, (unsigned long long)total);
-          base = __shfl_sync(0xffffffffu, base, 0) + (incl - cnt);
+        *reinterpret_cast<uint32_t*>(nprof + e * 4) = w[0];
+        *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = w[1];
+      }
+      __syncthreads();
+
+      // the warp's 32 windows are 96 consecutive 16-byte items; lane l moves
+      // items l, l + 32, l + 64 (window q / 3, part q % 3), one iteration ahead
+      int nw[3], np[3];
 #pragma unroll
-          for (int i = 0; i < ROWS_PER_LANE; i++)
-            if (mask & (1u << i)) {
-              const uint64_t p1 = a.pos1[u0 + g * ROWS_PER_LANE + i];
-              if ((int64_t)base < a.cap) {
-                a.out_key[base] = (p1 << a.sh) | p2;
-                a.out_val[base] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-              }
-              base++;
-            }
-        } else {
-          int at = wcnt + incl - cnt;
+      for (int j = 0; j < 3; j++) {
+        nw[j] = (lane + 32 * j) / 3;
+        np[j] = (lane + 32 * j) % 3;
+      }
+      uint4 pre[3];
 #pragma unroll
-          for (int i = 0; i < ROWS_PER_LANE; i++)
-            if (mask & (1u << i)) {
-              const uint64_t p1 = a.pos1[u0 + g * ROWS_PER_LANE + i];
-              my_wk[at] = (p1 << a.sh) | p2;
-              my_wv[at] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-              at++;
-            }
-          wcnt += total;
+      for (int j = 0; j < 3; j++) {
+        const int64_t v = v0 + warp * 32 + nw[j];
+        pre[j] = v < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + np[j]) : sent16;
+      }
+      for (int64_t vb = v0 + warp * 32; vb < v1; vb += NWARPS * 32) {
+        const int64_t v = vb + lane;
+        const bool vok = v < v1;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          uint32_t* d = reinterpret_cast<uint32_t*>(my_nstage + nw[j] * NSTRIDE + np[j] * 16);
+          d[0] = pre[j].x;
+          d[1] = pre[j].y;
+          d[2] = pre[j].z;
+          d[3] = pre[j].w;
         }
         __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+          const int64_t vn = vb + NWARPS * 32 + nw[j];
+          pre[j] = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + np[j]) : sent16;
+        }
+        uint32_t s[4], m[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) s[w] = m[w] = 0;
+        cell_pairs<0, 4, 4>(my_nrow, nprof, s, m);
+        emit_hits<4>(m, vok, rows, u0, v, a, s1x2, lane, my_wk, my_wv, wcnt);
       }
     }
     __syncthreads();  // the next tile rebuilds the profile

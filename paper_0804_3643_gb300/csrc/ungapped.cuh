@@ -4,13 +4,17 @@
 
 namespace plast {
 
+// tile shapes (ungapped.cu): rows per tile UNG_T1 (wide) or UNG_NT1 (narrow)
+constexpr int UNG_WIDE = 0;
+constexpr int UNG_NARROW = 1;
+
 struct UngArgs {
   const int8_t* nb1;        // bank-1 windows [n_idx1][48]
   const uint32_t* pos1;     // bank-1 padded positions, CSR order
   const int8_t* nb2;        // bank-2 windows [n_idx2][48]
   const uint32_t* pos2;     // bank-2 padded positions, CSR order
   const int64_t* key_off2;  // bank-2 CSR offsets [8801]
-  const int4* tiles;        // (key, first bank-1 CSR index, rows <= 64, 0)
+  const int4* tiles;        // (key, first bank-1 CSR index, rows, shape UNG_WIDE / UNG_NARROW)
   int32_t n_tiles;          // tiles handled by this launch
   int32_t tile_base;        // first tile of this launch in `tiles`
   int32_t* tile_counter;    // persistent schedule: next tile to take
@@ -49,6 +53,14 @@ cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int
                                   const int64_t* pad_off2, int32_t n2, plast_gapped* out, cudaStream_t st);
 // *n_dev = min(*count, cap): the hit count a planned chain feeds forward.
 cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st);
+cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev, cudaStream_t st);
+// Record sort of a search: the passing hits' keys and indexes gathered into
+// record slots, then (after sorting the pairs by key) the records written in
+// key order.
+cudaError_t launch_gather_pass(const GapArgs& a, const int64_t* at, uint64_t* rkey, uint32_t* ridx, cudaStream_t st);
+cudaError_t launch_write_sorted(const GapArgs& a, const uint64_t* skey, const uint32_t* sidx, int64_t m,
+                                const int64_t* m_dev, const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
+                                int32_t n2, plast_gapped* out, cudaStream_t st);
 cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* pad_off1, int32_t n1,
                                 const int64_t* pad_off2, int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad,
                                 cudaStream_t st);

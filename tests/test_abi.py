@@ -45,6 +45,16 @@ def test_host_only_entry_points(lib):
     B.plast_set_schedule(0)
     with pytest.raises(B.PlastError):
         B.plast_set_schedule(7)
+    with pytest.raises(B.PlastError):
+        B.plast_set_tile_shape(3)
+    B.plast_set_tile_shape(0)
+    c = B.plast_get_tile_costs()
+    assert c["wide_slot"] > 0 and c["narrow_slot"] > 0
+    with pytest.raises(B.PlastError):
+        B.plast_set_tile_costs(dict(c, narrow_slot=-1.0))
+    B.plast_set_tile_costs(dict(c, wide_tile=c["wide_tile"] + 1))
+    assert B.plast_get_tile_costs()["wide_tile"] == c["wide_tile"] + 1
+    B.plast_set_tile_costs(c)
 
 
 def test_record_layouts_match_header():
