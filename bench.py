@@ -224,6 +224,9 @@ def setup_tiles(args, B) -> dict:
         t0 = time.time()
         c = B.autotune()
         log(f"tile costs ({c['source']}, {time.time() - t0:.2f}s): {c}")
+    if args.wide_int16_cells is not None:
+        B.plast_set_tile_costs(dict(c, wide_int16_cells=args.wide_int16_cells))
+        c = dict(c, wide_int16_cells=args.wide_int16_cells, source=c["source"] + ", variant forced")
     return dict(c, shape=args.tile_shape)
 
 
@@ -611,6 +614,8 @@ def main():
     ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow"],
                     help="stage-2 tile shapes: by measured cost (default) or forced")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile costs")
+    ap.add_argument("--wide-int16-cells", type=int, default=None, choices=[0, 12, 14, 16, 18],
+                    help="force the wide stage-2 kernel variant (default: the autotuner's pick)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batching_stress", "tplastn", "serving", "query"],
                     help="the headline line is plastp_full; the others print their own lines")

@@ -273,15 +273,20 @@ int plast_set_schedule(int mode);
  * the current device (random banks, the stage-2 kernel timed with every tile
  * wide, then every tile narrow, against a long and a short bank 2; about a
  * second),
- * installs them and copies them to *out (may be NULL); plast_get_tile_costs /
- * plast_set_tile_costs read and install them (for a cached calibration;
- * PLAST_E_INVALID unless the slot costs are positive and the tile costs
- * non-negative).  plast_set_tile_shape forces the shape of every tile
+ * installs them and copies them to *out (may be NULL).  It also picks the
+ * wide kernel variant, how many cells of the wide profile are held as int16
+ * (no sign extension, twice the shared-memory traffic), by timing each.
+ * plast_get_tile_costs / plast_set_tile_costs read and install costs and
+ * variant (for a cached calibration; PLAST_E_INVALID unless the slot costs
+ * are positive, the tile costs non-negative and wide_int16_cells one of the
+ * variants).  plast_set_tile_shape forces the shape of every tile
  * (1 wide, 2 narrow; 0, the default, by cost).  Shapes change the schedule,
  * never the results.  Settings are process-wide and apply to later calls.
  */
 typedef struct plast_tile_costs {
   double wide_slot, wide_tile, narrow_slot, narrow_tile;
+  int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14, 16 or 18) */
+  int32_t reserved;         /* 0 */
 } plast_tile_costs;
 int plast_autotune(void* stream, plast_tile_costs* out);
 int plast_get_tile_costs(plast_tile_costs* out);

@@ -44,10 +44,11 @@ class plast_params(ctypes.Structure):
 
 
 class plast_tile_costs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")]
+    _fields_ = [(n, ctypes.c_double) for n in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")] + \
+        [("wide_int16_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 class PlastError(RuntimeError):
@@ -202,7 +203,8 @@ def plast_get_tile_costs() -> dict:
 
 
 def plast_set_tile_costs(costs: dict) -> None:
-    c = plast_tile_costs(**{k: float(costs[k]) for k, _ in plast_tile_costs._fields_})
+    c = plast_tile_costs(**{k: float(costs[k]) for k in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")},
+                         wide_int16_cells=int(costs.get("wide_int16_cells", 14)))
     rc = lib().plast_set_tile_costs(ctypes.byref(c))
     if rc:
         raise PlastError("plast_set_tile_costs", rc)

@@ -124,7 +124,7 @@ int num_sms() {
 // shape's rows x n2 rounded up to that granularity.  Defaults from a GB300;
 // plast_autotune measures them on the current device.
 std::mutex g_cost_mu;
-plast_tile_costs g_costs = {0.40, 6800.0, 0.71, 2500.0};
+plast_tile_costs g_costs = {0.320, 5500.0, 0.525, 633.0, 14, 0};
 std::atomic<int> g_shape{0};  // 0: by cost, 1: wide only, 2: narrow only
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
 constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tile
@@ -1082,6 +1082,8 @@ int plast_get_tile_costs(plast_tile_costs* out) {
   if (!out) return PLAST_E_INVALID;
   std::lock_guard<std::mutex> lk(g_cost_mu);
   *out = g_costs;
+  out->wide_int16_cells = ungapped_variant_n16(ungapped_variant());
+  out->reserved = 0;
   return PLAST_OK;
 }
 
@@ -1089,8 +1091,14 @@ int plast_set_tile_costs(const plast_tile_costs* c) {
   if (!c || !(c->wide_slot > 0) || !(c->narrow_slot > 0) || !(c->wide_tile >= 0) || !(c->narrow_tile >= 0) ||
       c->wide_slot > 1e6 || c->narrow_slot > 1e6 || c->wide_tile > 1e12 || c->narrow_tile > 1e12)
     return PLAST_E_INVALID;
+  int variant = -1;
+  for (int v = 0; v < UNG_VARIANTS; v++)
+    if (ungapped_variant_n16(v) == c->wide_int16_cells) variant = v;
+  if (variant < 0) return PLAST_E_INVALID;
   std::lock_guard<std::mutex> lk(g_cost_mu);
   g_costs = *c;
+  g_costs.reserved = 0;
+  set_ungapped_variant(variant);
   return PLAST_OK;
 }
 
@@ -1131,27 +1139,43 @@ int plast_autotune(void* stream, plast_tile_costs* out) {
   plast_tile_costs c;
   plast_get_tile_costs(&c);
   const double sms = (double)num_sms();
-  for (int shape = 1; shape <= 2 && rc == PLAST_OK; shape++) {
+  // slot and tile cost of a shape from its times on the long and short bank 2
+  auto fit = [&](int shape, double* slot, double* tile, double* t_long) {
     double t_l, s_l, n_l, t_s, s_s, n_s;
-    rc = time_stage2(b1, b2l, shape, st, 3, &t_l, &s_l, &n_l);
-    if (rc == PLAST_OK) rc = time_stage2(b1, b2s, shape, st, 3, &t_s, &s_s, &n_s);
-    if (rc != PLAST_OK) break;
+    int r = time_stage2(b1, b2l, shape, st, 3, &t_l, &s_l, &n_l);
+    if (r == PLAST_OK) r = time_stage2(b1, b2s, shape, st, 3, &t_s, &s_s, &n_s);
+    if (r != PLAST_OK) return r;
     // SM-nanoseconds = slot cost x slots + tile cost x tiles, for both banks
     const double y_l = t_l * 1e6 * sms, y_s = t_s * 1e6 * sms;
     const double det = s_l * n_s - s_s * n_l;
-    double slot = det != 0 ? (y_l * n_s - y_s * n_l) / det : 0;
-    double tile = det != 0 ? (s_l * y_s - s_s * y_l) / det : 0;
-    if (!(slot > 0) || !(tile >= 0)) {
-      slot = y_l / std::max(s_l, 1.0);
-      tile = 0;
+    *slot = det != 0 ? (y_l * n_s - y_s * n_l) / det : 0;
+    *tile = det != 0 ? (s_l * y_s - s_s * y_l) / det : 0;
+    if (!(*slot > 0) || !(*tile >= 0)) {
+      *slot = y_l / std::max(s_l, 1.0);
+      *tile = 0;
     }
-    if (shape == 1) {
+    *t_long = t_l;
+    return PLAST_OK;
+  };
+  const int saved_variant = ungapped_variant();
+  double best_t = 0;
+  int best_v = saved_variant;
+  for (int v = 0; v < UNG_VARIANTS && rc == PLAST_OK; v++) {
+    set_ungapped_variant(v);
+    double slot, tile, t_long;
+    rc = fit(1, &slot, &tile, &t_long);
+    if (rc == PLAST_OK && (v == 0 || t_long < best_t)) {
+      best_t = t_long;
+      best_v = v;
       c.wide_slot = slot;
       c.wide_tile = tile;
-    } else {
-      c.narrow_slot = slot;
-      c.narrow_tile = tile;
+      c.wide_int16_cells = ungapped_variant_n16(v);
     }
+  }
+  set_ungapped_variant(rc == PLAST_OK ? best_v : saved_variant);
+  if (rc == PLAST_OK) {
+    double t_long;
+    rc = fit(2, &c.narrow_slot, &c.narrow_tile, &t_long);
   }
   plast_bank_free(b1);
   plast_bank_free(b2l);

@@ -12,11 +12,21 @@
 // from the maxima (the reset of Annex 4).
 //
 // Two tile shapes share the kernel:
-//  * wide: up to 128 rows, profile rows of one (k, b) 144 bytes apart.  Lane
-//    (g, js) of a warp scores bank-2 window js (4 per warp) against rows
-//    16g .. 16g+15 with one 16-byte load per cell; the 8 lanes of a window
-//    read one 128-byte profile row, so a warp's 512 bytes come out of shared
-//    memory in the minimum 4 wavefronts.
+//  * wide: up to 128 rows.  Lane (g, js) of a warp scores bank-2 window js
+//    (4 per warp) against rows 16g .. 16g+15; the 8 lanes of a window read
+//    one 128-byte profile row per cell, so a warp's loads come out of shared
+//    memory in the minimum number of wavefronts.  Two refinements:
+//    - the seed cells.  Positions 1 and 4 of the subset seed have one class
+//      per residue (Section 3.3.1), so cells 0 and 3 pair a bank-1 residue
+//      with itself and score the diagonal entry d0, d3 > 0 of the row.  The
+//      profile folds them into cells 1 and 2: P1 = d0 + s(a1, b),
+//      M1 = d0 + max(0, s(a1, b)), P2 = s(a2, b) + d3, and the window starts
+//      from sum = P1[b1] + P2[b2] = S3 and max = max(M1[b1], S3), which are
+//      the running sum after cell 3 and max(0, S0, S1, S2, S3) (S2 < S3, the
+//      empty prefix and S0 are dominated).
+//    - N16 of the cells are stored as int16 (two 16-byte loads, no
+//      sign extension), trading shared-memory bandwidth, which has headroom,
+//      for ALU-pipe work, which has none; the rest are int8.
 //  * narrow: up to 8 rows, the profile in two planes of 4 rows, one 32-bit
 //    word per (k, b).  Every lane scores its own bank-2 window (32 per warp)
 //    against the 8 rows with two word loads per cell; the 22 words of a cell
@@ -34,22 +44,42 @@
 // one global atomic per 64 records, as (padded pos1 << sh | padded pos2,
 // score).  Tiles come from a device counter (persistent launch, costliest
 // tile first) or, in the plain schedule, one launch per key.
+#include <atomic>
+
 #include "common.cuh"
 #include "ungapped.cuh"
 
 namespace plast {
 
 constexpr int NWARPS = UNG_THREADS / 32;
-constexpr int WBUF = 64;
-constexpr int PROF_STRIDE = UNG_T1 + 16;                   // bytes per (k, b) profile row
-constexpr int PROF_BYTES = WIN * NCODE * PROF_STRIDE;      // 152064
+constexpr int WBUF = 32;
+constexpr int PROF_STRIDE = UNG_T1 + 16;                   // bytes per (k, b) row of an int8 plane
+constexpr int PROF16_STRIDE = 2 * UNG_T1 + 32;             // bytes per (k, b) row of an int16 plane
+constexpr int PLANE8 = NCODE * PROF_STRIDE;                // 3168
+constexpr int PLANE16 = NCODE * PROF16_STRIDE;             // 6336
+constexpr int SEED_PLANES = 3;                             // P1, M1, P2 (cells 0-3)
+constexpr int FIRST_CELL = 4;                              // first cell after the seed
 constexpr int TAB_BYTES = 512;                             // int8 [22][22], padded
-constexpr int ROWS_BYTES = WIN * UNG_T1;                   // 6144, cell-major
+constexpr int ROWS_BYTES = WIN * UNG_T1;                   // 6144, cell-major; shares the staging area
 constexpr int STAGE_BYTES = NWARPS * 4 * WIN;              // 6144: 4 bank-2 windows per warp
-constexpr int WKEY_BYTES = NWARPS * WBUF * 8;              // 16384
-constexpr int WVAL_BYTES = NWARPS * WBUF * 4;              // 8192
-constexpr int UNG_SMEM = PROF_BYTES + TAB_BYTES + ROWS_BYTES + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 16;
+constexpr int WKEY_BYTES = NWARPS * WBUF * 8;              // 8192
+constexpr int WVAL_BYTES = NWARPS * WBUF * 4;              // 4096
+static_assert(ROWS_BYTES <= STAGE_BYTES, "the tile's bank-1 rows fit the staging area");
 constexpr int ROWS_PER_LANE = UNG_T1 / 8;                  // 16
+
+// Wide-tile profile with N16 int16 cells (cells 4 .. 4 + N16 - 1):
+// int8 planes P1, M1, P2, then the int8 cells; then the int16 cells.
+template <int N16>
+struct Wide {
+  static_assert(N16 % 2 == 0 && N16 >= 0 && N16 <= WIN - FIRST_CELL, "int16 cells come in pairs");
+  static constexpr int N8 = SEED_PLANES + (WIN - FIRST_CELL - N16);
+  static constexpr int BASE16 = N8 * PLANE8;
+  static constexpr int PROF = BASE16 + N16 * PLANE16;
+  static constexpr int SMEM = PROF + TAB_BYTES + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 2 * 48;
+  __host__ __device__ static constexpr bool is16(int k) { return k >= FIRST_CELL && k < FIRST_CELL + N16; }
+  // int8 plane of cell k >= FIRST_CELL + N16
+  __host__ __device__ static constexpr int plane8(int k) { return SEED_PLANES + (k - FIRST_CELL - N16); }
+};
 
 // narrow tiles overlay the wide profile
 constexpr int NSTRIDE = 52;                                // staged window stride: 13 words, conflict-free bytes
@@ -57,10 +87,9 @@ constexpr int NPLANE = WIN * NCODE * 4;                     // 4224: one plane o
 constexpr int NPROF_BYTES = 2 * NPLANE;                     // 8448
 constexpr int NROWS_BYTES = WIN * UNG_NT1;                 // 384, cell-major
 constexpr int NSTAGE_BYTES = NWARPS * 32 * NSTRIDE;        // 53248: one window per lane
-static_assert(NPROF_BYTES + NROWS_BYTES + NSTAGE_BYTES <= PROF_BYTES, "narrow tile fits the wide profile area");
+static_assert(NPROF_BYTES + NROWS_BYTES + NSTAGE_BYTES <= Wide<0>::PROF, "narrow tile fits the wide profile area");
 static_assert(NPROF_BYTES % 16 == 0 && NROWS_BYTES % 16 == 0 && (32 * NSTRIDE) % 16 == 0, "alignment");
-
-size_t ungapped_smem_bytes() { return (size_t)UNG_SMEM; }
+static_assert(Wide<UNG_MAX_N16>::SMEM <= 232448, "shared memory per CTA");
 
 // bytes 2h, 2h+1 of x, sign-extended into the two halves of an int16x2
 __device__ __forceinline__ uint32_t sext_pair(uint32_t x, int h) {
@@ -103,37 +132,76 @@ __device__ __forceinline__ void flush_warp(const uint64_t* wk, const uint32_t* w
   }
 }
 
-// Cells K and K+1 of one bank-2 window against this lane's 2 * NW bank-1 rows,
-// then the following pairs (compile-time recursion over K = 0, 2, .., 46).
-// Wide (NW = 8): the lane's 16 row scores for (k, b) are the 16 bytes at
-// plane + (k * NCODE + b) * STRIDE.  Narrow (NW = 4): rows 0-3 are the word at
-// plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE bytes further.
-template <int K, int NW, int STRIDE>
-__device__ __forceinline__ void cell_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[NW],
-                                           uint32_t (&m)[NW]) {
+// The lane's 16 row scores of wide cell K against bank-2 residue b, as eight
+// int16x2 words (rows 2w, 2w+1 in word w).  plane = profile + 16 g.
+template <int K, int N16>
+__device__ __forceinline__ void wide_scores(const unsigned char* plane, uint32_t b, uint32_t (&u)[8]) {
+  if constexpr (Wide<N16>::is16(K)) {
+    // rows 16g .. 16g+7 at 16g, rows 16g+8 .. 16g+15 at 128 + 16g
+    const unsigned char* e = plane + Wide<N16>::BASE16 + (K - FIRST_CELL) * PLANE16 + b * PROF16_STRIDE;
+    const uint4 lo = *reinterpret_cast<const uint4*>(e);
+    const uint4 hi = *reinterpret_cast<const uint4*>(e + 128);
+    u[0] = lo.x;
+    u[1] = lo.y;
+    u[2] = lo.z;
+    u[3] = lo.w;
+    u[4] = hi.x;
+    u[5] = hi.y;
+    u[6] = hi.z;
+    u[7] = hi.w;
+  } else {
+    unpack16(*reinterpret_cast<const uint4*>(plane + Wide<N16>::plane8(K) * PLANE8 + b * PROF_STRIDE), u);
+  }
+}
+
+// Cells K and K+1 of one bank-2 window against the lane's 16 wide rows, then
+// the following pairs (compile-time recursion over K = 4, 6, .., 46).
+template <int K, int N16>
+__device__ __forceinline__ void wide_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[8],
+                                           uint32_t (&m)[8]) {
   if constexpr (K < WIN) {
     const uint32_t b0 = lds_u8<K>(row), b1 = lds_u8<K + 1>(row);
-    uint32_t u0[NW], u1[NW];
-    if constexpr (NW == 8) {
-      unpack16(*reinterpret_cast<const uint4*>(plane + (K * NCODE + b0) * STRIDE), u0);
-      unpack16(*reinterpret_cast<const uint4*>(plane + ((K + 1) * NCODE + b1) * STRIDE), u1);
-    } else {
-      const unsigned char* e0 = plane + (K * NCODE + b0) * 4;
-      const unsigned char* e1 = plane + ((K + 1) * NCODE + b1) * 4;
-      unpack8(*reinterpret_cast<const uint32_t*>(e0), *reinterpret_cast<const uint32_t*>(e0 + NPLANE), u0);
-      unpack8(*reinterpret_cast<const uint32_t*>(e1), *reinterpret_cast<const uint32_t*>(e1 + NPLANE), u1);
-    }
+    uint32_t u0[8], u1[8];
+    wide_scores<K, N16>(plane, b0, u0);
+    wide_scores<K + 1, N16>(plane, b1, u1);
 #pragma unroll
-    for (int w = 0; w < NW; w++) {
+    for (int w = 0; w < 8; w++) {
       const uint32_t t0 = __vadd2(s[w], u0[w]);
       s[w] = __vadd2(t0, u1[w]);
       m[w] = __vimax3_s16x2(m[w], t0, s[w]);
     }
     if constexpr (K + 1 == RIGHT - 1) {  // the reset of Annex 4
 #pragma unroll
-      for (int w = 0; w < NW; w++) s[w] = m[w];
+      for (int w = 0; w < 8; w++) s[w] = m[w];
     }
-    cell_pairs<K + 2, NW, STRIDE>(row, plane, s, m);
+    wide_pairs<K + 2, N16>(row, plane, s, m);
+  }
+}
+
+// Cells K and K+1 of the lane's bank-2 window against its 8 narrow rows (rows
+// 0-3 the word at plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE
+// bytes further), then the following pairs (K = 0, 2, .., 46).
+template <int K>
+__device__ __forceinline__ void narrow_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[4],
+                                             uint32_t (&m)[4]) {
+  if constexpr (K < WIN) {
+    const uint32_t b0 = lds_u8<K>(row), b1 = lds_u8<K + 1>(row);
+    uint32_t u0[4], u1[4];
+    const unsigned char* e0 = plane + (K * NCODE + b0) * 4;
+    const unsigned char* e1 = plane + ((K + 1) * NCODE + b1) * 4;
+    unpack8(*reinterpret_cast<const uint32_t*>(e0), *reinterpret_cast<const uint32_t*>(e0 + NPLANE), u0);
+    unpack8(*reinterpret_cast<const uint32_t*>(e1), *reinterpret_cast<const uint32_t*>(e1 + NPLANE), u1);
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+      const uint32_t t0 = __vadd2(s[w], u0[w]);
+      s[w] = __vadd2(t0, u1[w]);
+      m[w] = __vimax3_s16x2(m[w], t0, s[w]);
+    }
+    if constexpr (K + 1 == RIGHT - 1) {
+#pragma unroll
+      for (int w = 0; w < 4; w++) s[w] = m[w];
+    }
+    narrow_pairs<K + 2>(row, plane, s, m);
   }
 }
 
@@ -207,15 +275,47 @@ __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int
   __syncwarp();
 }
 
+// The next tile of a CTA, read by one thread while the CTA works on the
+// current one.
+struct TileSlot {
+  int4 tile;       // (key, first bank-1 CSR index, rows, shape)
+  int64_t v0, v1;  // the key's bank-2 CSR range
+  int t;           // tile index (>= n_tiles: none left)
+};
+static_assert(sizeof(TileSlot) <= 48, "tile slot size");
+
+__device__ __forceinline__ void fetch_tile(const UngArgs& a, int t, TileSlot* slot) {
+  slot->t = t;
+  if (t < a.n_tiles) {
+    const int4 tl = a.tiles[a.tile_base + t];
+    slot->tile = tl;
+    slot->v0 = a.key_off2[tl.x];
+    slot->v1 = a.key_off2[tl.x + 1];
+  }
+}
+
+// Four rows: byte r of the result is score(byte r of src, b).
+__device__ __forceinline__ uint32_t pack4(uint32_t src, const int8_t* tab, int b) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const int ar = (src >> (8 * r)) & 0xff;
+    x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
+  }
+  return x;
+}
+
+template <int N16>
 __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
+  using L = Wide<N16>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* prof = smem;
-  int8_t* tab = reinterpret_cast<int8_t*>(smem + PROF_BYTES);
-  uint8_t* rowsT = smem + PROF_BYTES + TAB_BYTES;
-  unsigned char* stage = smem + PROF_BYTES + TAB_BYTES + ROWS_BYTES;
+  int8_t* tab = reinterpret_cast<int8_t*>(smem + L::PROF);
+  unsigned char* stage = smem + L::PROF + TAB_BYTES;
+  uint8_t* rowsT = stage;  // the tile's bank-1 rows while its profile is built
   uint64_t* wkey = reinterpret_cast<uint64_t*>(stage + STAGE_BYTES);
   uint32_t* wval = reinterpret_cast<uint32_t*>(stage + STAGE_BYTES + WKEY_BYTES);
-  int* s_tile = reinterpret_cast<int*>(stage + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
+  TileSlot* slots = reinterpret_cast<TileSlot*>(stage + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
   // narrow-tile areas (inside the wide profile)
   unsigned char* nprof = smem;
   uint8_t* nrows = smem + NPROF_BYTES;
@@ -235,22 +335,17 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   for (int i = tid; i < NCODE * NCODE; i += UNG_THREADS) tab[i] = c_score[i];
   const uint32_t s1x2 = ((uint32_t)(uint16_t)a.s1 << 16) | (uint16_t)a.s1;
 
-  int iter = 0;
-  for (;;) {
-    int t;
-    if (a.persistent) {
-      if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1);
-      __syncthreads();
-      t = *s_tile;
-    } else {
-      t = iter == 0 ? (int)blockIdx.x : a.n_tiles;
-    }
-    iter++;
-    if (t >= a.n_tiles) break;
-    const int4 tile = a.tiles[a.tile_base + t];
-    const int key = tile.x, rows = tile.z;
+  // tiles: from the device counter (persistent) or this CTA's own; thread 0
+  // fetches the next one into the other slot while the CTA works
+  if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : (int)blockIdx.x, &slots[0]);
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
+    if (slots[buf].t >= a.n_tiles) break;
+    const int4 tile = slots[buf].tile;
+    const int64_t v0 = slots[buf].v0, v1 = slots[buf].v1;
+    if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : a.n_tiles, &slots[buf ^ 1]);
+    const int rows = tile.z;
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
-    const int64_t v0 = a.key_off2[key], v1 = a.key_off2[key + 1];
 
     if (tile.w == UNG_WIDE) {
       // bank-1 windows of the tile, transposed to cell-major (rowsT[k][r])
@@ -259,26 +354,61 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
         rowsT[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
       }
       __syncthreads();
-      // score profile prof[k][b][r], 16 rows per 16-byte item
-      for (int e = tid; e < WIN * NCODE * 8; e += UNG_THREADS) {
-        const int k = e / (NCODE * 8);
-        const int rem = e - k * (NCODE * 8);
+      // int8 planes: 16 rows per 16-byte item
+      for (int e = tid; e < L::N8 * NCODE * 8; e += UNG_THREADS) {
+        const int p = e / (NCODE * 8);
+        const int rem = e - p * (NCODE * 8);
         const int b = rem >> 3, gg = rem & 7;
+        uint32_t w[4];
+        if (p >= SEED_PLANES) {
+          const int k = p - SEED_PLANES + FIRST_CELL + N16;
+          const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
+          w[0] = pack4(c16.x, tab, b);
+          w[1] = pack4(c16.y, tab, b);
+          w[2] = pack4(c16.z, tab, b);
+          w[3] = pack4(c16.w, tab, b);
+        } else {
+          // P1 = d0 + s(a1, b), M1 = d0 + max(0, s(a1, b)), P2 = s(a2, b) + d3
+          const int kx = p == 2 ? 2 : 1, kd = p == 2 ? 3 : 0;
+          const uint4 cx = *reinterpret_cast<const uint4*>(rowsT + kx * UNG_T1 + gg * ROWS_PER_LANE);
+          const uint4 cd = *reinterpret_cast<const uint4*>(rowsT + kd * UNG_T1 + gg * ROWS_PER_LANE);
+          const uint32_t sx[4] = {cx.x, cx.y, cx.z, cx.w}, sd[4] = {cd.x, cd.y, cd.z, cd.w};
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+              const int ax = (sx[q] >> (8 * r)) & 0xff, ad = (sd[q] >> (8 * r)) & 0xff;
+              int v = tab[ax * NCODE + b];
+              if (p == 1) v = max(v, 0);
+              v += tab[ad * NCODE + ad];
+              x |= (uint32_t)(uint8_t)(int8_t)v << (8 * r);
+            }
+            w[q] = x;
+          }
+        }
+        *reinterpret_cast<uint4*>(prof + p * PLANE8 + b * PROF_STRIDE + gg * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      // int16 planes: 16 rows per item, rows 0-7 and 8-15 of the group 128 bytes apart
+      for (int e = tid; e < N16 * NCODE * 8; e += UNG_THREADS) {
+        const int c = e / (NCODE * 8);
+        const int rem = e - c * (NCODE * 8);
+        const int b = rem >> 3, gg = rem & 7;
+        const int k = FIRST_CELL + c;
         const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
         const uint32_t src[4] = {c16.x, c16.y, c16.z, c16.w};
-        uint32_t w[4];
+        uint32_t w[8];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-          uint32_t x = 0;
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const int ar = (src[q] >> (8 * r)) & 0xff;
-            x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
-          }
-          w[q] = x;
+          const int a0 = src[q] & 0xff, a1 = (src[q] >> 8) & 0xff, a2 = (src[q] >> 16) & 0xff, a3 = src[q] >> 24;
+          w[2 * q] = (uint32_t)(uint16_t)(int16_t)tab[a0 * NCODE + b] |
+                     ((uint32_t)(uint16_t)(int16_t)tab[a1 * NCODE + b] << 16);
+          w[2 * q + 1] = (uint32_t)(uint16_t)(int16_t)tab[a2 * NCODE + b] |
+                         ((uint32_t)(uint16_t)(int16_t)tab[a3 * NCODE + b] << 16);
         }
-        *reinterpret_cast<uint4*>(prof + (k * NCODE + b) * PROF_STRIDE + gg * 16) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        unsigned char* d = prof + L::BASE16 + c * PLANE16 + b * PROF16_STRIDE + gg * 16;
+        *reinterpret_cast<uint4*>(d) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(d + 128) = make_uint4(w[4], w[5], w[6], w[7]);
       }
       __syncthreads();
 
@@ -301,9 +431,18 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
           pre = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + lane % 3) : sent16;
         }
         uint32_t s[8], m[8];
+        {  // cells 0-3 from the folded seed planes
+          const uint32_t bs1 = lds_u8<1>(my_row), bs2 = lds_u8<2>(my_row);
+          uint32_t up[8], uq[8];
+          unpack16(*reinterpret_cast<const uint4*>(plane + bs1 * PROF_STRIDE), up);
+          unpack16(*reinterpret_cast<const uint4*>(plane + 2 * PLANE8 + bs2 * PROF_STRIDE), uq);
 #pragma unroll
-        for (int w = 0; w < 8; w++) s[w] = m[w] = 0;
-        cell_pairs<0, 8, PROF_STRIDE>(my_row, plane, s, m);
+          for (int w = 0; w < 8; w++) s[w] = __vadd2(up[w], uq[w]);
+          unpack16(*reinterpret_cast<const uint4*>(plane + PLANE8 + bs1 * PROF_STRIDE), up);
+#pragma unroll
+          for (int w = 0; w < 8; w++) m[w] = __vmaxs2(up[w], s[w]);
+        }
+        wide_pairs<FIRST_CELL, N16>(my_row, plane, s, m);
         emit_hits<8>(m, vok, rows - g * ROWS_PER_LANE, u0 + g * ROWS_PER_LANE, v, a, s1x2, lane, my_wk, my_wv,
                      wcnt);
       }
@@ -318,20 +457,8 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
       for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
         const int k = e / NCODE, b = e - k * NCODE;
         const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + k * UNG_NT1);
-        const uint32_t src[2] = {c8.x, c8.y};
-        uint32_t w[2];
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-          uint32_t x = 0;
-#pragma unroll
-          for (int r = 0; r < 4; r++) {
-            const int ar = (src[q] >> (8 * r)) & 0xff;
-            x |= (uint32_t)(uint8_t)tab[ar * NCODE + b] << (8 * r);
-          }
-          w[q] = x;
-        }
-        *reinterpret_cast<uint32_t*>(nprof + e * 4) = w[0];
-        *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = w[1];
+        *reinterpret_cast<uint32_t*>(nprof + e * 4) = pack4(c8.x, tab, b);
+        *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = pack4(c8.y, tab, b);
       }
       __syncthreads();
 
@@ -370,7 +497,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
         uint32_t s[4], m[4];
 #pragma unroll
         for (int w = 0; w < 4; w++) s[w] = m[w] = 0;
-        cell_pairs<0, 4, 4>(my_nrow, nprof, s, m);
+        narrow_pairs<0>(my_nrow, nprof, s, m);
         emit_hits<4>(m, vok, rows, u0, v, a, s1x2, lane, my_wk, my_wv, wcnt);
       }
     }
@@ -382,19 +509,51 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   }
 }
 
-cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
+namespace {
+std::atomic<int> g_variant{-1};  // index into UNG_N16 (-1: the default)
+constexpr int UNG_N16[UNG_VARIANTS] = {0, 12, 14, 16, UNG_MAX_N16};
+constexpr int UNG_DEFAULT_VARIANT = 2;
+
+template <int N16>
+cudaError_t launch_variant(const UngArgs& a, int grid, cudaStream_t st) {
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_ungapped, cudaFuncAttributeMaxDynamicSharedMemorySize, UNG_SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_ungapped<N16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide<N16>::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   if (grid <= 0) return cudaSuccess;
   note_launch();
-  k_ungapped<<<grid, UNG_THREADS, UNG_SMEM, st>>>(a);
+  k_ungapped<N16><<<grid, UNG_THREADS, Wide<N16>::SMEM, st>>>(a);
   return cudaGetLastError();
+}
+}  // namespace
+
+int ungapped_variant() {
+  const int v = g_variant.load();
+  return v < 0 ? UNG_DEFAULT_VARIANT : v;
+}
+
+int ungapped_variant_n16(int v) { return v >= 0 && v < UNG_VARIANTS ? UNG_N16[v] : -1; }
+
+void set_ungapped_variant(int v) { g_variant.store(v); }
+
+cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
+  switch (ungapped_variant()) {
+    case 0:
+      return launch_variant<UNG_N16[0]>(a, grid, st);
+    case 1:
+      return launch_variant<UNG_N16[1]>(a, grid, st);
+    case 3:
+      return launch_variant<UNG_N16[3]>(a, grid, st);
+    case 4:
+      return launch_variant<UNG_N16[4]>(a, grid, st);
+    default:
+      return launch_variant<UNG_N16[2]>(a, grid, st);
+  }
 }
 
 // ---------------------------------------------------------------------------

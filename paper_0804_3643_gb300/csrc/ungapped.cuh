@@ -27,7 +27,13 @@ struct UngArgs {
   int32_t sh;               // bits of a bank-2 padded position
 };
 
-size_t ungapped_smem_bytes();
+// Wide-tile variants of the stage-2 kernel: how many cells the profile holds
+// as int16 (UNG_N16 in ungapped.cu: 0, 12, 14, 16, UNG_MAX_N16).
+constexpr int UNG_VARIANTS = 5;
+constexpr int UNG_MAX_N16 = 18;
+int ungapped_variant();            // the variant launch_ungapped runs
+int ungapped_variant_n16(int v);   // its int16 cells (-1 for no such variant)
+void set_ungapped_variant(int v);  // -1: the default
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
                                const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,

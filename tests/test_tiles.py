@@ -24,7 +24,7 @@ def offsets(counts):
 def costs():
     B.lib()
     saved = B.plast_get_tile_costs()
-    c = dict(wide_slot=0.5, wide_tile=4000.0, narrow_slot=0.6, narrow_tile=1000.0)
+    c = dict(wide_slot=0.5, wide_tile=4000.0, narrow_slot=0.6, narrow_tile=1000.0, wide_int16_cells=14)
     B.plast_set_tile_costs(c)
     yield c
     B.plast_set_tile_costs(saved)
