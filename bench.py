@@ -136,10 +136,10 @@ def oracle_step(oracle, o1, o2, keys, threads):
     return len(h)
 
 
-def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int):
+def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads: int | None = None):
     import oracle
 
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.time()
     o1 = oracle.make_bank(b1.codes, b1.seq_off)
     o2 = oracle.make_bank(b2.codes, b2.seq_off)
@@ -365,7 +365,8 @@ def run_gpu(args, rank, world, local_rank):
         "dtype": "int16",
         "data": "synthetic",
         "config": {
-            "workload": f"PLAST-P full scale: {b1.n_seqs} x {b2.n_seqs} synthetic proteins "
+            "workload": f"PLAST-P {'full scale' if args.scale == 1.0 and not args.bank2_proteins else 'reduced'}: "
+                        f"{b1.n_seqs} x {b2.n_seqs} synthetic proteins "
                         f"({len(b1.codes)} / {len(b2.codes)} residues), 5% planted homologs, seed 1",
             "step": "index both banks + ungapped all pairs + sort + small gapped",
             "pairs_per_step": pairs,
@@ -611,6 +612,7 @@ def main():
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_key"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-threads", type=int, default=None, help="oracle threads (default: every host core)")
     ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow"],
                     help="stage-2 tile shapes: by measured cost (default) or forced")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile costs")
@@ -635,12 +637,13 @@ def main():
             return
         b1, b2 = synth.workload(WORKLOAD, seed=1, scale=args.scale)
         per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-        cb = run_oracle(b1, b2, per_step, args.steps, args.warmup)
+        cb = run_oracle(b1, b2, per_step, args.steps, args.warmup, args.cpu_threads)
         line = {
             "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"PLAST-P full scale: {b1.n_seqs} x {b2.n_seqs} synthetic proteins, seed 1",
+            "config": {"workload": f"PLAST-P {'full scale' if args.scale == 1.0 else 'reduced'}: "
+                                   f"{b1.n_seqs} x {b2.n_seqs} synthetic proteins, seed 1",
                        "step": "CPU oracle: stages 1-2 and 3.1 over a bounded random sample of keys"},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -664,7 +667,7 @@ def main():
     result, banks = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0)
+            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0, args.cpu_threads)
             result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -124,7 +124,7 @@ int num_sms() {
 // shape's rows x n2 rounded up to that granularity.  Defaults from a GB300;
 // plast_autotune measures them on the current device.
 std::mutex g_cost_mu;
-plast_tile_costs g_costs = {0.320, 5500.0, 0.525, 633.0, 14, 0};
+plast_tile_costs g_costs = {0.317, 4983.0, 0.512, 325.0, 12, 0};
 std::atomic<int> g_shape{0};  // 0: by cost, 1: wide only, 2: narrow only
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
 constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tile

@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
 namespace {
 std::atomic<int> g_variant{-1};  // index into UNG_N16 (-1: the default)
 constexpr int UNG_N16[UNG_VARIANTS] = {0, 12, 14, 16, UNG_MAX_N16};
-constexpr int UNG_DEFAULT_VARIANT = 2;
+constexpr int UNG_DEFAULT_VARIANT = 1;
 
 template <int N16>
 cudaError_t launch_variant(const UngArgs& a, int grid, cudaStream_t st) {
