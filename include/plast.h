@@ -263,28 +263,33 @@ int plast_set_schedule(int mode);
 /*
  * Stage-2 tile shapes.  The work of a key is cut into tiles of consecutive
  * bank-1 occurrences: wide tiles of 128 rows, whose profile serves 4 bank-2
- * windows per warp, and narrow tiles of 8 rows, one bank-2 window per lane,
- * for short lists (a small query bank against a large one, the end of a long
- * list).  The library picks, per key, the shape of the remainder after the
- * full wide tiles from a cost model: a tile of shape S costs
+ * windows per warp, and narrow tiles of 8, 4 or 2 rows, one bank-2 window
+ * per lane, for short lists (a small query bank against a large one, the end
+ * of a long list).  After the full wide tiles of a key, the library covers
+ * the remainder either with one wide tile or with narrow tiles (8 rows while
+ * 8 or more remain, the last 1-7 rows by the cheapest cover with 8, 4 and 2
+ * rows), from a cost model: a tile of shape S costs
  * S_slot x (rows of S) x ceil(n2 / P_S) x P_S + S_tile SM-nanoseconds, n2 the
  * key's bank-2 occurrences, P_S the bank-2 windows a CTA scores per pass
- * (128 wide, 1024 narrow).  plast_autotune measures the four constants on
- * the current device (random banks, the stage-2 kernel timed with every tile
- * wide, then every tile narrow, against a long and a short bank 2; about a
- * second),
- * installs them and copies them to *out (may be NULL).  It also picks the
- * wide kernel variant, how many cells of the wide profile are held as int16
- * (no sign extension, twice the shared-memory traffic), by timing each.
+ * (128 wide, 1024 narrow).  plast_autotune measures the constants on the
+ * current device (random banks, the stage-2 kernel timed with every tile of
+ * one shape, against a long and a short bank 2; about a second), installs
+ * them and copies them to *out (may be NULL).  It also picks the wide kernel
+ * variant, how many cells of the wide profile are held as int16 (no sign
+ * extension, twice the shared-memory traffic), by timing each.
  * plast_get_tile_costs / plast_set_tile_costs read and install costs and
  * variant (for a cached calibration; PLAST_E_INVALID unless the slot costs
  * are positive, the tile costs non-negative and wide_int16_cells one of the
- * variants).  plast_set_tile_shape forces the shape of every tile
- * (1 wide, 2 narrow; 0, the default, by cost).  Shapes change the schedule,
- * never the results.  Settings are process-wide and apply to later calls.
+ * variants).  plast_set_tile_shape forces the shape of every tile (1 wide;
+ * 2, 3, 4 narrow of 8, 4, 2 rows; 0, the default, by cost).  Shapes change
+ * the schedule, never the results.  Settings are process-wide and apply to
+ * later calls.
  */
 typedef struct plast_tile_costs {
-  double wide_slot, wide_tile, narrow_slot, narrow_tile;
+  double wide_slot, wide_tile;       /* 128 rows */
+  double narrow_slot, narrow_tile;   /* 8 rows */
+  double narrow4_slot, narrow4_tile; /* 4 rows */
+  double narrow2_slot, narrow2_tile; /* 2 rows */
   int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14, 16 or 18) */
   int32_t reserved;         /* 0 */
 } plast_tile_costs;
@@ -297,7 +302,7 @@ int plast_set_tile_shape(int mode);
  * CSR key offsets (host arrays of PLAST_NKEYS + 1 entries each, as
  * plast_bank_export_index returns): host-only, no device needed.  Fills
  * tiles[4 * t ..] with (key, first bank-1 CSR index, rows, shape: 0 wide,
- * 1 narrow) in launch order for t < *n_tiles; PLAST_E_CAPACITY if more than
+ * 1, 2, 3 narrow of 8, 4, 2 rows) in launch order for t < *n_tiles; PLAST_E_CAPACITY if more than
  * `cap` tiles (then *n_tiles = needed), PLAST_E_INVALID on decreasing offsets.
  */
 int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t* tiles, int64_t cap,

@@ -43,8 +43,12 @@ class plast_params(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+COST_FIELDS = ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile", "narrow4_slot", "narrow4_tile",
+               "narrow2_slot", "narrow2_tile")
+
+
 class plast_tile_costs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")] + \
+    _fields_ = [(n, ctypes.c_double) for n in COST_FIELDS] + \
         [("wide_int16_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
@@ -203,15 +207,16 @@ def plast_get_tile_costs() -> dict:
 
 
 def plast_set_tile_costs(costs: dict) -> None:
-    c = plast_tile_costs(**{k: float(costs[k]) for k in ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile")},
-                         wide_int16_cells=int(costs.get("wide_int16_cells", 14)))
+    c = plast_tile_costs(**{k: float(costs[k]) for k in COST_FIELDS},
+                         wide_int16_cells=int(costs.get("wide_int16_cells", 12)))
     rc = lib().plast_set_tile_costs(ctypes.byref(c))
     if rc:
         raise PlastError("plast_set_tile_costs", rc)
 
 
 def plast_set_tile_shape(mode: int) -> None:
-    """0: by cost (default), 1: every tile wide, 2: every tile narrow."""
+    """0: by cost (default), 1: every tile wide, 2 / 3 / 4: every tile narrow
+    of 8 / 4 / 2 rows."""
     rc = lib().plast_set_tile_shape(int(mode))
     if rc:
         raise PlastError("plast_set_tile_shape", rc)

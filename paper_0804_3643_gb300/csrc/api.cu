@@ -119,23 +119,58 @@ int num_sms() {
 
 // Stage-2 tile costs in SM-nanoseconds: per slot (a bank-1 row of the tile's
 // shape against a bank-2 window: 48 cells, whatever the tile's fill) and per
-// tile.  A CTA moves through a key's bank-2 windows WINDOWS_PER_PASS at a
-// time (32 warps x 4 windows wide, x 32 narrow), so a tile is charged its
-// shape's rows x n2 rounded up to that granularity.  Defaults from a GB300;
-// plast_autotune measures them on the current device.
+// tile.  A CTA moves through a key's bank-2 windows a pass at a time (32 warps
+// x 4 windows wide, x 32 narrow), so a tile is charged its shape's rows x n2
+// rounded up to that granularity.  Defaults from a GB300; plast_autotune
+// measures them on the current device.
 std::mutex g_cost_mu;
-plast_tile_costs g_costs = {0.317, 4983.0, 0.512, 325.0, 12, 0};
-std::atomic<int> g_shape{0};  // 0: by cost, 1: wide only, 2: narrow only
+plast_tile_costs g_costs = {0.317, 4983.0, 0.512, 325.0, 0.64, 300.0, 0.95, 300.0, 12, 0};
+// 0: by cost; 1: wide only; 2, 3, 4: narrow tiles of 8, 4, 2 rows only
+std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
-constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tile
+constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tiles
 int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) / g * g; }
+
+int shape_rows(int shape) {
+  switch (shape) {
+    case UNG_WIDE:
+      return UNG_T1;
+    case UNG_NARROW:
+      return UNG_NT1;
+    case UNG_NARROW4:
+      return UNG_NT1 / 2;
+    default:
+      return UNG_NT1 / 4;
+  }
+}
+
+double shape_slots(int shape, int64_t n2) {
+  return (double)shape_rows(shape) * (double)round_up(n2, shape == UNG_WIDE ? WIDE_PASS : NARROW_PASS);
+}
+
+double tile_cost(const plast_tile_costs& c, int shape, int64_t n2) {
+  const double slots = shape_slots(shape, n2);
+  switch (shape) {
+    case UNG_WIDE:
+      return c.wide_slot * slots + c.wide_tile;
+    case UNG_NARROW:
+      return c.narrow_slot * slots + c.narrow_tile;
+    case UNG_NARROW4:
+      return c.narrow4_slot * slots + c.narrow4_tile;
+    default:
+      return c.narrow2_slot * slots + c.narrow2_tile;
+  }
+}
 
 // Stage-2 work list: for every key present in both banks, tiles of
 // consecutive bank-1 occurrences.  Full wide tiles of UNG_T1 rows; the
-// remainder (or a short list) goes to one wide tile or to narrow tiles of
-// UNG_NT1 rows, whichever the cost model says is cheaper.
+// remainder (or a short list) goes to one wide tile or to narrow tiles,
+// whichever the cost model says is cheaper: narrow tiles of 8 rows while 8
+// or more rows remain, the last 1-7 rows by the cheapest cover with tiles of
+// 8, 4 and 2 rows.
 struct TileList {
   std::vector<int4> tiles;        // (key, first CSR index of bank 1, rows, shape)
+  int64_t n_wide = 0;             // persistent order: the wide tiles come first
   int64_t pairs = 0;
 };
 
@@ -148,38 +183,107 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     std::lock_guard<std::mutex> lk(g_cost_mu);
     c = g_costs;
   }
-  const int shape = shape_override >= 0 ? shape_override : g_shape.load();
+  const int mode = shape_override >= 0 ? shape_override : g_shape.load();
   std::vector<std::pair<double, int4>> w;
+  auto emit = [&](int k, int64_t first, int64_t rows, int shape, int64_t n2) {
+    w.push_back({tile_cost(c, shape, n2), make_int4(k, (int)first, (int)rows, shape)});
+  };
   for (int k = 0; k < NKEYS; k++) {
     if (key_mask && !(*key_mask)[k]) continue;
     const int64_t n1 = ko1[k + 1] - ko1[k];
     const int64_t n2 = ko2[k + 1] - ko2[k];
     if (n1 == 0 || n2 == 0) continue;
     tl->pairs += n1 * n2;
-    const int64_t first = ko1[k];
-    const double cost_w = c.wide_slot * UNG_T1 * (double)round_up(n2, WIDE_PASS) + c.wide_tile;
-    const double cost_n = c.narrow_slot * UNG_NT1 * (double)round_up(n2, NARROW_PASS) + c.narrow_tile;
-    int64_t u = 0;
-    if (shape != 2)
-      for (; n1 - u >= UNG_T1; u += UNG_T1) w.push_back({cost_w, make_int4(k, (int)(first + u), UNG_T1, UNG_WIDE)});
-    const int64_t rem = n1 - u;
+    int64_t u = ko1[k];
+    const int64_t end = ko1[k + 1];
+    if (mode >= 2) {  // one narrow shape only
+      const int shape = mode - 1, r = shape_rows(shape);
+      for (; u < end; u += r) emit(k, u, std::min<int64_t>(r, end - u), shape, n2);
+      continue;
+    }
+    for (; end - u >= UNG_T1; u += UNG_T1) emit(k, u, UNG_T1, UNG_WIDE, n2);
+    const int64_t rem = end - u;
     if (rem <= 0) continue;
-    const int64_t n_narrow = (rem + UNG_NT1 - 1) / UNG_NT1;
-    const bool narrow = shape == 2 || (shape == 0 && (double)n_narrow * cost_n < cost_w);
-    if (!narrow) {
-      for (; u < n1; u += UNG_T1)
-        w.push_back({cost_w, make_int4(k, (int)(first + u), (int)std::min<int64_t>(UNG_T1, n1 - u), UNG_WIDE)});
-    } else {
-      for (; u < n1; u += UNG_NT1)
-        w.push_back({cost_n, make_int4(k, (int)(first + u), (int)std::min<int64_t>(UNG_NT1, n1 - u), UNG_NARROW)});
+    if (mode == 1) {
+      emit(k, u, rem, UNG_WIDE, n2);
+      continue;
+    }
+    // cheapest cover of the last t rows (t < 8) by narrow tiles of 8, 4, 2
+    const double c8 = tile_cost(c, UNG_NARROW, n2), c4 = tile_cost(c, UNG_NARROW4, n2),
+                 c2 = tile_cost(c, UNG_NARROW2, n2);
+    double best[UNG_NT1];
+    int pick[UNG_NT1];
+    best[0] = 0;
+    pick[0] = 0;
+    for (int t = 1; t < UNG_NT1; t++) {
+      best[t] = c8;
+      pick[t] = UNG_NARROW;
+      const double v4 = c4 + best[std::max(t - 4, 0)], v2 = c2 + best[std::max(t - 2, 0)];
+      if (v4 < best[t]) best[t] = v4, pick[t] = UNG_NARROW4;
+      if (v2 < best[t]) best[t] = v2, pick[t] = UNG_NARROW2;
+    }
+    const int64_t full8 = rem / UNG_NT1;
+    const int tail = (int)(rem % UNG_NT1);
+    const double narrow_cost = (double)full8 * c8 + best[tail];
+    if (!(narrow_cost < tile_cost(c, UNG_WIDE, n2))) {
+      emit(k, u, rem, UNG_WIDE, n2);
+      continue;
+    }
+    for (int64_t i = 0; i < full8; i++, u += UNG_NT1) emit(k, u, UNG_NT1, UNG_NARROW, n2);
+    for (int t = tail; t > 0;) {
+      const int shape = pick[t], r = std::min(shape_rows(shape), t);
+      emit(k, u, r, shape, n2);
+      u += r;
+      t -= r;
     }
   }
-  if (largest_first)
+  if (largest_first) {
+    // wide tiles, then narrow ones (two launches), each costliest first
     std::stable_sort(w.begin(), w.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+      const bool wx = x.second.w == UNG_WIDE, wy = y.second.w == UNG_WIDE;
+      if (wx != wy) return wx;
       return x.first > y.first;
     });
+  }
   tl->tiles.reserve(w.size());
-  for (auto& x : w) tl->tiles.push_back(x.second);
+  tl->n_wide = 0;
+  for (auto& x : w) {
+    tl->tiles.push_back(x.second);
+    tl->n_wide += x.second.w == UNG_WIDE;
+  }
+}
+
+// Queues stage 2 over the tile list (its device copy is a.tiles): in the
+// persistent schedule the wide kernel over the wide tiles and the narrow
+// kernel over the rest, each on its own counter (counters[0], counters[1],
+// zeroed by the caller); in the plain schedule, per key one launch of each
+// kernel its tiles need.
+cudaError_t launch_tiles(const TileList& tl, UngArgs a, int32_t* counters, bool persistent, cudaStream_t st) {
+  const int64_t nt = (int64_t)tl.tiles.size();
+  auto run = [&](int64_t lo, int64_t hi, bool wide, int32_t* counter) -> cudaError_t {
+    if (hi <= lo) return cudaSuccess;
+    a.tile_base = (int32_t)lo;
+    a.n_tiles = (int32_t)(hi - lo);
+    a.tile_counter = counter;
+    a.persistent = persistent ? 1 : 0;
+    const int grid = persistent ? (int)std::min<int64_t>(num_sms(), hi - lo) : (int)(hi - lo);
+    return wide ? launch_ungapped(a, grid, st) : launch_ungapped_narrow(a, grid, st);
+  };
+  if (persistent) {
+    cudaError_t e = run(0, tl.n_wide, true, counters);
+    return e != cudaSuccess ? e : run(tl.n_wide, nt, false, counters + 1);
+  }
+  for (int64_t i = 0; i < nt;) {
+    int64_t j = i;
+    while (j < nt && tl.tiles[j].x == tl.tiles[i].x && tl.tiles[j].w == UNG_WIDE) j++;
+    int64_t k = j;
+    while (k < nt && tl.tiles[k].x == tl.tiles[i].x) k++;
+    cudaError_t e = run(i, j, true, counters);
+    if (e == cudaSuccess) e = run(j, k, false, counters + 1);
+    if (e != cudaSuccess) return e;
+    i = k;
+  }
+  return cudaSuccess;
 }
 
 void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl,
@@ -213,7 +317,7 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
   int32_t* d_counter;
   unsigned long long* d_count;
   CK(sc.get(&d_tiles, nt));
-  CK(sc.get(&d_counter, 1));
+  CK(sc.get(&d_counter, 2));
   CK(sc.get(&d_count, 1));
   CK(cudaMemcpyAsync(d_tiles, tl.tiles.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
 
@@ -223,7 +327,7 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
     uint32_t *v0, *v1;
     CK(sc.get(&k0, cap));
     CK(sc.get(&v0, cap));
-    CK(cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d_counter, 0, 2 * sizeof(int32_t), st));
     CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     UngArgs a;
     a.nb1 = b1->nb;
@@ -240,23 +344,7 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
     a.cap = cap;
     a.sh = sv->sh;
     t_timer.mark(1, st);
-    if (mode == 0) {
-      a.persistent = 1;
-      a.tile_base = 0;
-      a.n_tiles = (int32_t)nt;
-      CK(launch_ungapped(a, (int)std::min<int64_t>(num_sms(), nt), st));
-    } else {
-      a.persistent = 0;
-      int64_t i = 0;
-      while (i < nt) {
-        int64_t j = i;
-        while (j < nt && tl.tiles[j].x == tl.tiles[i].x) j++;
-        a.tile_base = (int32_t)i;
-        a.n_tiles = (int32_t)(j - i);
-        CK(launch_ungapped(a, (int)(j - i), st));
-        i = j;
-      }
-    }
+    CK(launch_tiles(tl, a, d_counter, mode == 0, st));
     t_timer.mark(2, st);
     unsigned long long n = 0;
     CK(cudaMemcpyAsync(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost, st));
@@ -768,6 +856,7 @@ struct plast_plan {
   plast_params prm{};
   int device = 0;
   int64_t max_hits = 0, max_records = 0, n_tiles = 0;
+  TileList tl;  // host copy of the work list (launch split)
   int sh = 0, bits = 0;
   int4* tiles = nullptr;
   int32_t* counter = nullptr;
@@ -829,7 +918,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
     plast_plan_free(p);
     return rc_of(e);
   };
-  TileList tl;
+  TileList& tl = p->tl;
   build_tiles(b1, b2, true, &tl);
   p->n_tiles = (int64_t)tl.tiles.size();
   cudaError_t e;
@@ -837,7 +926,8 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   p->rtb = radix_tmp_bytes(max_records);
   p->stb = scan_tmp_bytes(max_hits);
   if ((e = alloc((void**)&p->tiles, sizeof(int4) * (size_t)std::max<int64_t>(p->n_tiles, 1))) ||
-      (e = alloc((void**)&p->counter, sizeof(int32_t))) || (e = alloc((void**)&p->count, sizeof(unsigned long long))) ||
+      (e = alloc((void**)&p->counter, 2 * sizeof(int32_t))) ||
+      (e = alloc((void**)&p->count, sizeof(unsigned long long))) ||
       (e = alloc((void**)&p->n_dev, sizeof(int64_t))) || (e = alloc((void**)&p->m_dev, sizeof(int64_t))) ||
       (e = alloc((void**)&p->k0, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->v0, 4 * (size_t)max_hits)) ||
       (e = alloc((void**)&p->rk0, 8 * (size_t)max_records)) || (e = alloc((void**)&p->rk1, 8 * (size_t)max_records)) ||
@@ -854,7 +944,9 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   UngArgs none{};
   GapArgs gnone{};
   gnone.n = 0;
-  if ((e = launch_ungapped(none, 0, st)) || (e = launch_small_gapped(gnone, st))) return fail(e);
+  if ((e = launch_ungapped(none, 0, st)) || (e = launch_ungapped_narrow(none, 0, st)) ||
+      (e = launch_small_gapped(gnone, st)))
+    return fail(e);
   if ((e = cudaStreamSynchronize(st))) return fail(e);
   *out = p;
   return PLAST_OK;
@@ -863,7 +955,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
 int plast_plan_run(plast_plan* p, void* stream) {
   if (!p) return PLAST_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(p->counter, 0, sizeof(int32_t), st));
+  CK(cudaMemsetAsync(p->counter, 0, 2 * sizeof(int32_t), st));
   CK(cudaMemsetAsync(p->count, 0, sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(p->total, 0, sizeof(int64_t), st));
   if (p->n_tiles > 0) {
@@ -884,7 +976,7 @@ int plast_plan_run(plast_plan* p, void* stream) {
     a.out_count = p->count;
     a.cap = p->max_hits;
     a.sh = p->sh;
-    CK(launch_ungapped(a, (int)std::min<int64_t>(num_sms(), p->n_tiles), st));
+    CK(launch_tiles(p->tl, a, p->counter, true, st));
   }
   CK(launch_clamp_count(p->count, p->max_hits, p->n_dev, st));
   GapArgs g;
@@ -1009,8 +1101,7 @@ int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStrea
   *slots = 0;
   for (const int4& t : tl.tiles) {
     const int64_t n2 = b2->h_key_off[t.x + 1] - b2->h_key_off[t.x];
-    *slots += t.w == UNG_WIDE ? (double)UNG_T1 * (double)round_up(n2, WIDE_PASS)
-                              : (double)UNG_NT1 * (double)round_up(n2, NARROW_PASS);
+    *slots += shape_slots(t.w, n2);
   }
   *tiles = (double)tl.tiles.size();
   *ms = 0;
@@ -1023,7 +1114,7 @@ int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStrea
   uint32_t* v0;
   const int64_t cap = tl.pairs / 64 + (1 << 16);
   CK(sc.get(&d_tiles, tl.tiles.size()));
-  CK(sc.get(&d_counter, 1));
+  CK(sc.get(&d_counter, 2));
   CK(sc.get(&d_count, 1));
   CK(sc.get(&k0, cap));
   CK(sc.get(&v0, cap));
@@ -1056,10 +1147,10 @@ int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStrea
   std::vector<float> t;
   cudaError_t e = cudaSuccess;
   for (int r = 0; r <= reps && e == cudaSuccess; r++) {
-    e = cudaMemsetAsync(d_counter, 0, sizeof(int32_t), st);
+    e = cudaMemsetAsync(d_counter, 0, 2 * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    if (e == cudaSuccess) e = launch_ungapped(a, (int)std::min<int64_t>(num_sms(), tl.tiles.size()), st);
+    if (e == cudaSuccess) e = launch_tiles(tl, a, d_counter, true, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float x = 0;
@@ -1088,9 +1179,11 @@ int plast_get_tile_costs(plast_tile_costs* out) {
 }
 
 int plast_set_tile_costs(const plast_tile_costs* c) {
-  if (!c || !(c->wide_slot > 0) || !(c->narrow_slot > 0) || !(c->wide_tile >= 0) || !(c->narrow_tile >= 0) ||
-      c->wide_slot > 1e6 || c->narrow_slot > 1e6 || c->wide_tile > 1e12 || c->narrow_tile > 1e12)
-    return PLAST_E_INVALID;
+  if (!c) return PLAST_E_INVALID;
+  const double slot[4] = {c->wide_slot, c->narrow_slot, c->narrow4_slot, c->narrow2_slot};
+  const double tile[4] = {c->wide_tile, c->narrow_tile, c->narrow4_tile, c->narrow2_tile};
+  for (int i = 0; i < 4; i++)
+    if (!(slot[i] > 0) || !(tile[i] >= 0) || slot[i] > 1e6 || tile[i] > 1e12) return PLAST_E_INVALID;
   int variant = -1;
   for (int v = 0; v < UNG_VARIANTS; v++)
     if (ungapped_variant_n16(v) == c->wide_int16_cells) variant = v;
@@ -1122,7 +1215,7 @@ int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t
 }
 
 int plast_set_tile_shape(int mode) {
-  if (mode < 0 || mode > 2) return PLAST_E_INVALID;
+  if (mode < 0 || mode > 4) return PLAST_E_INVALID;
   g_shape.store(mode);
   return PLAST_OK;
 }
@@ -1173,10 +1266,10 @@ int plast_autotune(void* stream, plast_tile_costs* out) {
     }
   }
   set_ungapped_variant(rc == PLAST_OK ? best_v : saved_variant);
-  if (rc == PLAST_OK) {
-    double t_long;
-    rc = fit(2, &c.narrow_slot, &c.narrow_tile, &t_long);
-  }
+  double t_long;
+  if (rc == PLAST_OK) rc = fit(2, &c.narrow_slot, &c.narrow_tile, &t_long);
+  if (rc == PLAST_OK) rc = fit(3, &c.narrow4_slot, &c.narrow4_tile, &t_long);
+  if (rc == PLAST_OK) rc = fit(4, &c.narrow2_slot, &c.narrow2_tile, &t_long);
   plast_bank_free(b1);
   plast_bank_free(b2l);
   plast_bank_free(b2s);

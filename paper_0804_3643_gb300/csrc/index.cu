@@ -71,25 +71,41 @@ __global__ void k_key_offsets(const uint64_t* skey, int64_t n, int64_t* key_off)
   }
 }
 
+// 16 bytes of pad from address s forwards (byte 0 = pad[s]), from aligned
+// words; pad has slack on both sides, so the rounded reads stay inside it.
+__device__ __forceinline__ uint4 bytes16_fwd(const int8_t* pad, int64_t s) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(pad + (s & ~(int64_t)3));
+  const uint32_t sh = 8u * (uint32_t)(s & 3);
+  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
+  return make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                    __funnelshift_r(w3, w4, sh));
+}
+
+// 16 bytes of pad from address s backwards (byte 0 = pad[s], byte 1 = pad[s-1], ...)
+__device__ __forceinline__ uint4 bytes16_bwd(const int8_t* pad, int64_t s) {
+  const uint4 f = bytes16_fwd(pad, s - 15);
+  return make_uint4(__byte_perm(f.w, 0u, 0x0123u), __byte_perm(f.z, 0u, 0x0123u), __byte_perm(f.y, 0u, 0x0123u),
+                    __byte_perm(f.x, 0u, 0x0123u));
+}
+
+// Window of indexed word i: cells 0..25 = pad[p .. p+25], cells 26..47 =
+// pad[p-1], pad[p-2], .., pad[p-22]; one thread per 16-byte chunk.
 __global__ void k_neighbourhoods(const int8_t* pad, const uint32_t* pos, int64_t n, int8_t* nb) {
-  // one thread per 16-byte chunk of a 48-byte window
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * n; t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t / 3;
-    int c0 = (int)(t - i * 3) * 16;
-    int64_t p = pos[i];
-    uint32_t w[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      uint32_t x = 0;
-#pragma unroll
-      for (int b = 0; b < 4; b++) {
-        int c = c0 + q * 4 + b;
-        int64_t src = c < RIGHT ? p + c : p - (c - RIGHT + 1);
-        x |= (uint32_t)(uint8_t)pad[src] << (8 * b);
-      }
-      w[q] = x;
+    const int64_t i = t / 3;
+    const int part = (int)(t - i * 3);
+    const int64_t p = pos[i];
+    uint4 out;
+    if (part == 0) {
+      out = bytes16_fwd(pad, p);  // cells 0-15
+    } else if (part == 1) {
+      const uint4 f = bytes16_fwd(pad, p + 16);  // cells 16-25: bytes 0-9
+      const uint4 b = bytes16_bwd(pad, p - 1);   // cells 26-31: bytes 0-5
+      out = make_uint4(f.x, f.y, __byte_perm(f.z, b.x, 0x5410u), __byte_perm(b.x, b.y, 0x5432u));
+    } else {
+      out = bytes16_bwd(pad, p - 7);  // cells 32-47
     }
-    reinterpret_cast<uint4*>(nb)[t] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4*>(nb)[t] = out;
   }
 }
 

@@ -11,7 +11,8 @@
 // and maxima (exact: |sum| <= 48 * 32 < 2^15).  After cell 25 the sums restart
 // from the maxima (the reset of Annex 4).
 //
-// Two tile shapes share the kernel:
+// Two tile shapes, each in its own persistent kernel (k_ungapped<N16>,
+// k_ungapped_narrow), launched one after the other over the work list:
 //  * wide: up to 128 rows.  Lane (g, js) of a warp scores bank-2 window js
 //    (4 per warp) against rows 16g .. 16g+15; the 8 lanes of a window read
 //    one 128-byte profile row per cell, so a warp's loads come out of shared
@@ -27,13 +28,13 @@
 //    - N16 of the cells are stored as int16 (two 16-byte loads, no
 //      sign extension), trading shared-memory bandwidth, which has headroom,
 //      for ALU-pipe work, which has none; the rest are int8.
-//  * narrow: up to 8 rows, the profile in two planes of 4 rows, one 32-bit
-//    word per (k, b).  Every lane scores its own bank-2 window (32 per warp)
-//    against the 8 rows with two word loads per cell; the 22 words of a cell
-//    lie in 22 distinct banks, so 32 lanes with any residues read them in one
-//    wavefront.  It serves keys with few bank-1 occurrences (a small query
-//    bank against a large one, the remainder of a long list), where a wide
-//    tile would mostly score padding rows.
+//  * narrow: up to R = 8, 4 or 2 rows.  Every lane scores its own bank-2
+//    window (32 per warp) against the R rows: the profile holds one word per
+//    (k, b) and 4 rows (two planes for R = 8), or one halfword per (k, b) and
+//    2 rows; the 22 entries of a cell lie in distinct banks, so 32 lanes with
+//    any residues read them in one wavefront.  It serves short lists (a small
+//    query bank against a large one, the remainder of a long list), where a
+//    wide tile would mostly score padding rows.
 // The host picks the shape per key from measured per-cell and per-tile costs.
 //
 // Pipe balance on sm_103: byte and vector loads go to the LSU, IMAD and
@@ -42,8 +43,8 @@
 //
 // Hits (score >= s1) are staged in a per-warp shared buffer and flushed with
 // one global atomic per 64 records, as (padded pos1 << sh | padded pos2,
-// score).  Tiles come from a device counter (persistent launch, costliest
-// tile first) or, in the plain schedule, one launch per key.
+// score).  Tiles come from a device counter (persistent launches, costliest
+// tile first) or, in the plain schedule, one launch per key and shape.
 #include <atomic>
 
 #include "common.cuh"
@@ -81,13 +82,12 @@ struct Wide {
   __host__ __device__ static constexpr int plane8(int k) { return SEED_PLANES + (k - FIRST_CELL - N16); }
 };
 
-// narrow tiles overlay the wide profile
+// narrow tiles (their own kernel)
 constexpr int NSTRIDE = 52;                                // staged window stride: 13 words, conflict-free bytes
 constexpr int NPLANE = WIN * NCODE * 4;                     // 4224: one plane of 4 rows
 constexpr int NPROF_BYTES = 2 * NPLANE;                     // 8448
 constexpr int NROWS_BYTES = WIN * UNG_NT1;                 // 384, cell-major
 constexpr int NSTAGE_BYTES = NWARPS * 32 * NSTRIDE;        // 53248: one window per lane
-static_assert(NPROF_BYTES + NROWS_BYTES + NSTAGE_BYTES <= Wide<0>::PROF, "narrow tile fits the wide profile area");
 static_assert(NPROF_BYTES % 16 == 0 && NROWS_BYTES % 16 == 0 && (32 * NSTRIDE) % 16 == 0, "alignment");
 static_assert(Wide<UNG_MAX_N16>::SMEM <= 232448, "shared memory per CTA");
 
@@ -178,30 +178,50 @@ __device__ __forceinline__ void wide_pairs(uint32_t row, const unsigned char* pl
   }
 }
 
-// Cells K and K+1 of the lane's bank-2 window against its 8 narrow rows (rows
-// 0-3 the word at plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE
-// bytes further), then the following pairs (K = 0, 2, .., 46).
-template <int K>
-__device__ __forceinline__ void narrow_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[4],
-                                             uint32_t (&m)[4]) {
+// Cells K and K+1 of the lane's bank-2 window against its 2 * NW narrow rows,
+// then the following pairs (K = 0, 2, .., 46).  NW = 4: rows 0-3 the word at
+// plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE bytes further; NW = 2:
+// the word alone; NW = 1: rows 0-1 the halfword at plane + (k * NCODE + b) * 2.
+template <int NW>
+__device__ __forceinline__ void narrow_scores(const unsigned char* plane, int k, uint32_t b, uint32_t (&u)[NW]) {
+  if constexpr (NW == 1) {
+    uint32_t h;
+    asm("ld.shared.u16 %0, [%1];"
+        : "=r"(h)
+        : "r"((uint32_t)__cvta_generic_to_shared(plane + (k * NCODE + b) * 2)));
+    u[0] = sext_pair(h, 0);
+  } else {
+    const unsigned char* e = plane + (k * NCODE + b) * 4;
+    const uint32_t lo = *reinterpret_cast<const uint32_t*>(e);
+    u[0] = sext_pair(lo, 0);
+    u[1] = sext_pair(lo, 1);
+    if constexpr (NW == 4) {
+      const uint32_t hi = *reinterpret_cast<const uint32_t*>(e + NPLANE);
+      u[2] = sext_pair(hi, 0);
+      u[3] = sext_pair(hi, 1);
+    }
+  }
+}
+
+template <int K, int NW>
+__device__ __forceinline__ void narrow_pairs(uint32_t row, const unsigned char* plane, uint32_t (&s)[NW],
+                                             uint32_t (&m)[NW]) {
   if constexpr (K < WIN) {
     const uint32_t b0 = lds_u8<K>(row), b1 = lds_u8<K + 1>(row);
-    uint32_t u0[4], u1[4];
-    const unsigned char* e0 = plane + (K * NCODE + b0) * 4;
-    const unsigned char* e1 = plane + ((K + 1) * NCODE + b1) * 4;
-    unpack8(*reinterpret_cast<const uint32_t*>(e0), *reinterpret_cast<const uint32_t*>(e0 + NPLANE), u0);
-    unpack8(*reinterpret_cast<const uint32_t*>(e1), *reinterpret_cast<const uint32_t*>(e1 + NPLANE), u1);
+    uint32_t u0[NW], u1[NW];
+    narrow_scores<NW>(plane, K, b0, u0);
+    narrow_scores<NW>(plane, K + 1, b1, u1);
 #pragma unroll
-    for (int w = 0; w < 4; w++) {
+    for (int w = 0; w < NW; w++) {
       const uint32_t t0 = __vadd2(s[w], u0[w]);
       s[w] = __vadd2(t0, u1[w]);
       m[w] = __vimax3_s16x2(m[w], t0, s[w]);
     }
     if constexpr (K + 1 == RIGHT - 1) {
 #pragma unroll
-      for (int w = 0; w < 4; w++) s[w] = m[w];
+      for (int w = 0; w < NW; w++) s[w] = m[w];
     }
-    narrow_pairs<K + 2>(row, plane, s, m);
+    narrow_pairs<K + 2, NW>(row, plane, s, m);
   }
 }
 
@@ -212,13 +232,17 @@ template <int NW>
 __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int valid_rows, int64_t r0, int64_t v,
                                           const UngArgs& a, uint32_t s1x2, int lane, uint64_t* my_wk,
                                           uint32_t* my_wv, int& wcnt) {
-  uint32_t mx = __vimax3_s16x2(m[0], m[1], m[2]);
+  uint32_t mx = m[0];
   if constexpr (NW == 8) {
+    mx = __vimax3_s16x2(m[0], m[1], m[2]);
     mx = __vimax3_s16x2(mx, m[3], m[4]);
     mx = __vimax3_s16x2(mx, m[5], m[6]);
     mx = __vmaxs2(mx, m[7]);
-  } else {
+  } else if constexpr (NW == 4) {
+    mx = __vimax3_s16x2(m[0], m[1], m[2]);
     mx = __vmaxs2(mx, m[3]);
+  } else if constexpr (NW == 2) {
+    mx = __vmaxs2(m[0], m[1]);
   }
   const bool maybe = vok && __vcmpges2(mx, s1x2) != 0u;
   if (!__any_sync(0xffffffffu, maybe)) return;
@@ -305,6 +329,76 @@ __device__ __forceinline__ uint32_t pack4(uint32_t src, const int8_t* tab, int b
   return x;
 }
 
+// A narrow tile of 2 * NW rows: rows cell-major (nrows[k][r], stride 8),
+// the profile (NW = 4: planes nprof[p][k][b] of rows 4p .. 4p+3; NW = 2: one
+// plane; NW = 1: halfwords of rows 0-1), then every bank-2 window of the key
+// against it, one per lane.
+template <int NW>
+__device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t u0, int64_t v0, int64_t v1,
+                                            uint8_t* nrows, unsigned char* nprof, const int8_t* tab,
+                                            unsigned char* my_nstage, uint32_t my_nrow, uint32_t s1x2,
+                                            uint64_t* my_wk, uint32_t* my_wv, int& wcnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
+  for (int i = tid; i < NROWS_BYTES; i += UNG_THREADS) {
+    const int r = i & (UNG_NT1 - 1), k = i / UNG_NT1;
+    nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
+  }
+  __syncthreads();
+  for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
+    const int k = e / NCODE, b = e - k * NCODE;
+    const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + k * UNG_NT1);
+    if constexpr (NW == 1) {
+      const int a0 = c8.x & 0xff, a1 = (c8.x >> 8) & 0xff;
+      *reinterpret_cast<uint16_t*>(nprof + e * 2) =
+          (uint16_t)((uint8_t)tab[a0 * NCODE + b] | ((uint32_t)(uint8_t)tab[a1 * NCODE + b] << 8));
+    } else {
+      *reinterpret_cast<uint32_t*>(nprof + e * 4) = pack4(c8.x, tab, b);
+      if constexpr (NW == 4) *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = pack4(c8.y, tab, b);
+    }
+  }
+  __syncthreads();
+
+  // the warp's 32 windows are 96 consecutive 16-byte items; lane l moves
+  // items l, l + 32, l + 64 (window q / 3, part q % 3), one iteration ahead
+  int nw[3], np[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    nw[j] = (lane + 32 * j) / 3;
+    np[j] = (lane + 32 * j) % 3;
+  }
+  uint4 pre[3];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int64_t v = v0 + warp * 32 + nw[j];
+    pre[j] = v < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + np[j]) : sent16;
+  }
+  for (int64_t vb = v0 + warp * 32; vb < v1; vb += NWARPS * 32) {
+    const int64_t v = vb + lane;
+    const bool vok = v < v1;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      uint32_t* d = reinterpret_cast<uint32_t*>(my_nstage + nw[j] * NSTRIDE + np[j] * 16);
+      d[0] = pre[j].x;
+      d[1] = pre[j].y;
+      d[2] = pre[j].z;
+      d[3] = pre[j].w;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const int64_t vn = vb + NWARPS * 32 + nw[j];
+      pre[j] = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + np[j]) : sent16;
+    }
+    uint32_t s[NW], m[NW];
+#pragma unroll
+    for (int w = 0; w < NW; w++) s[w] = m[w] = 0;
+    narrow_pairs<0, NW>(my_nrow, nprof, s, m);
+    emit_hits<NW>(m, vok, rows, u0, v, a, s1x2, lane, my_wk, my_wv, wcnt);
+  }
+}
+
 template <int N16>
 __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   using L = Wide<N16>;
@@ -316,10 +410,6 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   uint64_t* wkey = reinterpret_cast<uint64_t*>(stage + STAGE_BYTES);
   uint32_t* wval = reinterpret_cast<uint32_t*>(stage + STAGE_BYTES + WKEY_BYTES);
   TileSlot* slots = reinterpret_cast<TileSlot*>(stage + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
-  // narrow-tile areas (inside the wide profile)
-  unsigned char* nprof = smem;
-  uint8_t* nrows = smem + NPROF_BYTES;
-  unsigned char* nstage = smem + NPROF_BYTES + NROWS_BYTES;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane & 7, js = lane >> 3;
@@ -327,8 +417,6 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   uint32_t* my_wv = wval + warp * WBUF;
   uint4* my_stage = reinterpret_cast<uint4*>(stage + warp * 4 * WIN);  // 12 x 16 bytes
   const uint32_t my_row = (uint32_t)__cvta_generic_to_shared(stage + warp * 4 * WIN + js * WIN);  // lane's window
-  unsigned char* my_nstage = nstage + warp * 32 * NSTRIDE;
-  const uint32_t my_nrow = (uint32_t)__cvta_generic_to_shared(my_nstage + lane * NSTRIDE);
   int wcnt = 0;  // warp-uniform fill of this warp's buffer
   const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
 
@@ -347,7 +435,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
     const int rows = tile.z;
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
 
-    if (tile.w == UNG_WIDE) {
+    {
       // bank-1 windows of the tile, transposed to cell-major (rowsT[k][r])
       for (int i = tid; i < ROWS_BYTES; i += UNG_THREADS) {
         const int r = i & (UNG_T1 - 1), k = i / UNG_T1;
@@ -446,61 +534,54 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
         emit_hits<8>(m, vok, rows - g * ROWS_PER_LANE, u0 + g * ROWS_PER_LANE, v, a, s1x2, lane, my_wk, my_wv,
                      wcnt);
       }
-    } else {
-      // narrow tile: rows cell-major (nrows[k][r]), profile planes
-      // nprof[p][k][b][r'] for rows 4p + r'
-      for (int i = tid; i < NROWS_BYTES; i += UNG_THREADS) {
-        const int r = i & (UNG_NT1 - 1), k = i / UNG_NT1;
-        nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
-      }
-      __syncthreads();
-      for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
-        const int k = e / NCODE, b = e - k * NCODE;
-        const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + k * UNG_NT1);
-        *reinterpret_cast<uint32_t*>(nprof + e * 4) = pack4(c8.x, tab, b);
-        *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = pack4(c8.y, tab, b);
-      }
-      __syncthreads();
-
-      // the warp's 32 windows are 96 consecutive 16-byte items; lane l moves
-      // items l, l + 32, l + 64 (window q / 3, part q % 3), one iteration ahead
-      int nw[3], np[3];
-#pragma unroll
-      for (int j = 0; j < 3; j++) {
-        nw[j] = (lane + 32 * j) / 3;
-        np[j] = (lane + 32 * j) % 3;
-      }
-      uint4 pre[3];
-#pragma unroll
-      for (int j = 0; j < 3; j++) {
-        const int64_t v = v0 + warp * 32 + nw[j];
-        pre[j] = v < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + np[j]) : sent16;
-      }
-      for (int64_t vb = v0 + warp * 32; vb < v1; vb += NWARPS * 32) {
-        const int64_t v = vb + lane;
-        const bool vok = v < v1;
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          uint32_t* d = reinterpret_cast<uint32_t*>(my_nstage + nw[j] * NSTRIDE + np[j] * 16);
-          d[0] = pre[j].x;
-          d[1] = pre[j].y;
-          d[2] = pre[j].z;
-          d[3] = pre[j].w;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          const int64_t vn = vb + NWARPS * 32 + nw[j];
-          pre[j] = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + np[j]) : sent16;
-        }
-        uint32_t s[4], m[4];
-#pragma unroll
-        for (int w = 0; w < 4; w++) s[w] = m[w] = 0;
-        narrow_pairs<0>(my_nrow, nprof, s, m);
-        emit_hits<4>(m, vok, rows, u0, v, a, s1x2, lane, my_wk, my_wv, wcnt);
-      }
     }
+    __syncthreads();  // the next tile rebuilds the profile
+  }
+  if (wcnt > 0) {
+    __syncwarp();
+    flush_warp(my_wk, my_wv, wcnt, lane, a.out_count, a.out_key, a.out_val, a.cap);
+  }
+}
+
+// Narrow tiles (8, 4 or 2 rows) in their own persistent kernel, so that the
+// wide kernel's registers and schedule are its own.
+constexpr int NARROW_SMEM = TAB_BYTES + NROWS_BYTES + NPROF_BYTES + NSTAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 2 * 48;
+static_assert((TAB_BYTES + NROWS_BYTES + NPROF_BYTES + NSTAGE_BYTES) % 16 == 0, "alignment");
+
+__global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped_narrow(UngArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int8_t* tab = reinterpret_cast<int8_t*>(smem);
+  uint8_t* nrows = smem + TAB_BYTES;
+  unsigned char* nprof = smem + TAB_BYTES + NROWS_BYTES;
+  unsigned char* nstage = smem + TAB_BYTES + NROWS_BYTES + NPROF_BYTES;
+  uint64_t* wkey = reinterpret_cast<uint64_t*>(nstage + NSTAGE_BYTES);
+  uint32_t* wval = reinterpret_cast<uint32_t*>(nstage + NSTAGE_BYTES + WKEY_BYTES);
+  TileSlot* slots = reinterpret_cast<TileSlot*>(nstage + NSTAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t* my_wk = wkey + warp * WBUF;
+  uint32_t* my_wv = wval + warp * WBUF;
+  unsigned char* my_nstage = nstage + warp * 32 * NSTRIDE;
+  const uint32_t my_nrow = (uint32_t)__cvta_generic_to_shared(my_nstage + lane * NSTRIDE);
+  int wcnt = 0;
+
+  for (int i = tid; i < NCODE * NCODE; i += UNG_THREADS) tab[i] = c_score[i];
+  const uint32_t s1x2 = ((uint32_t)(uint16_t)a.s1 << 16) | (uint16_t)a.s1;
+  if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : (int)blockIdx.x, &slots[0]);
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
+    if (slots[buf].t >= a.n_tiles) break;
+    const int4 tile = slots[buf].tile;
+    const int64_t v0 = slots[buf].v0, v1 = slots[buf].v1;
+    if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : a.n_tiles, &slots[buf ^ 1]);
+    const int rows = tile.z;
+    const int64_t u0 = (int64_t)(uint32_t)tile.y;
+    if (tile.w == UNG_NARROW)
+      narrow_tile<4>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
+    else if (tile.w == UNG_NARROW4)
+      narrow_tile<2>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
+    else
+      narrow_tile<1>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
     __syncthreads();  // the next tile rebuilds the profile
   }
   if (wcnt > 0) {
@@ -540,6 +621,21 @@ int ungapped_variant() {
 int ungapped_variant_n16(int v) { return v >= 0 && v < UNG_VARIANTS ? UNG_N16[v] : -1; }
 
 void set_ungapped_variant(int v) { g_variant.store(v); }
+
+cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st) {
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_ungapped_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, NARROW_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  if (grid <= 0) return cudaSuccess;
+  note_launch();
+  k_ungapped_narrow<<<grid, UNG_THREADS, NARROW_SMEM, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
   switch (ungapped_variant()) {

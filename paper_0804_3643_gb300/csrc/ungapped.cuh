@@ -4,9 +4,11 @@
 
 namespace plast {
 
-// tile shapes (ungapped.cu): rows per tile UNG_T1 (wide) or UNG_NT1 (narrow)
+// tile shapes (ungapped.cu): UNG_T1 rows (wide), UNG_NT1 = 8, 4 or 2 rows (narrow)
 constexpr int UNG_WIDE = 0;
 constexpr int UNG_NARROW = 1;
+constexpr int UNG_NARROW4 = 2;
+constexpr int UNG_NARROW2 = 3;
 
 struct UngArgs {
   const int8_t* nb1;        // bank-1 windows [n_idx1][48]
@@ -34,7 +36,9 @@ constexpr int UNG_MAX_N16 = 18;
 int ungapped_variant();            // the variant launch_ungapped runs
 int ungapped_variant_n16(int v);   // its int16 cells (-1 for no such variant)
 void set_ungapped_variant(int v);  // -1: the default
+// wide tiles (the current variant) / narrow tiles, each a persistent launch
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
                                const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
                                int32_t n2, plast_hit* out, int* bad, cudaStream_t st);

@@ -46,7 +46,7 @@ def test_host_only_entry_points(lib):
     with pytest.raises(B.PlastError):
         B.plast_set_schedule(7)
     with pytest.raises(B.PlastError):
-        B.plast_set_tile_shape(3)
+        B.plast_set_tile_shape(5)
     B.plast_set_tile_shape(0)
     c = B.plast_get_tile_costs()
     assert c["wide_slot"] > 0 and c["narrow_slot"] > 0

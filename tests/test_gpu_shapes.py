@@ -1,4 +1,4 @@
-"""Stage-2 tile shapes: wide-only, narrow-only and by-cost work lists give the
+"""Stage-2 tile shapes: wide-only, narrow-only (8, 4, 2 rows) and by-cost work lists give the
 oracle's hits and records bit for bit (shapes change the schedule, never the
 results), on the plain workload, a small query bank against a large bank
 (ragged narrow tiles), the low-complexity mix and the every-pair-passes case
@@ -40,7 +40,7 @@ def same(a, b):
 def each_shape(B, f):
     out = []
     try:
-        for shape in (1, 2, 0):
+        for shape in (1, 2, 3, 4, 0):
             B.plast_set_tile_shape(shape)
             out.append(f())
     finally:
@@ -72,7 +72,8 @@ def test_small_query_large_bank(B):
     gq, oq = both(B, c, o)
     gb, ob = both(B, bank.codes, bank.seq_off)
     tiles = B.plast_stage2_tiles(oq.idx.key_off, ob.idx.key_off)
-    assert (tiles[:, 3] == 1).mean() > 0.9  # by cost, almost all narrow
+    assert (tiles[:, 3] >= 1).mean() > 0.9  # by cost, almost all narrow
+    assert len(set(tiles[:, 3].tolist())) >= 2
     assert ((tiles[:, 2] % 8) != 0).any()    # ragged narrow tiles
     want_h = oracle.ungapped(oq, ob, threads=16)
     want = oracle.small_gapped(oq, ob, want_h)

@@ -1,7 +1,9 @@
 """Stage-2 work list (host logic, no GPU): every bank-1 occurrence of every
 key shared by both banks lies in exactly one tile; full wide tiles first,
-the remainder wide or narrow by the cost model; costliest tiles first in the
-persistent schedule, key order in the plain one."""
+the remainder one wide tile or narrow tiles (8 rows while 8 remain, the last
+1-7 rows by the cheapest cover with 8, 4 and 2) by the cost model; in the
+persistent schedule wide tiles (one launch) before narrow tiles (another),
+each costliest first; key order in the plain one."""
 import math
 
 import numpy as np
@@ -10,7 +12,8 @@ import pytest
 from paper_0804_3643_gb300 import binding as B
 
 NK = B.NKEYS
-WIDE, NARROW = 0, 1
+WIDE, NARROW, NARROW4, NARROW2 = 0, 1, 2, 3
+ROWS = {WIDE: 128, NARROW: 8, NARROW4: 4, NARROW2: 2}
 T1, NT1 = 128, 8
 
 
@@ -24,7 +27,8 @@ def offsets(counts):
 def costs():
     B.lib()
     saved = B.plast_get_tile_costs()
-    c = dict(wide_slot=0.5, wide_tile=4000.0, narrow_slot=0.6, narrow_tile=1000.0, wide_int16_cells=14)
+    c = dict(wide_slot=0.5, wide_tile=4000.0, narrow_slot=0.6, narrow_tile=1000.0, narrow4_slot=0.8,
+             narrow4_tile=900.0, narrow2_slot=1.1, narrow2_tile=800.0, wide_int16_cells=12)
     B.plast_set_tile_costs(c)
     yield c
     B.plast_set_tile_costs(saved)
@@ -44,16 +48,33 @@ def round_up(n, g):
 
 def tile_cost(c, shape, n2):
     # a CTA scores 128 (wide) or 1024 (narrow) bank-2 windows per pass
-    if shape == WIDE:
-        return c["wide_slot"] * T1 * round_up(n2, 128) + c["wide_tile"]
-    return c["narrow_slot"] * NT1 * round_up(n2, 1024) + c["narrow_tile"]
+    name = {WIDE: "wide", NARROW: "narrow", NARROW4: "narrow4", NARROW2: "narrow2"}[shape]
+    return c[name + "_slot"] * ROWS[shape] * round_up(n2, 128 if shape == WIDE else 1024) + c[name + "_tile"]
+
+
+def tail_cover(c, t, n2):
+    """Cheapest cover of t < 8 rows by narrow tiles of 8, 4, 2 rows, by brute
+    force over multisets: (cost, sorted list of shapes)."""
+    best = (0.0, [])
+    if t == 0:
+        return best
+    best = None
+    for a in range(0, 2):          # tiles of 8
+        for b in range(0, 3):      # tiles of 4
+            for d in range(0, 5):  # tiles of 2
+                if 8 * a + 4 * b + 2 * d < t or a + b + d == 0:
+                    continue
+                cost = a * tile_cost(c, NARROW, n2) + b * tile_cost(c, NARROW4, n2) + d * tile_cost(c, NARROW2, n2)
+                if best is None or cost < best[0] - 1e-9:
+                    best = (cost, sorted([NARROW] * a + [NARROW4] * b + [NARROW2] * d))
+    return best
 
 
 def check_cover(tiles, k1, n1, n2):
     by_key = {}
     for key, first, rows, shape in tiles:
-        assert shape in (WIDE, NARROW)
-        assert 1 <= rows <= (T1 if shape == WIDE else NT1)
+        assert shape in ROWS
+        assert 1 <= rows <= ROWS[shape]
         by_key.setdefault(int(key), []).append((int(first), int(rows), int(shape)))
     for k in range(NK):
         if n1[k] == 0 or n2[k] == 0:
@@ -82,19 +103,29 @@ def test_cover_and_shapes_by_cost(costs):
         if rem == 0:
             assert not rest
             continue
-        want_narrow = math.ceil(rem / NT1) * tile_cost(costs, NARROW, n2[k]) < tile_cost(costs, WIDE, n2[k])
-        if want_narrow:
-            assert all(s == NARROW for _, _, s in rest) and len(rest) == math.ceil(rem / NT1)
+        tail_cost, tail_shapes = tail_cover(costs, rem % NT1, n2[k])
+        narrow_cost = (rem // NT1) * tile_cost(costs, NARROW, n2[k]) + tail_cost
+        if narrow_cost < tile_cost(costs, WIDE, n2[k]):
+            shapes = [s_ for _, _, s_ in rest]
+            assert shapes[: rem // NT1] == [NARROW] * (rem // NT1)
+            assert all(r == NT1 for _, r, _ in rest[: rem // NT1])
+            assert sorted(shapes[rem // NT1:]) == tail_shapes
+            assert abs(sum(tile_cost(costs, s_, n2[k]) for s_ in shapes) - narrow_cost) < 1e-6
         else:
             assert len(rest) == 1 and rest[0][2] == WIDE and rest[0][1] == rem
-    # costliest first
-    c = [tile_cost(costs, s, n2[key]) for key, _, _, s in tiles]
-    assert all(a >= b for a, b in zip(c, c[1:]))
-    # both shapes occur in this mix
-    assert (tiles[:, 3] == WIDE).any() and (tiles[:, 3] == NARROW).any()
+    # wide tiles first (one launch), then narrow ones (another), each costliest first
+    wide = tiles[:, 3] == WIDE
+    n_wide = int(wide.sum())
+    assert wide[:n_wide].all() and not wide[n_wide:].any()
+    for part in (tiles[:n_wide], tiles[n_wide:]):
+        c = [tile_cost(costs, s, n2[key]) for key, _, _, s in part]
+        assert all(a >= b for a, b in zip(c, c[1:]))
+    # every shape occurs in this mix
+    for shape in ROWS:
+        assert (tiles[:, 3] == shape).any(), shape
 
 
-@pytest.mark.parametrize("shape", [1, 2])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
 def test_forced_shapes(costs, shape):
     rng = np.random.default_rng(6)
     n1, n2 = random_counts(rng)
@@ -102,7 +133,7 @@ def test_forced_shapes(costs, shape):
     B.plast_set_tile_shape(shape)
     tiles = B.plast_stage2_tiles(k1, k2)
     check_cover(tiles, k1, n1, n2)
-    assert (tiles[:, 3] == (WIDE if shape == 1 else NARROW)).all()
+    assert (tiles[:, 3] == shape - 1).all()
 
 
 def test_plain_schedule_keeps_key_order(costs):
@@ -119,10 +150,10 @@ def test_plain_schedule_keeps_key_order(costs):
 
 def test_small_query_goes_narrow(costs):
     # a query bank with a few occurrences per key against a large bank
-    n1 = np.full(NK, 3, dtype=np.int64)
     n2 = np.full(NK, 40000, dtype=np.int64)
-    tiles = B.plast_stage2_tiles(offsets(n1), offsets(n2))
-    assert (tiles[:, 3] == NARROW).all() and len(tiles) == NK
+    for n, shape in [(1, NARROW2), (2, NARROW2), (4, NARROW4), (8, NARROW)]:
+        tiles = B.plast_stage2_tiles(offsets(np.full(NK, n, dtype=np.int64)), offsets(n2))
+        assert (tiles[:, 3] == shape).all() and len(tiles) == NK, n
 
 
 def test_bad_offsets(costs):
