@@ -616,7 +616,7 @@ def main():
     ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow", "narrow4", "narrow2"],
                     help="stage-2 tile shapes: by measured cost (default) or forced")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile costs")
-    ap.add_argument("--wide-int16-cells", type=int, default=None, choices=[0, 12, 14, 16, 18],
+    ap.add_argument("--wide-int16-cells", type=int, default=None, choices=[0, 12, 14, 16],
                     help="force the wide stage-2 kernel variant (default: the autotuner's pick)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "batching_stress", "tplastn", "serving", "query"],

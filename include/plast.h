@@ -290,7 +290,7 @@ typedef struct plast_tile_costs {
   double narrow_slot, narrow_tile;   /* 8 rows */
   double narrow4_slot, narrow4_tile; /* 4 rows */
   double narrow2_slot, narrow2_tile; /* 2 rows */
-  int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14, 16 or 18) */
+  int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14 or 16) */
   int32_t reserved;         /* 0 */
 } plast_tile_costs;
 int plast_autotune(void* stream, plast_tile_costs* out);

@@ -61,6 +61,8 @@ constexpr int PLANE16 = NCODE * PROF16_STRIDE;             // 6336
 constexpr int SEED_PLANES = 3;                             // P1, M1, P2 (cells 0-3)
 constexpr int FIRST_CELL = 4;                              // first cell after the seed
 constexpr int TAB_BYTES = 512;                             // int8 [22][22], padded
+constexpr int T24_STRIDE = 24;                             // bytes per residue a of the word table
+constexpr int T24_BYTES = 544;                             // int8 [22][24] (b = 22, 23 zero), padded
 constexpr int ROWS_BYTES = WIN * UNG_T1;                   // 6144, cell-major; shares the staging area
 constexpr int STAGE_BYTES = NWARPS * 4 * WIN;              // 6144: 4 bank-2 windows per warp
 constexpr int WKEY_BYTES = NWARPS * WBUF * 8;              // 8192
@@ -76,7 +78,7 @@ struct Wide {
   static constexpr int N8 = SEED_PLANES + (WIN - FIRST_CELL - N16);
   static constexpr int BASE16 = N8 * PLANE8;
   static constexpr int PROF = BASE16 + N16 * PLANE16;
-  static constexpr int SMEM = PROF + TAB_BYTES + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 2 * 48;
+  static constexpr int SMEM = PROF + TAB_BYTES + T24_BYTES + STAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 2 * 48;
   __host__ __device__ static constexpr bool is16(int k) { return k >= FIRST_CELL && k < FIRST_CELL + N16; }
   // int8 plane of cell k >= FIRST_CELL + N16
   __host__ __device__ static constexpr int plane8(int k) { return SEED_PLANES + (k - FIRST_CELL - N16); }
@@ -318,6 +320,22 @@ __device__ __forceinline__ void fetch_tile(const UngArgs& a, int t, TileSlot* sl
   }
 }
 
+// Four rows against four residue codes: out[j] byte r = score(byte r of
+// rows4, 4 * b4 + j).  Four word loads from the [22][24] table (row a holds
+// score(a, b) for b = 0 .. 21 and two zero bytes) and a 4 x 4 byte transpose.
+__device__ __forceinline__ void score4x4(const uint32_t* t24, uint32_t rows4, int b4, uint32_t (&out)[4]) {
+  const uint32_t r0 = t24[__byte_perm(rows4, 0u, 0x4440u) * (T24_STRIDE / 4) + b4];
+  const uint32_t r1 = t24[__byte_perm(rows4, 0u, 0x4441u) * (T24_STRIDE / 4) + b4];
+  const uint32_t r2 = t24[__byte_perm(rows4, 0u, 0x4442u) * (T24_STRIDE / 4) + b4];
+  const uint32_t r3 = t24[__byte_perm(rows4, 0u, 0x4443u) * (T24_STRIDE / 4) + b4];
+  const uint32_t t0 = __byte_perm(r0, r1, 0x5140u), t1 = __byte_perm(r0, r1, 0x7362u);
+  const uint32_t t2 = __byte_perm(r2, r3, 0x5140u), t3 = __byte_perm(r2, r3, 0x7362u);
+  out[0] = __byte_perm(t0, t2, 0x5410u);
+  out[1] = __byte_perm(t0, t2, 0x7632u);
+  out[2] = __byte_perm(t1, t3, 0x5410u);
+  out[3] = __byte_perm(t1, t3, 0x7632u);
+}
+
 // Four rows: byte r of the result is score(byte r of src, b).
 __device__ __forceinline__ uint32_t pack4(uint32_t src, const int8_t* tab, int b) {
   uint32_t x = 0;
@@ -405,7 +423,8 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char* prof = smem;
   int8_t* tab = reinterpret_cast<int8_t*>(smem + L::PROF);
-  unsigned char* stage = smem + L::PROF + TAB_BYTES;
+  uint32_t* t24 = reinterpret_cast<uint32_t*>(smem + L::PROF + TAB_BYTES);
+  unsigned char* stage = smem + L::PROF + TAB_BYTES + T24_BYTES;
   uint8_t* rowsT = stage;  // the tile's bank-1 rows while its profile is built
   uint64_t* wkey = reinterpret_cast<uint64_t*>(stage + STAGE_BYTES);
   uint32_t* wval = reinterpret_cast<uint32_t*>(stage + STAGE_BYTES + WKEY_BYTES);
@@ -421,6 +440,10 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
 
   for (int i = tid; i < NCODE * NCODE; i += UNG_THREADS) tab[i] = c_score[i];
+  for (int i = tid; i < NCODE * T24_STRIDE; i += UNG_THREADS) {
+    const int aa = i / T24_STRIDE, b = i - aa * T24_STRIDE;
+    reinterpret_cast<int8_t*>(t24)[i] = b < NCODE ? c_score[aa * NCODE + b] : (int8_t)0;
+  }
   const uint32_t s1x2 = ((uint32_t)(uint16_t)a.s1 << 16) | (uint16_t)a.s1;
 
   // tiles: from the device counter (persistent) or this CTA's own; thread 0
@@ -442,61 +465,63 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
         rowsT[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
       }
       __syncthreads();
-      // int8 planes: 16 rows per 16-byte item
-      for (int e = tid; e < L::N8 * NCODE * 8; e += UNG_THREADS) {
+      // seed planes: 16 rows per 16-byte item, one residue code b per item
+      // P1 = d0 + s(a1, b), M1 = d0 + max(0, s(a1, b)), P2 = s(a2, b) + d3
+      for (int e = tid; e < SEED_PLANES * NCODE * 8; e += UNG_THREADS) {
         const int p = e / (NCODE * 8);
         const int rem = e - p * (NCODE * 8);
         const int b = rem >> 3, gg = rem & 7;
+        const int kx = p == 2 ? 2 : 1, kd = p == 2 ? 3 : 0;
+        const uint4 cx = *reinterpret_cast<const uint4*>(rowsT + kx * UNG_T1 + gg * ROWS_PER_LANE);
+        const uint4 cd = *reinterpret_cast<const uint4*>(rowsT + kd * UNG_T1 + gg * ROWS_PER_LANE);
+        const uint32_t sx[4] = {cx.x, cx.y, cx.z, cx.w}, sd[4] = {cd.x, cd.y, cd.z, cd.w};
         uint32_t w[4];
-        if (p >= SEED_PLANES) {
-          const int k = p - SEED_PLANES + FIRST_CELL + N16;
-          const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
-          w[0] = pack4(c16.x, tab, b);
-          w[1] = pack4(c16.y, tab, b);
-          w[2] = pack4(c16.z, tab, b);
-          w[3] = pack4(c16.w, tab, b);
-        } else {
-          // P1 = d0 + s(a1, b), M1 = d0 + max(0, s(a1, b)), P2 = s(a2, b) + d3
-          const int kx = p == 2 ? 2 : 1, kd = p == 2 ? 3 : 0;
-          const uint4 cx = *reinterpret_cast<const uint4*>(rowsT + kx * UNG_T1 + gg * ROWS_PER_LANE);
-          const uint4 cd = *reinterpret_cast<const uint4*>(rowsT + kd * UNG_T1 + gg * ROWS_PER_LANE);
-          const uint32_t sx[4] = {cx.x, cx.y, cx.z, cx.w}, sd[4] = {cd.x, cd.y, cd.z, cd.w};
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            uint32_t x = 0;
+        for (int q = 0; q < 4; q++) {
+          uint32_t x = 0;
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-              const int ax = (sx[q] >> (8 * r)) & 0xff, ad = (sd[q] >> (8 * r)) & 0xff;
-              int v = tab[ax * NCODE + b];
-              if (p == 1) v = max(v, 0);
-              v += tab[ad * NCODE + ad];
-              x |= (uint32_t)(uint8_t)(int8_t)v << (8 * r);
-            }
-            w[q] = x;
+          for (int r = 0; r < 4; r++) {
+            const int ax = (sx[q] >> (8 * r)) & 0xff, ad = (sd[q] >> (8 * r)) & 0xff;
+            int v = tab[ax * NCODE + b];
+            if (p == 1) v = max(v, 0);
+            v += tab[ad * NCODE + ad];
+            x |= (uint32_t)(uint8_t)(int8_t)v << (8 * r);
           }
+          w[q] = x;
         }
         *reinterpret_cast<uint4*>(prof + p * PLANE8 + b * PROF_STRIDE + gg * 16) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-      // int16 planes: 16 rows per item, rows 0-7 and 8-15 of the group 128 bytes apart
-      for (int e = tid; e < N16 * NCODE * 8; e += UNG_THREADS) {
-        const int c = e / (NCODE * 8);
-        const int rem = e - c * (NCODE * 8);
-        const int b = rem >> 3, gg = rem & 7;
-        const int k = FIRST_CELL + c;
+      // the other planes: 16 rows x 4 residue codes per item, by 4 x 4 transposes
+      constexpr int NB4 = (NCODE + 3) / 4;  // 6 groups of 4 codes
+      constexpr int N8C = L::N8 - SEED_PLANES;
+      for (int e = tid; e < (N8C + N16) * NB4 * 8; e += UNG_THREADS) {
+        const int c = e / (NB4 * 8);
+        const int rem = e - c * (NB4 * 8);
+        const int b4 = rem >> 3, gg = rem & 7;
+        const bool i16 = c >= N8C;  // int16 cells first in the cell order, last in this loop
+        const int k = i16 ? FIRST_CELL + (c - N8C) : FIRST_CELL + N16 + c;
         const uint4 c16 = *reinterpret_cast<const uint4*>(rowsT + k * UNG_T1 + gg * ROWS_PER_LANE);
-        const uint32_t src[4] = {c16.x, c16.y, c16.z, c16.w};
-        uint32_t w[8];
+        uint32_t o[4][4];  // o[q][j]: rows 4q .. 4q+3 of the group against code 4 * b4 + j
+        score4x4(t24, c16.x, b4, o[0]);
+        score4x4(t24, c16.y, b4, o[1]);
+        score4x4(t24, c16.z, b4, o[2]);
+        score4x4(t24, c16.w, b4, o[3]);
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int a0 = src[q] & 0xff, a1 = (src[q] >> 8) & 0xff, a2 = (src[q] >> 16) & 0xff, a3 = src[q] >> 24;
-          w[2 * q] = (uint32_t)(uint16_t)(int16_t)tab[a0 * NCODE + b] |
-                     ((uint32_t)(uint16_t)(int16_t)tab[a1 * NCODE + b] << 16);
-          w[2 * q + 1] = (uint32_t)(uint16_t)(int16_t)tab[a2 * NCODE + b] |
-                         ((uint32_t)(uint16_t)(int16_t)tab[a3 * NCODE + b] << 16);
+        for (int j = 0; j < 4; j++) {
+          const int b = 4 * b4 + j;
+          if (b >= NCODE) break;
+          if (!i16) {
+            *reinterpret_cast<uint4*>(prof + (SEED_PLANES + c) * PLANE8 + b * PROF_STRIDE + gg * 16) =
+                make_uint4(o[0][j], o[1][j], o[2][j], o[3][j]);
+          } else {
+            // int16: rows 0-7 of the group at 16 gg, rows 8-15 128 bytes further
+            unsigned char* d = prof + L::BASE16 + (c - N8C) * PLANE16 + b * PROF16_STRIDE + gg * 16;
+            *reinterpret_cast<uint4*>(d) = make_uint4(sext_pair(o[0][j], 0), sext_pair(o[0][j], 1),
+                                                      sext_pair(o[1][j], 0), sext_pair(o[1][j], 1));
+            *reinterpret_cast<uint4*>(d + 128) = make_uint4(sext_pair(o[2][j], 0), sext_pair(o[2][j], 1),
+                                                            sext_pair(o[3][j], 0), sext_pair(o[3][j], 1));
+          }
         }
-        unsigned char* d = prof + L::BASE16 + c * PLANE16 + b * PROF16_STRIDE + gg * 16;
-        *reinterpret_cast<uint4*>(d) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(d + 128) = make_uint4(w[4], w[5], w[6], w[7]);
       }
       __syncthreads();
 
@@ -592,7 +617,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped_narrow(UngArgs a) {
 
 namespace {
 std::atomic<int> g_variant{-1};  // index into UNG_N16 (-1: the default)
-constexpr int UNG_N16[UNG_VARIANTS] = {0, 12, 14, 16, UNG_MAX_N16};
+constexpr int UNG_N16[UNG_VARIANTS] = {0, 12, 14, UNG_MAX_N16};
 constexpr int UNG_DEFAULT_VARIANT = 1;
 
 template <int N16>
@@ -645,8 +670,6 @@ cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
       return launch_variant<UNG_N16[1]>(a, grid, st);
     case 3:
       return launch_variant<UNG_N16[3]>(a, grid, st);
-    case 4:
-      return launch_variant<UNG_N16[4]>(a, grid, st);
     default:
       return launch_variant<UNG_N16[2]>(a, grid, st);
   }

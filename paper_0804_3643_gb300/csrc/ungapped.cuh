@@ -30,9 +30,9 @@ struct UngArgs {
 };
 
 // Wide-tile variants of the stage-2 kernel: how many cells the profile holds
-// as int16 (UNG_N16 in ungapped.cu: 0, 12, 14, 16, UNG_MAX_N16).
-constexpr int UNG_VARIANTS = 5;
-constexpr int UNG_MAX_N16 = 18;
+// as int16 (UNG_N16 in ungapped.cu: 0, 12, 14, UNG_MAX_N16).
+constexpr int UNG_VARIANTS = 4;
+constexpr int UNG_MAX_N16 = 16;
 int ungapped_variant();            // the variant launch_ungapped runs
 int ungapped_variant_n16(int v);   // its int16 cells (-1 for no such variant)
 void set_ungapped_variant(int v);  // -1: the default

@@ -53,8 +53,8 @@ def test_host_only_entry_points(lib):
     with pytest.raises(B.PlastError):
         B.plast_set_tile_costs(dict(c, narrow_slot=-1.0))
     with pytest.raises(B.PlastError):
-        B.plast_set_tile_costs(dict(c, wide_int16_cells=20))
-    for n16 in (0, 12, 14, 16, 18):
+        B.plast_set_tile_costs(dict(c, wide_int16_cells=18))
+    for n16 in (0, 12, 14, 16):
         B.plast_set_tile_costs(dict(c, wide_int16_cells=n16))
         assert B.plast_get_tile_costs()["wide_int16_cells"] == n16
     B.plast_set_tile_costs(dict(c, wide_tile=c["wide_tile"] + 1))

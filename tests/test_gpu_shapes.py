@@ -122,7 +122,7 @@ def test_autotune(B):
 
 
 def test_wide_variants_parity(B):
-    # every wide-kernel variant (int16 cells 0, 12, 14, 16, 18) gives the oracle's hits,
+    # every wide-kernel variant (int16 cells 0, 12, 14, 16) gives the oracle's hits,
     # with full tiles, a ragged last tile and rows of sentinels
     b1, b2 = synth.workload("plastp_plain", seed=8, scale=0.5)
     g1, o1 = both(B, b1.codes, b1.seq_off)
@@ -133,7 +133,7 @@ def test_wide_variants_parity(B):
     saved = B.plast_get_tile_costs()
     try:
         B.plast_set_tile_shape(1)
-        for n16 in (0, 12, 14, 16, 18):
+        for n16 in (0, 12, 14, 16):
             B.plast_set_tile_costs(dict(saved, wide_int16_cells=n16))
             assert same(B.hits_numpy(B.plast_ungapped(g1, g2)), want)
             assert same(B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s1=20))), want20)
