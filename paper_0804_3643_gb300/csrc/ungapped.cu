@@ -349,8 +349,9 @@ __device__ __forceinline__ uint32_t pack4(uint32_t src, const int8_t* tab, int b
 
 // A narrow tile of 2 * NW rows: rows cell-major (nrows[k][r], stride 8),
 // the profile (NW = 4: planes nprof[p][k][b] of rows 4p .. 4p+3; NW = 2: one
-// plane; NW = 1: halfwords of rows 0-1), then every bank-2 window of the key
-// against it, one per lane.
+// plane; NW = 1: halfwords of rows 0-1; cells 0-3 folded into P1, M1, P2 as
+// in the wide tiles), then every bank-2 window of the key against it, one per
+// lane.
 template <int NW>
 __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t u0, int64_t v0, int64_t v1,
                                             uint8_t* nrows, unsigned char* nprof, const int8_t* tab,
@@ -363,16 +364,38 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
   }
   __syncthreads();
+  // cells 4 .. 47 at their own slots; slots 0, 1, 2 hold the folded seed
+  // planes P1, M1, P2 (as in the wide tiles); slot 3 is unused
   for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
     const int k = e / NCODE, b = e - k * NCODE;
-    const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + k * UNG_NT1);
-    if constexpr (NW == 1) {
-      const int a0 = c8.x & 0xff, a1 = (c8.x >> 8) & 0xff;
-      *reinterpret_cast<uint16_t*>(nprof + e * 2) =
-          (uint16_t)((uint8_t)tab[a0 * NCODE + b] | ((uint32_t)(uint8_t)tab[a1 * NCODE + b] << 8));
+    if (k == 3) continue;
+    uint32_t w[2];
+    const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + (k < 3 ? (k == 2 ? 2 : 1) : k) * UNG_NT1);
+    if (k >= FIRST_CELL) {
+      w[0] = pack4(c8.x, tab, b);
+      w[1] = pack4(c8.y, tab, b);
     } else {
-      *reinterpret_cast<uint32_t*>(nprof + e * 4) = pack4(c8.x, tab, b);
-      if constexpr (NW == 4) *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = pack4(c8.y, tab, b);
+      const uint2 cd = *reinterpret_cast<const uint2*>(nrows + (k == 2 ? 3 : 0) * UNG_NT1);
+      const uint32_t sx[2] = {c8.x, c8.y}, sd[2] = {cd.x, cd.y};
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        uint32_t x = 0;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const int ax = (sx[q] >> (8 * r)) & 0xff, ad = (sd[q] >> (8 * r)) & 0xff;
+          int v = tab[ax * NCODE + b];
+          if (k == 1) v = max(v, 0);
+          v += tab[ad * NCODE + ad];
+          x |= (uint32_t)(uint8_t)(int8_t)v << (8 * r);
+        }
+        w[q] = x;
+      }
+    }
+    if constexpr (NW == 1) {
+      *reinterpret_cast<uint16_t*>(nprof + e * 2) = (uint16_t)(w[0] & 0xffffu);
+    } else {
+      *reinterpret_cast<uint32_t*>(nprof + e * 4) = w[0];
+      if constexpr (NW == 4) *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = w[1];
     }
   }
   __syncthreads();
@@ -385,15 +408,17 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     nw[j] = (lane + 32 * j) / 3;
     np[j] = (lane + 32 * j) % 3;
   }
+  // window indexes relative to the key's first (32-bit arithmetic)
+  const int n2 = (int)(v1 - v0);
+  const uint4* src = reinterpret_cast<const uint4*>(a.nb2 + v0 * WIN);
   uint4 pre[3];
 #pragma unroll
   for (int j = 0; j < 3; j++) {
-    const int64_t v = v0 + warp * 32 + nw[j];
-    pre[j] = v < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + np[j]) : sent16;
+    const int v = warp * 32 + nw[j];
+    pre[j] = v < n2 ? __ldg(src + (int64_t)v * 3 + np[j]) : sent16;
   }
-  for (int64_t vb = v0 + warp * 32; vb < v1; vb += NWARPS * 32) {
-    const int64_t v = vb + lane;
-    const bool vok = v < v1;
+  for (int vb = warp * 32; vb < n2; vb += NWARPS * 32) {
+    const bool vok = vb + lane < n2;
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 3; j++) {
@@ -406,14 +431,23 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      const int64_t vn = vb + NWARPS * 32 + nw[j];
-      pre[j] = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + np[j]) : sent16;
+      const int vn = vb + NWARPS * 32 + nw[j];
+      pre[j] = vn < n2 ? __ldg(src + (int64_t)vn * 3 + np[j]) : sent16;
     }
     uint32_t s[NW], m[NW];
+    {  // cells 0-3 from the folded seed planes
+      const uint32_t bs1 = lds_u8<1>(my_nrow), bs2 = lds_u8<2>(my_nrow);
+      uint32_t up[NW], uq[NW];
+      narrow_scores<NW>(nprof, 0, bs1, up);
+      narrow_scores<NW>(nprof, 2, bs2, uq);
 #pragma unroll
-    for (int w = 0; w < NW; w++) s[w] = m[w] = 0;
-    narrow_pairs<0, NW>(my_nrow, nprof, s, m);
-    emit_hits<NW>(m, vok, rows, u0, v, a, s1x2, lane, my_wk, my_wv, wcnt);
+      for (int w = 0; w < NW; w++) s[w] = __vadd2(up[w], uq[w]);
+      narrow_scores<NW>(nprof, 1, bs1, up);
+#pragma unroll
+      for (int w = 0; w < NW; w++) m[w] = __vmaxs2(up[w], s[w]);
+    }
+    narrow_pairs<FIRST_CELL, NW>(my_nrow, nprof, s, m);
+    emit_hits<NW>(m, vok, rows, u0, v0 + vb + lane, a, s1x2, lane, my_wk, my_wv, wcnt);
   }
 }
 
@@ -527,21 +561,20 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
 
       const unsigned char* plane = prof + g * 16;
       // lanes 0..11 fetch the warp's next 4 windows (12 x 16 bytes) one
-      // iteration ahead; sentinel windows past the end of the key
+      // iteration ahead; sentinel windows past the end of the key.  Window
+      // indexes are relative to the key's first (32-bit arithmetic).
+      const int n2 = (int)(v1 - v0), lw = lane / 3;
+      const uint4* src = reinterpret_cast<const uint4*>(a.nb2 + v0 * WIN) + lane % 3;
       uint4 pre = sent16;
-      if (lane < 12) {
-        const int64_t v = v0 + warp * 4 + lane / 3;
-        if (v < v1) pre = __ldg(reinterpret_cast<const uint4*>(a.nb2 + v * WIN) + lane % 3);
-      }
-      for (int64_t vb = v0 + warp * 4; vb < v1; vb += NWARPS * 4) {
-        const int64_t v = vb + js;
-        const bool vok = v < v1;
+      if (lane < 12 && warp * 4 + lw < n2) pre = __ldg(src + (int64_t)(warp * 4 + lw) * 3);
+      for (int vb = warp * 4; vb < n2; vb += NWARPS * 4) {
+        const bool vok = vb + js < n2;
         __syncwarp();
         if (lane < 12) my_stage[lane] = pre;
         __syncwarp();
         if (lane < 12) {
-          const int64_t vn = vb + NWARPS * 4 + lane / 3;
-          pre = vn < v1 ? __ldg(reinterpret_cast<const uint4*>(a.nb2 + vn * WIN) + lane % 3) : sent16;
+          const int vn = vb + NWARPS * 4 + lw;
+          pre = vn < n2 ? __ldg(src + (int64_t)vn * 3) : sent16;
         }
         uint32_t s[8], m[8];
         {  // cells 0-3 from the folded seed planes
@@ -556,8 +589,8 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
           for (int w = 0; w < 8; w++) m[w] = __vmaxs2(up[w], s[w]);
         }
         wide_pairs<FIRST_CELL, N16>(my_row, plane, s, m);
-        emit_hits<8>(m, vok, rows - g * ROWS_PER_LANE, u0 + g * ROWS_PER_LANE, v, a, s1x2, lane, my_wk, my_wv,
-                     wcnt);
+        emit_hits<8>(m, vok, rows - g * ROWS_PER_LANE, u0 + g * ROWS_PER_LANE, v0 + vb + js, a, s1x2, lane, my_wk,
+                     my_wv, wcnt);
       }
     }
     __syncthreads();  // the next tile rebuilds the profile
