@@ -383,7 +383,8 @@ def run_gpu(args, rank, world, local_rank):
         "stage_ms": stages,
         "roofline": {
             "bound": "alu",
-            "kernel": "k_ungapped",
+            "kernel": f"stage 2: k_ungapped<{tiles.get('wide_int16_cells', '?')}> (wide tiles) then "
+                      "k_ungapped_narrow (narrow tiles), timed together",
             "achieved": achieved_cells / 1e12,
             "peak": peak_cells / 1e12,
             "unit": "Tcell/s",

@@ -124,7 +124,7 @@ int num_sms() {
 // rounded up to that granularity.  Defaults from a GB300; plast_autotune
 // measures them on the current device.
 std::mutex g_cost_mu;
-plast_tile_costs g_costs = {0.317, 4983.0, 0.512, 325.0, 0.64, 300.0, 0.95, 300.0, 12, 0};
+plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1090.0, 12, 0};
 // 0: by cost; 1: wide only; 2, 3, 4: narrow tiles of 8, 4, 2 rows only
 std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
