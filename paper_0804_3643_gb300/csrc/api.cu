@@ -129,7 +129,8 @@ plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1
 std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
 constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tiles
-int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) / g * g; }
+int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) & ~(g - 1); }  // g a power of two
+static_assert((WIDE_PASS & (WIDE_PASS - 1)) == 0 && (NARROW_PASS & (NARROW_PASS - 1)) == 0, "passes");
 
 int shape_rows(int shape) {
   switch (shape) {
@@ -178,39 +179,76 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
                       const std::vector<char>* key_mask, int shape_override) {
   tl->tiles.clear();
   tl->pairs = 0;
+  tl->n_wide = 0;
   plast_tile_costs c;
   {
     std::lock_guard<std::mutex> lk(g_cost_mu);
     c = g_costs;
   }
   const int mode = shape_override >= 0 ? shape_override : g_shape.load();
-  std::vector<std::pair<double, int4>> w;
-  auto emit = [&](int k, int64_t first, int64_t rows, int shape, int64_t n2) {
-    w.push_back({tile_cost(c, shape, n2), make_int4(k, (int)first, (int)rows, shape)});
-  };
+  // Keys in launch order: the persistent schedule takes them by decreasing
+  // n2, which orders the tiles of each shape by decreasing cost (a tile's
+  // cost depends on its shape and n2 only), so the tiles need no sort.
+  std::vector<int> keys;
+  keys.reserve(NKEYS);
   for (int k = 0; k < NKEYS; k++) {
     if (key_mask && !(*key_mask)[k]) continue;
+    if (ko1[k + 1] == ko1[k] || ko2[k + 1] == ko2[k]) continue;
+    keys.push_back(k);
+  }
+  if (largest_first) {
+    // counting sort by decreasing ceil(n2 / 128), the quantity every tile
+    // cost depends on (monotonically), stable in key order
+    constexpr int NB = 1 << 16;
+    static thread_local std::vector<int32_t> count;
+    count.assign(NB + 1, 0);
+    auto bucket = [&](int k) {
+      const int64_t b = round_up(ko2[k + 1] - ko2[k], WIDE_PASS) / WIDE_PASS;
+      return NB - 1 - (int)std::min<int64_t>(b, NB - 1);
+    };
+    for (const int k : keys) count[bucket(k) + 1]++;
+    for (int b = 0; b < NB; b++) count[b + 1] += count[b];
+    std::vector<int> sorted(keys.size());
+    for (const int k : keys) sorted[count[bucket(k)]++] = k;
+    keys.swap(sorted);
+  }
+  // wide tiles, then narrow tiles of 8, 4 and 2 rows, each in key order
+  // (narrow tiles with their cost, for the merge)
+  int64_t rows_total = 0;
+  for (const int k : keys) rows_total += ko1[k + 1] - ko1[k];
+  std::vector<int4> wide;
+  std::vector<std::pair<float, int4>> by_shape[4];
+  std::vector<int4>* out = largest_first ? nullptr : &tl->tiles;  // plain schedule: key by key
+  if (out) out->reserve((size_t)(rows_total / UNG_T1 + 4 * keys.size()));
+  else wide.reserve((size_t)(rows_total / UNG_T1 + keys.size()));
+  double cost_now[4] = {0, 0, 0, 0};  // tile costs of the current key's n2
+  auto emit = [&](int k, int64_t first, int64_t rows, int shape) {
+    const int4 t = make_int4(k, (int)first, (int)rows, shape);
+    if (out) out->push_back(t);
+    else if (shape == UNG_WIDE) wide.push_back(t);
+    else by_shape[shape].push_back({(float)cost_now[shape], t});
+  };
+  for (const int k : keys) {
     const int64_t n1 = ko1[k + 1] - ko1[k];
     const int64_t n2 = ko2[k + 1] - ko2[k];
-    if (n1 == 0 || n2 == 0) continue;
     tl->pairs += n1 * n2;
+    for (int shape = UNG_NARROW; shape <= UNG_NARROW2; shape++) cost_now[shape] = tile_cost(c, shape, n2);
     int64_t u = ko1[k];
     const int64_t end = ko1[k + 1];
     if (mode >= 2) {  // one narrow shape only
       const int shape = mode - 1, r = shape_rows(shape);
-      for (; u < end; u += r) emit(k, u, std::min<int64_t>(r, end - u), shape, n2);
+      for (; u < end; u += r) emit(k, u, std::min<int64_t>(r, end - u), shape);
       continue;
     }
-    for (; end - u >= UNG_T1; u += UNG_T1) emit(k, u, UNG_T1, UNG_WIDE, n2);
+    for (; end - u >= UNG_T1; u += UNG_T1) emit(k, u, UNG_T1, UNG_WIDE);
     const int64_t rem = end - u;
     if (rem <= 0) continue;
     if (mode == 1) {
-      emit(k, u, rem, UNG_WIDE, n2);
+      emit(k, u, rem, UNG_WIDE);
       continue;
     }
     // cheapest cover of the last t rows (t < 8) by narrow tiles of 8, 4, 2
-    const double c8 = tile_cost(c, UNG_NARROW, n2), c4 = tile_cost(c, UNG_NARROW4, n2),
-                 c2 = tile_cost(c, UNG_NARROW2, n2);
+    const double c8 = cost_now[UNG_NARROW], c4 = cost_now[UNG_NARROW4], c2 = cost_now[UNG_NARROW2];
     double best[UNG_NT1];
     int pick[UNG_NT1];
     best[0] = 0;
@@ -226,30 +264,39 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     const int tail = (int)(rem % UNG_NT1);
     const double narrow_cost = (double)full8 * c8 + best[tail];
     if (!(narrow_cost < tile_cost(c, UNG_WIDE, n2))) {
-      emit(k, u, rem, UNG_WIDE, n2);
+      emit(k, u, rem, UNG_WIDE);
       continue;
     }
-    for (int64_t i = 0; i < full8; i++, u += UNG_NT1) emit(k, u, UNG_NT1, UNG_NARROW, n2);
+    for (int64_t i = 0; i < full8; i++, u += UNG_NT1) emit(k, u, UNG_NT1, UNG_NARROW);
     for (int t = tail; t > 0;) {
       const int shape = pick[t], r = std::min(shape_rows(shape), t);
-      emit(k, u, r, shape, n2);
+      emit(k, u, r, shape);
       u += r;
       t -= r;
     }
   }
-  if (largest_first) {
-    // wide tiles, then narrow ones (two launches), each costliest first
-    std::stable_sort(w.begin(), w.end(), [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
-      const bool wx = x.second.w == UNG_WIDE, wy = y.second.w == UNG_WIDE;
-      if (wx != wy) return wx;
-      return x.first > y.first;
-    });
+  if (!largest_first) {
+    for (const int4& t : tl->tiles) tl->n_wide += t.w == UNG_WIDE;
+    return;
   }
-  tl->tiles.reserve(w.size());
-  tl->n_wide = 0;
-  for (auto& x : w) {
-    tl->tiles.push_back(x.second);
-    tl->n_wide += x.second.w == UNG_WIDE;
+  // wide tiles (one launch), then the narrow ones (another), costliest first:
+  // a three-way merge of the per-shape lists, each already in cost order
+  size_t total = wide.size();
+  for (const auto& v : by_shape) total += v.size();
+  tl->tiles.reserve(total);
+  tl->tiles.insert(tl->tiles.end(), wide.begin(), wide.end());
+  tl->n_wide = (int64_t)wide.size();
+  size_t at[4] = {0, 0, 0, 0};
+  for (;;) {
+    int pickd = -1;
+    float bestc = 0;
+    for (int shape = UNG_NARROW; shape <= UNG_NARROW2; shape++) {
+      if (at[shape] >= by_shape[shape].size()) continue;
+      const float v = by_shape[shape][at[shape]].first;
+      if (pickd < 0 || v > bestc) pickd = shape, bestc = v;
+    }
+    if (pickd < 0) break;
+    tl->tiles.push_back(by_shape[pickd][at[pickd]++].second);
   }
 }
 
