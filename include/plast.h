@@ -125,14 +125,20 @@ int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_co
  *           (device); total length < 2^31 - 2^26
  *   params  may be NULL (defaults)
  *   *out    receives the new bank (host)
- * The inputs are copied; the caller may free them after the call.
+ * The inputs are consumed before the call returns; the caller may free them
+ * then.  The last step (laying out the neighbourhoods) may still be running
+ * on `stream` when the call returns: every later call that takes the bank
+ * waits for it, on whatever stream it is given, and plast_bank_free waits
+ * too, so the caller may go on to host work (another bank, planning) while
+ * it finishes.
  * Errors: PLAST_E_INVALID (code outside 0..20, bad offsets, n_seqs < 0,
  * unsupported params), PLAST_E_OOM, PLAST_E_CUDA.
  */
 int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs, const plast_params* params,
                      void* stream, plast_bank** out);
 
-/* Release a bank and its device memory (NULL is ignored). */
+/* Release a bank and its device memory, after its construction has finished
+ * (NULL is ignored). */
 void plast_bank_free(plast_bank* bank);
 
 /* Number of sequences / residues / indexed positions of a bank (host). */

@@ -486,6 +486,10 @@ int plast_set_schedule(int mode) {
 
 void plast_bank_free(plast_bank* b) {
   if (!b) return;
+  if (b->ready) {
+    cudaEventSynchronize(b->ready);  // the build may still be running on its stream
+    cudaEventDestroy(b->ready);
+  }
   // pool memory, returned in order with the legacy default stream
   for (void* p : {(void*)b->pad_alloc, (void*)b->pad_off, (void*)b->key_off, (void*)b->pos, (void*)b->nb})
     if (p) cudaFreeAsync(p, 0);
@@ -601,14 +605,18 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
         return fail(rc);
     }
     if ((rc = ck(launch_key_offsets(skey, n_idx, b->key_off, st)))) return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->nb, (size_t)std::max<int64_t>(n_idx, 1) * WIN, st)))) return fail(rc);
-    if ((rc = ck(launch_neighbourhoods(b->pad, b->pos, n_idx, b->nb, st)))) return fail(rc);
     b->h_key_off.resize(NKEYS + 1);
     if ((rc = ck(cudaMemcpyAsync(b->h_key_off.data(), b->key_off, (NKEYS + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st))))
       return fail(rc);
+    if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
+    // the windows are laid out while the caller goes on (later calls wait on
+    // b->ready)
+    if ((rc = ck(cudaMallocAsync((void**)&b->nb, (size_t)std::max<int64_t>(n_idx, 1) * WIN, st)))) return fail(rc);
+    if ((rc = ck(launch_neighbourhoods(b->pad, b->pos, n_idx, b->nb, st)))) return fail(rc);
+    if ((rc = ck(cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming)))) return fail(rc);
+    if ((rc = ck(cudaEventRecord(b->ready, st)))) return fail(rc);
   }
-  if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
   *out = b;
   return PLAST_OK;
 }
@@ -617,6 +625,7 @@ int plast_bank_export_index(const plast_bank* b, int64_t* key_off, int32_t* pos,
                             void* stream) {
   if (!b || !n_out || !key_off) return PLAST_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  CK(bank_wait(b, st));
   *n_out = b->n_idx;
   if (cap < b->n_idx) return PLAST_E_CAPACITY;
   if (b->n_idx > 0 && !pos) return PLAST_E_INVALID;
@@ -650,6 +659,8 @@ static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
+  CK(bank_wait(b1, st));
+  CK(bank_wait(b2, st));
   *n_out = 0;
   CK(upload_tables_once());
   t_timer.reset();
@@ -778,6 +789,8 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
   if (n_in > 0 && !in) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
+  CK(bank_wait(b1, st));
+  CK(bank_wait(b2, st));
   *n_out = 0;
   CK(upload_tables_once());
   t_timer.reset();
@@ -815,6 +828,8 @@ static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_p
   }
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
+  CK(bank_wait(b1, st));
+  CK(bank_wait(b2, st));
   *n_out = 0;
   if (n_ungapped_out) *n_ungapped_out = 0;
   CK(upload_tables_once());
@@ -950,6 +965,9 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   CK(upload_tables_once());
+  // the banks are complete before any run (runs may be captured in a graph)
+  if (b1->ready) CK(cudaEventSynchronize(b1->ready));
+  if (b2->ready) CK(cudaEventSynchronize(b2->ready));
   plast_plan* p = new (std::nothrow) plast_plan();
   if (!p) return PLAST_E_OOM;
   cudaGetDevice(&p->device);
@@ -1144,6 +1162,8 @@ int random_bank(int32_t n_seqs, int len, uint64_t seed, cudaStream_t st, plast_b
 int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStream_t st, int reps, double* ms,
                 double* slots, double* tiles) {
   TileList tl;
+  CK(bank_wait(b1, st));
+  CK(bank_wait(b2, st));
   build_tiles(b1, b2, true, &tl, nullptr, shape);
   *slots = 0;
   for (const int4& t : tl.tiles) {

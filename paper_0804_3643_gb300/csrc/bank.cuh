@@ -23,4 +23,11 @@ struct plast_bank {
   int pad_bits = 1;            // bits needed by a padded position
   std::vector<int64_t> h_key_off;
   std::vector<int64_t> h_pad_off;
+  cudaEvent_t ready = nullptr;  // recorded after the last kernel that builds the bank
 };
+
+// Orders work queued on st after the bank's construction (which may still be
+// running on the stream it was built on).
+inline cudaError_t bank_wait(const plast_bank* b, cudaStream_t st) {
+  return b && b->ready ? cudaStreamWaitEvent(st, b->ready, 0) : cudaSuccess;
+}

@@ -90,6 +90,7 @@ extern "C" int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank
     return PLAST_E_INVALID;
   *n_out = 0;
   cudaStream_t st = (cudaStream_t)stream;
+  if (bank_wait(b1, st) != cudaSuccess || bank_wait(b2, st) != cudaSuccess) return PLAST_E_CUDA;
 
   cudaError_t err;
   unsigned char* base = scratch_on_current_device(&err);

@@ -230,3 +230,23 @@ def test_errors(B):
     with pytest.raises(B.PlastError) as e:
         B.plast_translate6(dna, torch.tensor([0, 3], dtype=torch.int64, device="cuda"))
     assert e.value.code == B.PLAST_E_INVALID
+
+
+def test_bank_built_on_another_stream(B):
+    # the index call returns while its last kernel may still run on its
+    # stream; a search on another stream must wait for it, and a free right
+    # after the build must too
+    b1, b2 = synth.workload("plastp_plain", seed=14, scale=0.3)
+    o1, o2 = oracle.make_bank(b1.codes, b1.seq_off), oracle.make_bank(b2.codes, b2.seq_off)
+    want = oracle.small_gapped(o1, o2, oracle.ungapped(o1, o2, threads=8))
+    side = torch.cuda.Stream()
+    d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
+    d2 = B.DeviceBank.from_host(b2.codes, b2.seq_off)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g1 = B.plast_index_bank(d1.codes, d1.seq_off, stream=side)
+        g2 = B.plast_index_bank(d2.codes, d2.seq_off, stream=side)
+        recs, _ = B.plast_search(g1, g2)  # current stream
+        assert same(B.gapped_numpy(recs), want)
+        g3 = B.plast_index_bank(d2.codes, d2.seq_off, stream=side)
+        g3.free()
