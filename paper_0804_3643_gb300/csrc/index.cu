@@ -71,41 +71,32 @@ __global__ void k_key_offsets(const uint64_t* skey, int64_t n, int64_t* key_off)
   }
 }
 
-// 16 bytes of pad from address s forwards (byte 0 = pad[s]), from aligned
-// words; pad has slack on both sides, so the rounded reads stay inside it.
-__device__ __forceinline__ uint4 bytes16_fwd(const int8_t* pad, int64_t s) {
-  const uint32_t* w = reinterpret_cast<const uint32_t*>(pad + (s & ~(int64_t)3));
-  const uint32_t sh = 8u * (uint32_t)(s & 3);
-  const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3), w4 = __ldg(w + 4);
-  return make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
-                    __funnelshift_r(w3, w4, sh));
-}
-
-// 16 bytes of pad from address s backwards (byte 0 = pad[s], byte 1 = pad[s-1], ...)
-__device__ __forceinline__ uint4 bytes16_bwd(const int8_t* pad, int64_t s) {
-  const uint4 f = bytes16_fwd(pad, s - 15);
-  return make_uint4(__byte_perm(f.w, 0u, 0x0123u), __byte_perm(f.z, 0u, 0x0123u), __byte_perm(f.y, 0u, 0x0123u),
-                    __byte_perm(f.x, 0u, 0x0123u));
-}
-
 // Window of indexed word i: cells 0..25 = pad[p .. p+25], cells 26..47 =
-// pad[p-1], pad[p-2], .., pad[p-22]; one thread per 16-byte chunk.
+// pad[p-1], pad[p-2], .., pad[p-22]; one thread per window.  The thread reads
+// the 48 bytes S[j] = pad[p - 22 + j] with 13 aligned word loads (pad has
+// slack on both sides, so the rounded range stays inside it), forms their 12
+// words with funnel shifts, and writes the window as three 16-byte stores:
+// cells 0-25 are S[22..47], cells 26-47 are S[21], S[20], .., S[0].
 __global__ void k_neighbourhoods(const int8_t* pad, const uint32_t* pos, int64_t n, int8_t* nb) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 3 * n; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / 3;
-    const int part = (int)(t - i * 3);
-    const int64_t p = pos[i];
-    uint4 out;
-    if (part == 0) {
-      out = bytes16_fwd(pad, p);  // cells 0-15
-    } else if (part == 1) {
-      const uint4 f = bytes16_fwd(pad, p + 16);  // cells 16-25: bytes 0-9
-      const uint4 b = bytes16_bwd(pad, p - 1);   // cells 26-31: bytes 0-5
-      out = make_uint4(f.x, f.y, __byte_perm(f.z, b.x, 0x5410u), __byte_perm(b.x, b.y, 0x5432u));
-    } else {
-      out = bytes16_bwd(pad, p - 7);  // cells 32-47
-    }
-    reinterpret_cast<uint4*>(nb)[t] = out;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = (int64_t)pos[i] - 22;
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(pad + (s0 & ~(int64_t)3));
+    const uint32_t sh = 8u * (uint32_t)(s0 & 3);
+    uint32_t raw[13], S[12];
+#pragma unroll
+    for (int k = 0; k < 13; k++) raw[k] = __ldg(w + k);
+#pragma unroll
+    for (int k = 0; k < 12; k++) S[k] = __funnelshift_r(raw[k], raw[k + 1], sh);
+    uint32_t o[12];
+#pragma unroll
+    for (int q = 0; q < 6; q++) o[q] = __funnelshift_r(S[5 + q], S[6 + q], 16);  // S[22 + 4q ..]
+    o[6] = __byte_perm(S[11], S[5], 0x4532u);                                   // S46 S47 S21 S20
+#pragma unroll
+    for (int q = 7; q < 12; q++) o[q] = __byte_perm(S[11 - q], 0u, 0x0123u);    // S[4(11-q)+3] .. S[4(11-q)]
+    uint4* d = reinterpret_cast<uint4*>(nb + i * WIN);
+    d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    d[2] = make_uint4(o[8], o[9], o[10], o[11]);
   }
 }
 
@@ -209,7 +200,7 @@ cudaError_t launch_key_offsets(const uint64_t* skey, int64_t n, int64_t* key_off
 cudaError_t launch_neighbourhoods(const int8_t* pad, const uint32_t* pos, int64_t n, int8_t* nb, cudaStream_t st) {
   if (n > 0) {
     note_launch();
-    k_neighbourhoods<<<grid_for(3 * n, 256), 256, 0, st>>>(pad, pos, n, nb);
+    k_neighbourhoods<<<grid_for(n, 256), 256, 0, st>>>(pad, pos, n, nb);
   }
   return cudaGetLastError();
 }

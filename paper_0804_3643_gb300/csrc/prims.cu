@@ -218,34 +218,56 @@ __global__ void k_radix_hist(const uint64_t* keys, int64_t n, int shift, int32_t
   hist[(int64_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
 }
 
+// Scatter of one tile: ranks by digit as in a stable counting sort, the tile
+// reordered by digit in shared memory, then written out digit run by digit
+// run (consecutive threads write consecutive addresses).
 __global__ void k_radix_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
-                                int shift, const int64_t* off, int64_t nt, const int64_t* n_dev) {
+                                int shift, const int32_t* hist, const int64_t* off, int64_t nt,
+                                const int64_t* n_dev) {
   n = count_of(n, n_dev);
-  __shared__ int64_t s_base[256];
+  __shared__ int64_t s_base[256];  // global start of this tile's run of digit d
+  __shared__ int s_start[256];     // start of digit d within the tile
   __shared__ int s_cnt[RS_WARPS][256];
   __shared__ int s_run[256];
+  __shared__ int s_wsum[RS_WARPS];
+  __shared__ uint64_t s_key[RS_TILE];
+  __shared__ uint32_t s_val[RS_TILE];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   s_base[tid] = off[(int64_t)tid * nt + blockIdx.x];
+  {  // exclusive scan of the tile's histogram over the digits (thread = digit)
+    const int c = hist[(int64_t)tid * nt + blockIdx.x];
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += s_wsum[w];
+    s_start[tid] = before + x - c;
+  }
   s_run[tid] = 0;
-  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   for (int r = 0; r < RS_ROUNDS; r++) {
 #pragma unroll
     for (int w = 0; w < RS_WARPS; w++) s_cnt[w][tid] = 0;
     __syncthreads();
-    int64_t i = base + r * RS_THREADS + tid;
-    bool valid = i < n;
-    uint64_t k = valid ? kin[i] : 0;
-    uint32_t v = valid ? vin[i] : 0;
-    int d = valid ? (int)((k >> shift) & 255) : 256 + lane;  // padding lanes get unique dummies
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int rank = __popc(peers & ((1u << lane) - 1u));
+    const int64_t i = base + r * RS_THREADS + tid;
+    const bool valid = i < n;
+    const uint64_t k = valid ? kin[i] : 0;
+    const uint32_t v = valid ? vin[i] : 0;
+    const int d = valid ? (int)((k >> shift) & 255) : 256 + lane;  // padding lanes get unique dummies
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
     __syncthreads();
     {
       int run = s_run[tid];
 #pragma unroll
       for (int w = 0; w < RS_WARPS; w++) {
-        int c = s_cnt[w][tid];
+        const int c = s_cnt[w][tid];
         s_cnt[w][tid] = run;
         run += c;
       }
@@ -253,11 +275,19 @@ __global__ void k_radix_scatter(const uint64_t* kin, const uint32_t* vin, uint64
     }
     __syncthreads();
     if (valid) {
-      int64_t dst = s_base[d] + s_cnt[warp][d] + rank;
-      kout[dst] = k;
-      vout[dst] = v;
+      const int lp = s_start[d] + s_cnt[warp][d] + rank;
+      s_key[lp] = k;
+      s_val[lp] = v;
     }
     __syncthreads();
+  }
+  const int in_tile = (int)min((int64_t)RS_TILE, n - base);
+  for (int j = tid; j < in_tile; j += RS_THREADS) {
+    const uint64_t k = s_key[j];
+    const int d = (int)((k >> shift) & 255);
+    const int64_t dst = s_base[d] + (j - s_start[d]);
+    kout[dst] = k;
+    vout[dst] = s_val[j];
   }
 }
 
@@ -288,7 +318,7 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     cudaError_t e = scan_exclusive(hist, off, (int64_t)h, nullptr, stmp, stmp_bytes, st);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_radix_scatter<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, off, nt, n_dev);
+    k_radix_scatter<<<(unsigned)nt, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, hist, off, nt, n_dev);
     uint64_t* tk = ki;
     ki = ko;
     ko = tk;
