@@ -250,3 +250,21 @@ def test_bank_built_on_another_stream(B):
         assert same(B.gapped_numpy(recs), want)
         g3 = B.plast_index_bank(d2.codes, d2.seq_off, stream=side)
         g3.free()
+
+
+def test_plastx_translated_queries(B):
+    # PLAST-X: a nucleotide query bank translated in six frames against a
+    # protein bank (the queries as bank 1)
+    b_prot, dna = synth.tplastn_workload(seed=15, scale=0.004)
+    aa, so, _ = B.plast_translate6(torch.from_numpy(dna.codes).cuda(), torch.from_numpy(dna.seq_off).cuda())
+    w_aa, w_so, _ = oracle.translate6(dna.codes, dna.seq_off)
+    assert np.array_equal(aa.cpu().numpy(), w_aa) and np.array_equal(so.cpu().numpy(), w_so)
+    gq = B.plast_index_bank(aa, so)
+    oq = oracle.make_bank(w_aa, w_so)
+    gp, op = both(B, b_prot.codes, b_prot.seq_off)
+    want_h = oracle.ungapped(oq, op, threads=8)
+    assert len(want_h) > 0
+    assert same(B.hits_numpy(B.plast_ungapped(gq, gp)), want_h)
+    recs, n_ung = B.plast_search(gq, gp)
+    assert n_ung == len(want_h)
+    assert same(B.gapped_numpy(recs), oracle.small_gapped(oq, op, want_h))
