@@ -277,7 +277,7 @@ int plast_set_schedule(int mode);
  * rows), from a cost model: a tile of shape S costs
  * S_slot x (rows of S) x ceil(n2 / P_S) x P_S + S_tile SM-nanoseconds, n2 the
  * key's bank-2 occurrences, P_S the bank-2 windows a CTA scores per pass
- * (128 wide, 1024 narrow).  plast_autotune measures the constants on the
+ * (128 wide, 512 narrow).  plast_autotune measures the constants on the
  * current device (random banks, the stage-2 kernel timed with every tile of
  * one shape, against a long and a short bank 2; about a second), installs
  * them and copies them to *out (may be NULL).  It also picks the wide kernel
@@ -306,12 +306,14 @@ int plast_set_tile_shape(int mode);
 /*
  * The stage-2 work list the library would run for two banks with the given
  * CSR key offsets (host arrays of PLAST_NKEYS + 1 entries each, as
- * plast_bank_export_index returns): host-only, no device needed.  Fills
- * tiles[4 * t ..] with (key, first bank-1 CSR index, rows, shape: 0 wide,
- * 1, 2, 3 narrow of 8, 4, 2 rows) in launch order for t < *n_tiles; PLAST_E_CAPACITY if more than
- * `cap` tiles (then *n_tiles = needed), PLAST_E_INVALID on decreasing offsets.
+ * plast_bank_export_index returns) on a GPU of n_sms SMs (0: no splitting of
+ * long lists): host-only, no device needed.  Fills tiles[6 * t ..] with (key,
+ * first bank-1 CSR index, rows, shape: 0 wide, 1, 2, 3 narrow of 8, 4, 2
+ * rows, first and end offset of its bank-2 windows in the key's list) in
+ * launch order for t < *n_tiles; PLAST_E_CAPACITY if more than `cap` tiles
+ * (then *n_tiles = needed), PLAST_E_INVALID on decreasing offsets.
  */
-int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t* tiles, int64_t cap,
+int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t n_sms, int32_t* tiles, int64_t cap,
                        int64_t* n_tiles);
 
 /*

@@ -125,7 +125,7 @@ def lib() -> ctypes.CDLL:
         L.plast_get_tile_costs.restype = ctypes.c_int
         L.plast_set_tile_costs.argtypes = [pCost]
         L.plast_set_tile_costs.restype = ctypes.c_int
-        L.plast_stage2_tiles.argtypes = [P, P, P, i64, pI64]
+        L.plast_stage2_tiles.argtypes = [P, P, i32, P, i64, pI64]
         L.plast_stage2_tiles.restype = ctypes.c_int
         L.plast_set_tile_shape.argtypes = [ctypes.c_int]
         L.plast_set_tile_shape.restype = ctypes.c_int
@@ -222,9 +222,10 @@ def plast_set_tile_shape(mode: int) -> None:
         raise PlastError("plast_set_tile_shape", rc)
 
 
-def plast_stage2_tiles(key_off1: np.ndarray, key_off2: np.ndarray) -> np.ndarray:
-    """Host-only: the stage-2 tiles [t, 4] = (key, first bank-1 CSR index,
-    rows, shape) for two banks' CSR key offsets."""
+def plast_stage2_tiles(key_off1: np.ndarray, key_off2: np.ndarray, n_sms: int = 0) -> np.ndarray:
+    """Host-only: the stage-2 tiles [t, 6] = (key, first bank-1 CSR index,
+    rows, shape, first and end bank-2 offset in the key's list) for two
+    banks' CSR key offsets, long lists cut for a GPU of ``n_sms`` SMs."""
     k1 = np.ascontiguousarray(key_off1, dtype=np.int64)
     k2 = np.ascontiguousarray(key_off2, dtype=np.int64)
     if len(k1) != NKEYS + 1 or len(k2) != NKEYS + 1:
@@ -232,8 +233,9 @@ def plast_stage2_tiles(key_off1: np.ndarray, key_off2: np.ndarray) -> np.ndarray
     n = ctypes.c_int64()
     cap = 0
     for _ in range(2):
-        out = np.zeros((max(cap, 1), 4), dtype=np.int32)
-        rc = lib().plast_stage2_tiles(k1.ctypes.data, k2.ctypes.data, out.ctypes.data, cap, ctypes.byref(n))
+        out = np.zeros((max(cap, 1), 6), dtype=np.int32)
+        rc = lib().plast_stage2_tiles(k1.ctypes.data, k2.ctypes.data, int(n_sms), out.ctypes.data, cap,
+                                      ctypes.byref(n))
         if rc == PLAST_E_CAPACITY:
             cap = n.value
             continue

@@ -7,6 +7,7 @@
 // of the computation runs in the kernels of index.cu, ungapped.cu, gapped.cu
 // and prims.cu.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -128,7 +129,7 @@ plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1
 // 0: by cost; 1: wide only; 2, 3, 4: narrow tiles of 8, 4, 2 rows only
 std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
-constexpr int64_t NARROW_PASS = (UNG_THREADS / 32) * 32;  // narrow tiles
+constexpr int64_t NARROW_PASS = UNG_NARROW_PASS;           // narrow tiles
 int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) & ~(g - 1); }  // g a power of two
 static_assert((WIDE_PASS & (WIDE_PASS - 1)) == 0 && (NARROW_PASS & (NARROW_PASS - 1)) == 0, "passes");
 
@@ -175,8 +176,49 @@ struct TileList {
   int64_t pairs = 0;
 };
 
+// When a launch has too few tiles to keep its CTAs busy to the end (a small
+// query bank: a few hundred keys with one or two bank-1 occurrences), the
+// costliest tiles are cut along their bank-2 lists into pieces of whole
+// passes, so that no piece costs more than about 1/4 of a CTA's share; the
+// pieces re-sorted costliest first.  v[lo, hi) is one launch's tile list.
+void split_long_tiles(const plast_tile_costs& c, std::vector<int4>& v, int64_t lo, int64_t hi, int64_t ctas) {
+  if (hi <= lo || ctas <= 0) return;
+  auto cost = [&](const int4& t) { return tile_cost(c, tile_shape(t), (int64_t)t.w - t.z); };
+  double total = 0;
+  for (int64_t i = lo; i < hi; i++) total += cost(v[i]);
+  const double target = total / (4.0 * (double)ctas);
+  bool any = false;
+  for (int64_t i = lo; i < hi && !any; i++) any = cost(v[i]) > 2 * target;
+  if (!any) return;
+  std::vector<std::pair<double, int4>> out;
+  out.reserve((size_t)(hi - lo) * 2);
+  for (int64_t i = lo; i < hi; i++) {
+    const int4 t = v[i];
+    const double ct = cost(t);
+    const int shape = tile_shape(t);
+    const int64_t pass = shape == UNG_WIDE ? WIDE_PASS : NARROW_PASS, n2 = (int64_t)t.w - t.z;
+    const int64_t pieces = std::min<int64_t>((int64_t)std::ceil(ct / target), (n2 + pass - 1) / pass);
+    if (ct <= 2 * target || pieces < 2) {
+      out.push_back({ct, t});
+      continue;
+    }
+    const int64_t chunk = round_up((n2 + pieces - 1) / pieces, pass);
+    for (int64_t a = 0; a < n2; a += chunk) {
+      const int4 p = make_tile(tile_key(t), t.y, tile_rows(t), shape, t.z + (int)a,
+                               t.z + (int)std::min<int64_t>(a + chunk, n2));
+      out.push_back({cost(p), p});
+    }
+  }
+  std::stable_sort(out.begin(), out.end(),
+                   [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) { return x.first > y.first; });
+  std::vector<int4> nv(v.begin(), v.begin() + lo);
+  for (const auto& x : out) nv.push_back(x.second);
+  nv.insert(nv.end(), v.begin() + hi, v.end());
+  v.swap(nv);
+}
+
 void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first, TileList* tl,
-                      const std::vector<char>* key_mask, int shape_override) {
+                      const std::vector<char>* key_mask, int shape_override, int n_sms) {
   tl->tiles.clear();
   tl->pairs = 0;
   tl->n_wide = 0;
@@ -222,8 +264,9 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
   if (out) out->reserve((size_t)(rows_total / UNG_T1 + 4 * keys.size()));
   else wide.reserve((size_t)(rows_total / UNG_T1 + keys.size()));
   double cost_now[4] = {0, 0, 0, 0};  // tile costs of the current key's n2
+  int32_t n2_now = 0;
   auto emit = [&](int k, int64_t first, int64_t rows, int shape) {
-    const int4 t = make_int4(k, (int)first, (int)rows, shape);
+    const int4 t = make_tile(k, (int)first, (int)rows, shape, 0, n2_now);
     if (out) out->push_back(t);
     else if (shape == UNG_WIDE) wide.push_back(t);
     else by_shape[shape].push_back({(float)cost_now[shape], t});
@@ -232,6 +275,7 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     const int64_t n1 = ko1[k + 1] - ko1[k];
     const int64_t n2 = ko2[k + 1] - ko2[k];
     tl->pairs += n1 * n2;
+    n2_now = (int32_t)n2;
     for (int shape = UNG_NARROW; shape <= UNG_NARROW2; shape++) cost_now[shape] = tile_cost(c, shape, n2);
     int64_t u = ko1[k];
     const int64_t end = ko1[k + 1];
@@ -276,7 +320,7 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     }
   }
   if (!largest_first) {
-    for (const int4& t : tl->tiles) tl->n_wide += t.w == UNG_WIDE;
+    for (const int4& t : tl->tiles) tl->n_wide += tile_shape(t) == UNG_WIDE;
     return;
   }
   // wide tiles (one launch), then the narrow ones (another), costliest first:
@@ -298,6 +342,15 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     if (pickd < 0) break;
     tl->tiles.push_back(by_shape[pickd][at[pickd]++].second);
   }
+  if (n_sms > 0) {
+    std::vector<int4> wide(tl->tiles.begin(), tl->tiles.begin() + tl->n_wide);
+    std::vector<int4> narrow(tl->tiles.begin() + tl->n_wide, tl->tiles.end());
+    split_long_tiles(c, wide, 0, (int64_t)wide.size(), (int64_t)n_sms);
+    split_long_tiles(c, narrow, 0, (int64_t)narrow.size(), (int64_t)UNG_NARROW_CTAS_PER_SM * n_sms);
+    tl->tiles.assign(wide.begin(), wide.end());
+    tl->n_wide = (int64_t)wide.size();
+    tl->tiles.insert(tl->tiles.end(), narrow.begin(), narrow.end());
+  }
 }
 
 // Queues stage 2 over the tile list (its device copy is a.tiles): in the
@@ -313,7 +366,8 @@ cudaError_t launch_tiles(const TileList& tl, UngArgs a, int32_t* counters, bool 
     a.n_tiles = (int32_t)(hi - lo);
     a.tile_counter = counter;
     a.persistent = persistent ? 1 : 0;
-    const int grid = persistent ? (int)std::min<int64_t>(num_sms(), hi - lo) : (int)(hi - lo);
+    const int per_sm = wide ? 1 : UNG_NARROW_CTAS_PER_SM;
+    const int grid = persistent ? (int)std::min<int64_t>((int64_t)per_sm * num_sms(), hi - lo) : (int)(hi - lo);
     return wide ? launch_ungapped(a, grid, st) : launch_ungapped_narrow(a, grid, st);
   };
   if (persistent) {
@@ -322,9 +376,10 @@ cudaError_t launch_tiles(const TileList& tl, UngArgs a, int32_t* counters, bool 
   }
   for (int64_t i = 0; i < nt;) {
     int64_t j = i;
-    while (j < nt && tl.tiles[j].x == tl.tiles[i].x && tl.tiles[j].w == UNG_WIDE) j++;
+    const int key = tile_key(tl.tiles[i]);
+    while (j < nt && tile_key(tl.tiles[j]) == key && tile_shape(tl.tiles[j]) == UNG_WIDE) j++;
     int64_t k = j;
-    while (k < nt && tl.tiles[k].x == tl.tiles[i].x) k++;
+    while (k < nt && tile_key(tl.tiles[k]) == key) k++;
     cudaError_t e = run(i, j, true, counters);
     if (e == cudaSuccess) e = run(j, k, false, counters + 1);
     if (e != cudaSuccess) return e;
@@ -335,7 +390,8 @@ cudaError_t launch_tiles(const TileList& tl, UngArgs a, int32_t* counters, bool 
 
 void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first, TileList* tl,
                  const std::vector<char>* key_mask = nullptr, int shape_override = -1) {
-  build_tiles_from(b1->h_key_off.data(), b2->h_key_off.data(), largest_first, tl, key_mask, shape_override);
+  build_tiles_from(b1->h_key_off.data(), b2->h_key_off.data(), largest_first, tl, key_mask, shape_override,
+                   largest_first ? num_sms() : 0);
 }
 
 // Device state shared by the stage-2 calls: sorted survivor keys and values.
@@ -1167,8 +1223,7 @@ int time_stage2(const plast_bank* b1, const plast_bank* b2, int shape, cudaStrea
   build_tiles(b1, b2, true, &tl, nullptr, shape);
   *slots = 0;
   for (const int4& t : tl.tiles) {
-    const int64_t n2 = b2->h_key_off[t.x + 1] - b2->h_key_off[t.x];
-    *slots += shape_slots(t.w, n2);
+    *slots += shape_slots(tile_shape(t), (int64_t)t.w - t.z);
   }
   *tiles = (double)tl.tiles.size();
   *ms = 0;
@@ -1262,21 +1317,27 @@ int plast_set_tile_costs(const plast_tile_costs* c) {
   return PLAST_OK;
 }
 
-int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t* tiles, int64_t cap,
+int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t n_sms, int32_t* tiles, int64_t cap,
                        int64_t* n_tiles) {
-  if (!key_off1 || !key_off2 || !n_tiles || cap < 0 || (cap > 0 && !tiles)) return PLAST_E_INVALID;
+  if (!key_off1 || !key_off2 || !n_tiles || cap < 0 || n_sms < 0 || (cap > 0 && !tiles)) return PLAST_E_INVALID;
   for (int k = 0; k < NKEYS; k++)
-    if (key_off1[k + 1] < key_off1[k] || key_off2[k + 1] < key_off2[k] || key_off1[k + 1] > INT32_MAX)
+    if (key_off1[k + 1] < key_off1[k] || key_off2[k + 1] < key_off2[k] || key_off1[k + 1] > INT32_MAX ||
+        key_off2[k + 1] - key_off2[k] > INT32_MAX)
       return PLAST_E_INVALID;
   TileList tl;
-  build_tiles_from(key_off1, key_off2, g_schedule.load() == 0, &tl, nullptr, -1);
+  const bool persistent = g_schedule.load() == 0;
+  build_tiles_from(key_off1, key_off2, persistent, &tl, nullptr, -1, persistent ? n_sms : 0);
   *n_tiles = (int64_t)tl.tiles.size();
   if (*n_tiles > cap) return PLAST_E_CAPACITY;
   for (size_t i = 0; i < tl.tiles.size(); i++) {
-    tiles[4 * i] = tl.tiles[i].x;
-    tiles[4 * i + 1] = tl.tiles[i].y;
-    tiles[4 * i + 2] = tl.tiles[i].z;
-    tiles[4 * i + 3] = tl.tiles[i].w;
+    const int4 t = tl.tiles[i];
+    int32_t* o = tiles + 6 * i;
+    o[0] = tile_key(t);
+    o[1] = t.y;
+    o[2] = tile_rows(t);
+    o[3] = tile_shape(t);
+    o[4] = t.z;
+    o[5] = t.w;
   }
   return PLAST_OK;
 }

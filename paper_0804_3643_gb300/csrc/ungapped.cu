@@ -89,7 +89,12 @@ constexpr int NSTRIDE = 52;                                // staged window stri
 constexpr int NPLANE = WIN * NCODE * 4;                     // 4224: one plane of 4 rows
 constexpr int NPROF_BYTES = 2 * NPLANE;                     // 8448
 constexpr int NROWS_BYTES = WIN * UNG_NT1;                 // 384, cell-major
-constexpr int NSTAGE_BYTES = NWARPS * 32 * NSTRIDE;        // 53248: one window per lane
+constexpr int NT_THREADS = 512;                            // narrow kernel: 2 CTAs of 16 warps per SM
+constexpr int NT_WARPS = NT_THREADS / 32;
+constexpr int NSTAGE_BYTES = NT_WARPS * 32 * NSTRIDE;      // 26624: one window per lane
+constexpr int NWKEY_BYTES = NT_WARPS * WBUF * 8;           // 4096
+constexpr int NWVAL_BYTES = NT_WARPS * WBUF * 4;           // 2048
+static_assert(UNG_NARROW_PASS == NT_WARPS * 32, "narrow pass = one window per lane");
 static_assert(NPROF_BYTES % 16 == 0 && NROWS_BYTES % 16 == 0 && (32 * NSTRIDE) % 16 == 0, "alignment");
 static_assert(Wide<UNG_MAX_N16>::SMEM <= 232448, "shared memory per CTA");
 
@@ -304,8 +309,8 @@ __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int
 // The next tile of a CTA, read by one thread while the CTA works on the
 // current one.
 struct TileSlot {
-  int4 tile;       // (key, first bank-1 CSR index, rows, shape)
-  int64_t v0, v1;  // the key's bank-2 CSR range
+  int4 tile;       // the tile (make_tile)
+  int64_t v0, v1;  // its bank-2 CSR range
   int t;           // tile index (>= n_tiles: none left)
 };
 static_assert(sizeof(TileSlot) <= 48, "tile slot size");
@@ -314,9 +319,10 @@ __device__ __forceinline__ void fetch_tile(const UngArgs& a, int t, TileSlot* sl
   slot->t = t;
   if (t < a.n_tiles) {
     const int4 tl = a.tiles[a.tile_base + t];
+    const int64_t base = a.key_off2[tile_key(tl)];
     slot->tile = tl;
-    slot->v0 = a.key_off2[tl.x];
-    slot->v1 = a.key_off2[tl.x + 1];
+    slot->v0 = base + tl.z;
+    slot->v1 = base + tl.w;
   }
 }
 
@@ -359,14 +365,14 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
                                             uint64_t* my_wk, uint32_t* my_wv, int& wcnt) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
-  for (int i = tid; i < NROWS_BYTES; i += UNG_THREADS) {
+  for (int i = tid; i < NROWS_BYTES; i += NT_THREADS) {
     const int r = i & (UNG_NT1 - 1), k = i / UNG_NT1;
     nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
   }
   __syncthreads();
   // cells 4 .. 47 at their own slots; slots 0, 1, 2 hold the folded seed
   // planes P1, M1, P2 (as in the wide tiles); slot 3 is unused
-  for (int e = tid; e < WIN * NCODE; e += UNG_THREADS) {
+  for (int e = tid; e < WIN * NCODE; e += NT_THREADS) {
     const int k = e / NCODE, b = e - k * NCODE;
     if (k == 3) continue;
     uint32_t w[2];
@@ -417,7 +423,7 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     const int v = warp * 32 + nw[j];
     pre[j] = v < n2 ? __ldg(src + (int64_t)v * 3 + np[j]) : sent16;
   }
-  for (int vb = warp * 32; vb < n2; vb += NWARPS * 32) {
+  for (int vb = warp * 32; vb < n2; vb += NT_WARPS * 32) {
     const bool vok = vb + lane < n2;
     __syncwarp();
 #pragma unroll
@@ -431,7 +437,7 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      const int vn = vb + NWARPS * 32 + nw[j];
+      const int vn = vb + NT_WARPS * 32 + nw[j];
       pre[j] = vn < n2 ? __ldg(src + (int64_t)vn * 3 + np[j]) : sent16;
     }
     uint32_t s[NW], m[NW];
@@ -489,7 +495,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
     const int4 tile = slots[buf].tile;
     const int64_t v0 = slots[buf].v0, v1 = slots[buf].v1;
     if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : a.n_tiles, &slots[buf ^ 1]);
-    const int rows = tile.z;
+    const int rows = tile_rows(tile);
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
 
     {
@@ -602,19 +608,22 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
 }
 
 // Narrow tiles (8, 4 or 2 rows) in their own persistent kernel, so that the
-// wide kernel's registers and schedule are its own.
-constexpr int NARROW_SMEM = TAB_BYTES + NROWS_BYTES + NPROF_BYTES + NSTAGE_BYTES + WKEY_BYTES + WVAL_BYTES + 2 * 48;
+// wide kernel's registers and schedule are its own; two CTAs of 512 threads
+// per SM, so that one CTA's tile changes (profile build, barriers) overlap
+// the other's scoring.
+constexpr int NARROW_SMEM = TAB_BYTES + NROWS_BYTES + NPROF_BYTES + NSTAGE_BYTES + NWKEY_BYTES + NWVAL_BYTES + 2 * 48;
 static_assert((TAB_BYTES + NROWS_BYTES + NPROF_BYTES + NSTAGE_BYTES) % 16 == 0, "alignment");
+static_assert(2 * NARROW_SMEM <= 228 * 1024, "two narrow CTAs per SM");
 
-__global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped_narrow(UngArgs a) {
+__global__ void __launch_bounds__(NT_THREADS, 2) k_ungapped_narrow(UngArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   int8_t* tab = reinterpret_cast<int8_t*>(smem);
   uint8_t* nrows = smem + TAB_BYTES;
   unsigned char* nprof = smem + TAB_BYTES + NROWS_BYTES;
   unsigned char* nstage = smem + TAB_BYTES + NROWS_BYTES + NPROF_BYTES;
   uint64_t* wkey = reinterpret_cast<uint64_t*>(nstage + NSTAGE_BYTES);
-  uint32_t* wval = reinterpret_cast<uint32_t*>(nstage + NSTAGE_BYTES + WKEY_BYTES);
-  TileSlot* slots = reinterpret_cast<TileSlot*>(nstage + NSTAGE_BYTES + WKEY_BYTES + WVAL_BYTES);
+  uint32_t* wval = reinterpret_cast<uint32_t*>(nstage + NSTAGE_BYTES + NWKEY_BYTES);
+  TileSlot* slots = reinterpret_cast<TileSlot*>(nstage + NSTAGE_BYTES + NWKEY_BYTES + NWVAL_BYTES);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t* my_wk = wkey + warp * WBUF;
@@ -623,7 +632,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped_narrow(UngArgs a) {
   const uint32_t my_nrow = (uint32_t)__cvta_generic_to_shared(my_nstage + lane * NSTRIDE);
   int wcnt = 0;
 
-  for (int i = tid; i < NCODE * NCODE; i += UNG_THREADS) tab[i] = c_score[i];
+  for (int i = tid; i < NCODE * NCODE; i += NT_THREADS) tab[i] = c_score[i];
   const uint32_t s1x2 = ((uint32_t)(uint16_t)a.s1 << 16) | (uint16_t)a.s1;
   if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : (int)blockIdx.x, &slots[0]);
   __syncthreads();
@@ -632,11 +641,12 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped_narrow(UngArgs a) {
     const int4 tile = slots[buf].tile;
     const int64_t v0 = slots[buf].v0, v1 = slots[buf].v1;
     if (tid == 0) fetch_tile(a, a.persistent ? atomicAdd(a.tile_counter, 1) : a.n_tiles, &slots[buf ^ 1]);
-    const int rows = tile.z;
+    const int rows = tile_rows(tile);
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
-    if (tile.w == UNG_NARROW)
+    const int shape = tile_shape(tile);
+    if (shape == UNG_NARROW)
       narrow_tile<4>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
-    else if (tile.w == UNG_NARROW4)
+    else if (shape == UNG_NARROW4)
       narrow_tile<2>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
     else
       narrow_tile<1>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
@@ -691,7 +701,7 @@ cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st) 
   }
   if (grid <= 0) return cudaSuccess;
   note_launch();
-  k_ungapped_narrow<<<grid, UNG_THREADS, NARROW_SMEM, st>>>(a);
+  k_ungapped_narrow<<<grid, NT_THREADS, NARROW_SMEM, st>>>(a);
   return cudaGetLastError();
 }
 

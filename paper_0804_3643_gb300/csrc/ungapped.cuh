@@ -10,6 +10,16 @@ constexpr int UNG_NARROW = 1;
 constexpr int UNG_NARROW4 = 2;
 constexpr int UNG_NARROW2 = 3;
 
+// A stage-2 tile: x = key | shape << 14 | rows << 16, y = first bank-1 CSR
+// index of its rows, [z, w) = the bank-2 windows it scores, as offsets in
+// the key's list (a long list may be cut over several tiles).
+__host__ __device__ inline int4 make_tile(int key, int first, int rows, int shape, int vlo, int vhi) {
+  return make_int4(key | (shape << 14) | (rows << 16), first, vlo, vhi);
+}
+__host__ __device__ inline int tile_key(const int4& t) { return t.x & 0x3fff; }
+__host__ __device__ inline int tile_shape(const int4& t) { return (t.x >> 14) & 3; }
+__host__ __device__ inline int tile_rows(const int4& t) { return (t.x >> 16) & 0xff; }
+
 struct UngArgs {
   const int8_t* nb1;        // bank-1 windows [n_idx1][48]
   const uint32_t* pos1;     // bank-1 padded positions, CSR order
@@ -39,6 +49,8 @@ void set_ungapped_variant(int v);  // -1: the default
 // wide tiles (the current variant) / narrow tiles, each a persistent launch
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st);
+constexpr int UNG_NARROW_CTAS_PER_SM = 2;
+constexpr int UNG_NARROW_PASS = 512;  // bank-2 windows a narrow CTA scores per pass
 cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
                                const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
                                int32_t n2, plast_hit* out, int* bad, cudaStream_t st);

@@ -47,9 +47,9 @@ def round_up(n, g):
 
 
 def tile_cost(c, shape, n2):
-    # a CTA scores 128 (wide) or 1024 (narrow) bank-2 windows per pass
+    # a CTA scores 128 (wide) or 512 (narrow) bank-2 windows per pass
     name = {WIDE: "wide", NARROW: "narrow", NARROW4: "narrow4", NARROW2: "narrow2"}[shape]
-    return c[name + "_slot"] * ROWS[shape] * round_up(n2, 128 if shape == WIDE else 1024) + c[name + "_tile"]
+    return c[name + "_slot"] * ROWS[shape] * round_up(n2, 128 if shape == WIDE else 512) + c[name + "_tile"]
 
 
 def tail_cover(c, t, n2):
@@ -71,11 +71,21 @@ def tail_cover(c, t, n2):
 
 
 def check_cover(tiles, k1, n1, n2):
-    by_key = {}
-    for key, first, rows, shape in tiles:
+    """Rows: every bank-1 occurrence of a shared key in exactly one row range;
+    windows: for each row range, the bank-2 ranges of its pieces partition
+    [0, n2) of the key's list in whole passes (the last piece ragged)."""
+    by_key, pieces = {}, {}
+    for key, first, rows, shape, vlo, vhi in tiles:
         assert shape in ROWS
         assert 1 <= rows <= ROWS[shape]
-        by_key.setdefault(int(key), []).append((int(first), int(rows), int(shape)))
+        assert 0 <= vlo < vhi <= n2[key]
+        pieces.setdefault((int(key), int(first), int(rows), int(shape)), []).append((int(vlo), int(vhi)))
+    for (key, first, rows, shape), v in pieces.items():
+        v.sort()
+        assert v[0][0] == 0 and v[-1][1] == n2[key]
+        for (a, b), (a2, _) in zip(v, v[1:]):
+            assert b == a2 and (b - a) % (128 if shape == WIDE else 512) == 0
+        by_key.setdefault(key, []).append((first, rows, shape))
     for k in range(NK):
         if n1[k] == 0 or n2[k] == 0:
             assert k not in by_key
@@ -94,6 +104,8 @@ def test_cover_and_shapes_by_cost(costs):
     k1, k2 = offsets(n1), offsets(n2)
     tiles = B.plast_stage2_tiles(k1, k2)
     by_key = check_cover(tiles, k1, n1, n2)
+    # no SM count given: no list is cut
+    assert (tiles[:, 4] == 0).all() and (tiles[:, 5] == n2[tiles[:, 0]]).all()
     for k, t in by_key.items():
         t = sorted(t)
         full = n1[k] // T1
@@ -118,7 +130,7 @@ def test_cover_and_shapes_by_cost(costs):
     n_wide = int(wide.sum())
     assert wide[:n_wide].all() and not wide[n_wide:].any()
     for part in (tiles[:n_wide], tiles[n_wide:]):
-        c = [tile_cost(costs, s, n2[key]) for key, _, _, s in part]
+        c = [tile_cost(costs, s, hi - lo) for _, _, _, s, lo, hi in part]
         assert all(a >= b for a, b in zip(c, c[1:]))
     # every shape occurs in this mix
     for shape in ROWS:
@@ -154,6 +166,28 @@ def test_small_query_goes_narrow(costs):
     for n, shape in [(1, NARROW2), (2, NARROW2), (4, NARROW4), (8, NARROW)]:
         tiles = B.plast_stage2_tiles(offsets(np.full(NK, n, dtype=np.int64)), offsets(n2))
         assert (tiles[:, 3] == shape).all() and len(tiles) == NK, n
+
+
+def test_few_tiles_cut_long_lists(costs):
+    # a two-protein query: a few hundred keys with one occurrence each against
+    # long bank-2 lists, fewer tiles than the narrow launch's CTAs
+    rng = np.random.default_rng(8)
+    n1 = np.zeros(NK, dtype=np.int64)
+    n1[rng.choice(NK, 300, replace=False)] = 1
+    n2 = rng.integers(1000, 60000, size=NK).astype(np.int64)
+    k1, k2 = offsets(n1), offsets(n2)
+    whole = B.plast_stage2_tiles(k1, k2)
+    cut = B.plast_stage2_tiles(k1, k2, n_sms=152)
+    assert len(whole) == 300 and len(cut) > 2 * 152
+    check_cover(cut, k1, n1, n2)
+    cost = [tile_cost(costs, s, hi - lo) for _, _, _, s, lo, hi in cut]
+    assert all(a >= b for a, b in zip(cost, cost[1:]))
+    # no piece above twice the target of a quarter of a CTA's share
+    assert max(cost) <= 2 * sum(cost) / (4 * 2 * 152) + tile_cost(costs, NARROW2, 512)
+    # a large mix has tiles enough: nothing is cut
+    n1, n2 = random_counts(rng)
+    k1, k2 = offsets(n1), offsets(n2)
+    assert (B.plast_stage2_tiles(k1, k2, n_sms=152) == B.plast_stage2_tiles(k1, k2)).all()
 
 
 def test_bad_offsets(costs):
