@@ -38,7 +38,7 @@ assert HIT_DTYPE.itemsize == 20 and GAPPED_DTYPE.itemsize == 28
 
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2")]
+                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2", "s0")]
 
 
 @dataclass
@@ -46,7 +46,8 @@ class Params:
     """Method parameters.  w, nl, nr: Section 3.3.2 neighbourhoods (48-cell
     window of Annex 4 read as 22 + 4 + 22); s1, s2: thresholds of Section
     3.2; lg, band: extent of the small gapped extension of Section 3.3.4;
-    gap_open / gap_extend: a gap of length k costs open + k * extend."""
+    gap_open / gap_extend: a gap of length k costs open + k * extend; s0:
+    Section 4.2's filter threshold (0: no filter)."""
     w: int = 4
     nl: int = 22
     nr: int = 22
@@ -56,10 +57,11 @@ class Params:
     gap_open: int = 11
     gap_extend: int = 1
     s2: int = 47
+    s0: int = 0
 
     def c(self) -> _Params:
         return _Params(self.w, self.nl, self.nr, self.s1, self.lg, self.band,
-                       self.gap_open, self.gap_extend, self.s2)
+                       self.gap_open, self.gap_extend, self.s2, self.s0)
 
 
 def build(force: bool = False) -> str:
@@ -96,7 +98,9 @@ def lib() -> ctypes.CDLL:
         L.oracle_gapped_side.restype = i32
         L.oracle_small_gapped_pair.argtypes = [P, i64, i64, P, i64, i64, P, P, P, P, P]
         L.oracle_small_gapped_pair.restype = i32
-        L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, P, i32, P, P]
+        L.oracle_filter_pair.argtypes = [P, i64, i64, P, i64, i64, P]
+        L.oracle_filter_pair.restype = i32
+        L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, P, i32, P, P, P]
         L.oracle_ungapped.restype = i64
         L.oracle_small_gapped.argtypes = [P, P, P, P, P, P, i64, P]
         L.oracle_small_gapped.restype = i64
@@ -173,6 +177,14 @@ def ungapped_pair(s1, p1: int, s2, p2: int, params: Params = Params()):
     return u, rl.value, ll.value
 
 
+def filter_pair(s1, p1: int, s2, p2: int, params: Params = Params()) -> int:
+    """Section 4.2's raw score of the pair at seed starts p1, p2: the sum of
+    the positive substitution scores over the ungapped window."""
+    a, b = _i8(s1), _i8(s2)
+    prm = params.c()
+    return lib().oracle_filter_pair(_p(a), a.size, p1, _p(b), b.size, p2, ctypes.byref(prm))
+
+
 @dataclass
 class Bank:
     codes: np.ndarray    # int8, concatenated residues
@@ -194,9 +206,12 @@ def make_bank(codes, seq_off) -> Bank:
 
 
 def ungapped(b1: Bank, b2: Bank, params: Params = Params(), key_lo: int = 0, key_hi: int = NKEYS,
-             threads: int = 1, return_pairs: bool = False, keys=None):
+             threads: int = 1, return_pairs: bool = False, keys=None, return_filtered: bool = False):
     """Stages 1-2 over keys [key_lo, key_hi) (or over the key list ``keys``):
-    ungapped hits with U >= s1, sorted by (seq1, pos1, seq2, pos2)."""
+    ungapped hits with U >= s1, sorted by (seq1, pos1, seq2, pos2).  With
+    params.s0 > 0, only pairs through Section 4.2's filter are extended.
+    ``return_pairs`` adds the number of pairs, ``return_filtered`` the number
+    of them that went through the filter."""
     b1.indexed()
     b2.indexed()
     klist = None
@@ -204,17 +219,18 @@ def ungapped(b1: Bank, b2: Bank, params: Params = Params(), key_lo: int = 0, key
         klist = np.ascontiguousarray(keys, dtype=np.int32)
         key_lo, key_hi = 0, len(klist)
     out = ctypes.c_void_p()
-    pairs = ctypes.c_int64()
+    pairs, filtered = ctypes.c_int64(), ctypes.c_int64()
     prm = params.c()
     L = lib()
     n = L.oracle_ungapped(_p(b1.codes), _p(b1.seq_off), b1.n_seqs, _p(b1.idx.key_off), _p(b1.idx.pos),
                           _p(b2.codes), _p(b2.seq_off), b2.n_seqs, _p(b2.idx.key_off), _p(b2.idx.pos),
                           ctypes.byref(prm), key_lo, key_hi, _p(klist) if klist is not None else None, threads,
-                          ctypes.byref(out), ctypes.byref(pairs))
+                          ctypes.byref(out), ctypes.byref(pairs), ctypes.byref(filtered))
     buf = (ctypes.c_char * (n * HIT_DTYPE.itemsize)).from_address(out.value) if n else b""
     hits = np.frombuffer(bytes(buf), dtype=HIT_DTYPE).copy()
     L.oracle_free(out)
-    return (hits, pairs.value) if return_pairs else hits
+    res = (hits,) + ((pairs.value,) if return_pairs else ()) + ((filtered.value,) if return_filtered else ())
+    return res if len(res) > 1 else hits
 
 
 # --------------------------------------------------------------------------

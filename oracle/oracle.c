@@ -17,6 +17,8 @@
  *   seed_class / seed_key ....... Section 3.3.1 example and class counts
  *   index ....................... brute-force enumeration of words
  *   ungapped_pair ............... identity closed form, brute force, symmetry
+ *   filter_pair ................. bound U <= F, identity closed form, worked
+ *                                 example, brute force
  *   gapped_side / small_gapped .. band-0 reduction, Smith-Waterman bound and
  *                                 equality, single-gap closed form, symmetry
  *   translate6 .................. genetic-code degeneracy, back-translation
@@ -169,6 +171,7 @@ int64_t oracle_index(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
  * ---------------------------------------------------------------------- */
 typedef struct {
   int32_t w, nl, nr, s1, lg, band, gap_open, gap_extend, s2;
+  int32_t s0; /* Section 4.2's filter threshold; 0 = no filter */
 } oracle_params;
 
 /* ------------------------------------------------------------------------
@@ -211,6 +214,31 @@ int32_t oracle_ungapped_pair(const int8_t* s1, int64_t len1, int64_t p1, const i
   if (rlen) *rlen = rl;
   if (llen) *llen = ll;
   return best;
+}
+
+/* ------------------------------------------------------------------------
+ * Section 4.2's filter: the raw score of two neighbourhoods is the sum of
+ * the substitution scores of the residue pairs that score above zero,
+ * taken here over the same window, clipped at the sequence ends the same
+ * way, as the ungapped extension above (a reading: the paper's example uses
+ * 12-residue subsequences; its filter runs on the neighbourhood blocks of
+ * stage 2).  A pair goes on to the ungapped extension only if this score
+ * reaches S0.
+ * ---------------------------------------------------------------------- */
+int32_t oracle_filter_pair(const int8_t* s1, int64_t len1, int64_t p1, const int8_t* s2, int64_t len2, int64_t p2,
+                           const oracle_params* prm) {
+  int64_t tr = prm->w + prm->nr;
+  if (len1 - p1 < tr) tr = len1 - p1;
+  if (len2 - p2 < tr) tr = len2 - p2;
+  int64_t tl = prm->nl;
+  if (p1 < tl) tl = p1;
+  if (p2 < tl) tl = p2;
+  int32_t f = 0;
+  for (int64_t t = -tl; t < tr; t++) {
+    int32_t sc = B62[s1[p1 + t]][s2[p2 + t]];
+    if (sc > 0) f += sc;
+  }
+  return f;
 }
 
 /* ------------------------------------------------------------------------
@@ -366,7 +394,7 @@ typedef struct {
   pthread_mutex_t* lock;
   oracle_hit* out;
   int64_t n, cap;
-  int64_t pairs;
+  int64_t pairs, filtered; /* pairs extended; of them, pairs through the filter */
 } ungapped_job;
 
 static void push_hit(ungapped_job* j, oracle_hit h) {
@@ -397,10 +425,14 @@ static void* ungapped_worker(void* arg) {
         int32_t q2 = seq_of(b2->seq_off, b2->n_seqs, g2);
         int64_t o2 = b2->seq_off[q2];
         int64_t len2 = b2->seq_off[q2 + 1] - o2;
+        j->pairs++;
+        if (j->prm->s0 > 0 &&
+            oracle_filter_pair(b1->codes + o1, len1, g1 - o1, b2->codes + o2, len2, g2 - o2, j->prm) < j->prm->s0)
+          continue; /* Section 4.2: filtered out before the ungapped extension */
+        j->filtered++;
         int32_t rl, ll;
         int32_t u_score = oracle_ungapped_pair(b1->codes + o1, len1, g1 - o1, b2->codes + o2, len2, g2 - o2, j->prm,
                                                &rl, &ll);
-        j->pairs++;
         if (u_score >= j->prm->s1) {
           oracle_hit h;
           h.seq1 = q1;
@@ -426,7 +458,7 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
                         const int32_t* pos1, const int8_t* codes2, const int64_t* seq_off2, int32_t n2,
                         const int64_t* key_off2, const int32_t* pos2, const oracle_params* prm, int32_t key_lo,
                         int32_t key_hi, const int32_t* key_list, int32_t n_threads, oracle_hit** out,
-                        int64_t* pairs) {
+                        int64_t* pairs, int64_t* filtered) {
   bank_view b1 = {codes1, seq_off1, n1, key_off1, pos1};
   bank_view b2 = {codes2, seq_off2, n2, key_off2, pos2};
   if (n_threads < 1) n_threads = 1;
@@ -450,10 +482,11 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
     for (int32_t t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, ungapped_worker, &jobs[t]);
     for (int32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
   }
-  int64_t total = 0, npairs = 0;
+  int64_t total = 0, npairs = 0, nfilt = 0;
   for (int32_t t = 0; t < n_threads; t++) {
     total += jobs[t].n;
     npairs += jobs[t].pairs;
+    nfilt += jobs[t].filtered;
   }
   oracle_hit* all = (oracle_hit*)malloc(sizeof(oracle_hit) * (size_t)(total > 0 ? total : 1));
   int64_t at = 0;
@@ -468,6 +501,7 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
   pthread_mutex_destroy(&lock);
   *out = all;
   if (pairs) *pairs = npairs;
+  if (filtered) *filtered = nfilt;
   return total;
 }
 
