@@ -129,16 +129,17 @@ def oracle_sample_keys(o1, o2, target_pairs: float, seed: int = 7):
     return sorted(keys), pairs
 
 
-def oracle_step(oracle, o1, o2, keys, threads):
+def oracle_step(oracle, o1, o2, keys, threads, prm):
     """Stages 1-2 over the sampled keys, then stage 3.1 of their hits."""
-    h = oracle.ungapped(o1, o2, keys=keys, threads=threads)
-    oracle.small_gapped(o1, o2, h)
+    h = oracle.ungapped(o1, o2, prm, keys=keys, threads=threads)
+    oracle.small_gapped(o1, o2, h, prm)
     return len(h)
 
 
-def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads: int | None = None):
+def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads: int | None = None, s0: int = 0):
     import oracle
 
+    prm = oracle.Params(s0=s0)
     threads = threads or os.cpu_count() or 1
     t0 = time.time()
     o1 = oracle.make_bank(b1.codes, b1.seq_off)
@@ -147,15 +148,15 @@ def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads
     # calibrate the sample: a small probe, then scale to the time budget
     probe_keys, probe_pairs = oracle_sample_keys(o1, o2, 2e7, seed=3)
     t0 = time.time()
-    oracle_step(oracle, o1, o2, probe_keys, threads)
+    oracle_step(oracle, o1, o2, probe_keys, threads, prm)
     rate = probe_pairs / max(time.time() - t0, 1e-3)
     keys, pairs = oracle_sample_keys(o1, o2, rate * seconds_per_step)
     for _ in range(warmup):
-        oracle_step(oracle, o1, o2, keys, threads)
+        oracle_step(oracle, o1, o2, keys, threads, prm)
     times = []
     for _ in range(steps):
         t0 = time.time()
-        oracle_step(oracle, o1, o2, keys, threads)
+        oracle_step(oracle, o1, o2, keys, threads, prm)
         times.append(time.time() - t0)
     per = sum(times) / len(times)
     return {
@@ -243,6 +244,7 @@ def run_gpu(args, rank, world, local_rank):
     B.lib()
     B.plast_set_schedule(1 if args.schedule == "per_key" else 0)
     tiles = setup_tiles(args, B)
+    prm = B.plast_default_params(s0=args.s0)
 
     t0 = time.time()
     b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale, n2=2)
@@ -262,7 +264,7 @@ def run_gpu(args, rank, world, local_rank):
     g1 = B.plast_index_bank(d1c, d1o)
     g2 = B.plast_index_bank(d2c, d2o)
     pairs = B.plast_pair_count(g1, g2)
-    recs, n_ung = B.plast_search(g1, g2)
+    recs, n_ung = B.plast_search(g1, g2, prm)
     cap = int(recs.shape[0] * 1.05) + 1024
     out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device=dev)
     n_recs = recs.shape[0]
@@ -278,7 +280,7 @@ def run_gpu(args, rank, world, local_rank):
     def step(c1, o1_, c2, o2_):
         a = B.plast_index_bank(c1, o1_)
         b = B.plast_index_bank(c2, o2_)
-        r, _ = B.plast_search(a, b, out=out, cap=cap)
+        r, _ = B.plast_search(a, b, prm, out=out, cap=cap)
         stage_ms.append(B.plast_stage_times())
         a.free()
         b.free()
@@ -368,11 +370,12 @@ def run_gpu(args, rank, world, local_rank):
             "workload": f"PLAST-P {'full scale' if args.scale == 1.0 and not args.bank2_proteins else 'reduced'}: "
                         f"{b1.n_seqs} x {b2.n_seqs} synthetic proteins "
                         f"({len(b1.codes)} / {len(b2.codes)} residues), 5% planted homologs, seed 1",
-            "step": "index both banks + ungapped all pairs + sort + small gapped",
+            "step": "index both banks + ungapped all pairs + sort + small gapped"
+                    + (f" (Section 4.2 filter on, S0 = {args.s0}: lossy, fewer hits)" if args.s0 else ""),
             "pairs_per_step": pairs,
             "stage2_hits_per_step": n_ung,
             "records_per_step": n_recs,
-            "params": B.plast_default_params().as_dict(),
+            "params": prm.as_dict(),
             "schedule": args.schedule,
             "stage2_tiles": tiles,
             "l2": f"inputs larger than L2 (129 MB): {nb_gb:.2f} GB of neighbourhood arrays rebuilt and "
@@ -511,6 +514,50 @@ def run_tplastn(args):
     }
 
 
+def run_plastx(args):
+    """PLAST-X: 1,000 nucleotide sequences of about 1 kbp vs a 50 Mbp
+    nucleotide bank, both translated in six frames on the device, then
+    stage 0 of both translated banks and the search, per step."""
+    import torch
+
+    from paper_0804_3643_gb300 import binding as B
+
+    tiles = setup_tiles(args, B)
+    q, subj = synth.plastx_workload(seed=1, scale=args.scale)
+    hq, oq = torch.from_numpy(q.codes).cuda(), torch.from_numpy(q.seq_off).cuda()
+    hs, os_ = torch.from_numpy(subj.codes).cuda(), torch.from_numpy(subj.seq_off).cuda()
+    a1, s1, _ = B.plast_translate6(hq, oq)
+    a2, s2, _ = B.plast_translate6(hs, os_)
+    g1 = B.plast_index_bank(a1, s1)
+    g2 = B.plast_index_bank(a2, s2)
+    pairs = B.plast_pair_count(g1, g2)
+    recs, n_ung = B.plast_search(g1, g2)
+    cap = int(recs.shape[0] * 1.05) + 1024
+    out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
+    n_rec = int(recs.shape[0])
+    n_aa = (len(a1), len(a2))
+    del g1, g2, a1, a2, s1, s2
+
+    def step():
+        x_aa, x_so, _ = B.plast_translate6(hq, oq)
+        y_aa, y_so, _ = B.plast_translate6(hs, os_)
+        x = B.plast_index_bank(x_aa, x_so)
+        y = B.plast_index_bank(y_aa, y_so)
+        B.plast_search(x, y, out=out, cap=cap)
+        x.free()
+        y.free()
+
+    ms = _time_steps(step, args.steps, args.warmup)
+    return {
+        "metric": "ungapped pairs/s, PLAST-X chain (translate6 of both banks + index + search)", "unit": "pairs/s",
+        "value": pairs / (ms / 1e3), "ms_per_step": ms,
+        "workload": f"PLAST-X: {q.n_seqs} sequences ({len(q.codes) / 1e6:.2f} Mbp) vs {len(subj.codes) / 1e6:.1f} Mbp "
+                    f"in {subj.n_seqs} sequences ({n_aa[0]} / {n_aa[1]} translated residues), "
+                    f"{len(q.planted['regions'])} / {len(subj.planted['regions'])} planted regions, seed 1",
+        "pairs": pairs, "stage2_hits": n_ung, "records": n_rec, "stage2_tiles": tiles,
+    }
+
+
 def run_query(args):
     """One query bank of --query-proteins proteins against a resident bank of
     --bank2-proteins (default 1,000,000): the search a serving request runs,
@@ -620,8 +667,11 @@ def main():
     ap.add_argument("--wide-int16-cells", type=int, default=None, choices=[0, 12, 14, 16],
                     help="force the wide stage-2 kernel variant (default: the autotuner's pick)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batching_stress", "tplastn", "serving", "query"],
+                    choices=[WORKLOAD, "batching_stress", "tplastn", "plastx", "serving", "query"],
                     help="the headline line is plastp_full; the others print their own lines")
+    ap.add_argument("--s0", type=int, default=0,
+                    help="Section 4.2 filter threshold for the headline workload (0: off, the bit-exact default; "
+                         "53: the calibrated value)")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per arrival rate")
     ap.add_argument("--query-proteins", type=int, default=250, help="query: proteins of the query bank")
     ap.add_argument("--bank2-proteins", type=int, default=None,
@@ -654,8 +704,8 @@ def main():
 
     if args.workload != WORKLOAD:
         if rank == 0:
-            fn = {"batching_stress": run_stress, "tplastn": run_tplastn, "serving": run_serving,
-                  "query": run_query}[args.workload]
+            fn = {"batching_stress": run_stress, "tplastn": run_tplastn, "plastx": run_plastx,
+                  "serving": run_serving, "query": run_query}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 
@@ -668,7 +718,7 @@ def main():
     result, banks = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0, args.cpu_threads)
+            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0, args.cpu_threads, s0=args.s0)
             result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(result), flush=True)
     if world > 1:

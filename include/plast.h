@@ -60,11 +60,21 @@ typedef struct plast_bank plast_bank;
  *   gap_open, gap_extend  a gap of length k costs gap_open + k*gap_extend
  *              (both >= 0)
  *   s2         small gapped threshold: kept if the score >= s2
- * Defaults (plast_default_params): 4, 22, 22, 38, 64, 8, 11, 1, 47.
+ *   s0         filter threshold of Section 4.2, 0 = no filter (0..30000):
+ *              a pair is kept by stage 2 only if, besides its ungapped
+ *              score reaching s1, the sum of the positive substitution
+ *              scores over its window (clipped like the ungapped score)
+ *              reaches s0.  Lossy: it removes hits the unfiltered search
+ *              keeps.  PLAST_FILTER_S0 is the value that lets about 2.5 %
+ *              of random pairs through, as the paper reports.
+ * Defaults (plast_default_params): 4, 22, 22, 38, 64, 8, 11, 1, 47, 0.
  */
 typedef struct {
   int32_t w, nl, nr, s1, lg, band, gap_open, gap_extend, s2;
+  int32_t s0;
 } plast_params;
+
+#define PLAST_FILTER_S0 53
 
 /*
  * Ungapped hit (stage 2).  score = R + max(0, L) as defined by Section
@@ -156,8 +166,9 @@ int plast_bank_export_index(const plast_bank* bank, int64_t* key_off, int32_t* p
 /*
  * Stages 1-2 (Sections 3.3.2-3.3.3, Annex 4): for every key present in both
  * banks, every pair of occurrences gets an ungapped extension; pairs scoring
- * >= params->s1 are written to out[0 .. *n_out) sorted by
- * (seq1, pos1, seq2, pos2).  out: [cap] plast_hit (device).
+ * >= params->s1 (and, when params->s0 > 0, passing Section 4.2's filter)
+ * are written to out[0 .. *n_out) sorted by (seq1, pos1, seq2, pos2).
+ * out: [cap] plast_hit (device).
  * Errors: PLAST_E_INVALID, PLAST_E_CAPACITY (*n_out = needed), PLAST_E_OOM,
  * PLAST_E_CUDA, PLAST_E_TIMEOUT.
  */
@@ -244,7 +255,8 @@ int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank* b2, const
  * on a non-default `stream` and keeps the instantiated graph in the plan,
  * and plast_plan_launch replays it.  plast_plan_result synchronises `stream`
  * and returns the record count of the last run (records in canonical order,
- * as plast_search) and its stage-2 hit count; PLAST_E_CAPACITY if either
+ * as plast_search) and its stage-2 hit count (those through the S0 filter
+ * when params->s0 > 0; max_hits bounds the count before it); PLAST_E_CAPACITY if either
  * limit was exceeded (*n_records then holds the hit or record count that did
  * not fit, and the records are an incomplete subset).  PLAST_E_INVALID at
  * creation unless max_records >= 1 and 1 <= max_hits < 2^32.  Runs of one

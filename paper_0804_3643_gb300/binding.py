@@ -35,9 +35,12 @@ HIT_BYTES = HIT_DTYPE.itemsize        # 20
 GAPPED_BYTES = GAPPED_DTYPE.itemsize  # 28
 
 
+PLAST_FILTER_S0 = 53  # the header's calibrated Section 4.2 filter threshold
+
+
 class plast_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2")]
+                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2", "s0")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

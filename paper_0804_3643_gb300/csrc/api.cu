@@ -17,6 +17,7 @@
 
 #include "bank.cuh"
 #include "common.cuh"
+#include "filter.cuh"
 #include "index.cuh"
 #include "ungapped.cuh"
 
@@ -91,7 +92,7 @@ bool params_ok(const plast_params* p) {
   if (!p) return true;
   return p->w == 4 && p->nl == LEFT && p->nr == RIGHT - 4 && p->lg == LG && p->band == BAND && p->gap_open >= 0 &&
          p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 1000 && p->s1 >= -30000 &&
-         p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000;
+         p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000 && p->s0 >= 0 && p->s0 <= 30000;
 }
 
 plast_params resolve(const plast_params* p) {
@@ -458,6 +459,21 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
       cap = (int64_t)n + 1024;
       continue;
     }
+    if (prm.s0 > 0 && n > 0) {
+      // Section 4.2's filter on the survivors
+      uint64_t* kf;
+      uint32_t* vf;
+      CK(sc.get(&kf, (int64_t)n));
+      CK(sc.get(&vf, (int64_t)n));
+      CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
+      CK(launch_filter_gate(k0, v0, (int64_t)n, nullptr, sv->sh, b1->pad, b2->pad, prm.s0, kf, vf, d_count, st));
+      CK(cudaMemcpyAsync(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      sc.release(k0);
+      sc.release(v0);
+      k0 = kf;
+      v0 = vf;
+    }
     sv->n = (int64_t)n;
     if (n == 0) return PLAST_OK;
     if (!sort) {
@@ -502,6 +518,7 @@ void plast_default_params(plast_params* p) {
   p->gap_open = 11;
   p->gap_extend = 1;
   p->s2 = 47;
+  p->s0 = 0;
 }
 
 const char* plast_strerror(int code) {
@@ -983,6 +1000,9 @@ struct plast_plan {
   int64_t* m_dev = nullptr;   // records, clamped to max_records
   uint64_t* k0 = nullptr;     // survivors (kernel order)
   uint32_t* v0 = nullptr;
+  uint64_t* kf = nullptr;     // survivors through the S0 filter (when s0 > 0)
+  uint32_t* vf = nullptr;
+  unsigned long long* count_f = nullptr;
   uint64_t *rk0 = nullptr, *rk1 = nullptr;  // record keys and hit indexes, sorted
   uint32_t *ri0 = nullptr, *ri1 = nullptr;
   void* rtmp = nullptr;
@@ -1007,7 +1027,8 @@ void plast_plan_free(plast_plan* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   for (void* q : {(void*)p->tiles, (void*)p->counter, (void*)p->count, (void*)p->n_dev, (void*)p->m_dev,
                   (void*)p->k0, (void*)p->v0, (void*)p->rk0, (void*)p->rk1, (void*)p->ri0, (void*)p->ri1, p->rtmp,
-                  (void*)p->score, (void*)p->ends, (void*)p->pass, (void*)p->at, (void*)p->total, p->stmp})
+                  (void*)p->score, (void*)p->ends, (void*)p->pass, (void*)p->at, (void*)p->total, p->stmp,
+                  (void*)p->kf, (void*)p->vf, (void*)p->count_f})
     if (q) cudaFree(q);
   delete p;
 }
@@ -1058,6 +1079,10 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
       (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->at, 8 * (size_t)max_hits)) ||
       (e = alloc((void**)&p->total, sizeof(int64_t))) || (e = alloc(&p->stmp, p->stb)))
     return fail(e);
+  if (p->prm.s0 > 0 &&
+      ((e = alloc((void**)&p->kf, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->vf, 4 * (size_t)max_hits)) ||
+       (e = alloc((void**)&p->count_f, sizeof(unsigned long long)))))
+    return fail(e);
   if (p->n_tiles > 0 &&
       (e = cudaMemcpyAsync(p->tiles, tl.tiles.data(), sizeof(int4) * p->n_tiles, cudaMemcpyHostToDevice, st)))
     return fail(e);
@@ -1100,11 +1125,18 @@ int plast_plan_run(plast_plan* p, void* stream) {
     CK(launch_tiles(p->tl, a, p->counter, true, st));
   }
   CK(launch_clamp_count(p->count, p->max_hits, p->n_dev, st));
+  const bool filter = p->prm.s0 > 0;
+  if (filter) {
+    CK(cudaMemsetAsync(p->count_f, 0, sizeof(unsigned long long), st));
+    CK(launch_filter_gate(p->k0, p->v0, p->max_hits, p->n_dev, p->sh, p->b1->pad, p->b2->pad, p->prm.s0, p->kf,
+                          p->vf, p->count_f, st));
+    CK(launch_clamp_count(p->count_f, p->max_hits, p->n_dev, st));
+  }
   GapArgs g;
   g.pad1 = p->b1->pad;
   g.pad2 = p->b2->pad;
-  g.key = p->k0;
-  g.val = p->v0;
+  g.key = filter ? p->kf : p->k0;
+  g.val = filter ? p->vf : p->v0;
   g.n = p->max_hits;
   g.sh = p->sh;
   g.gap_open = p->prm.gap_open;
@@ -1160,12 +1192,13 @@ int plast_plan_launch(plast_plan* p, void* stream) {
 int plast_plan_result(const plast_plan* p, int64_t* n_records, int64_t* n_hits, void* stream) {
   if (!p || !n_records) return PLAST_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned long long hits = 0;
+  unsigned long long hits = 0, kept = 0;
   int64_t recs = 0;
   CK(cudaMemcpyAsync(&hits, p->count, sizeof(hits), cudaMemcpyDeviceToHost, st));
+  if (p->count_f) CK(cudaMemcpyAsync(&kept, p->count_f, sizeof(kept), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&recs, p->total, sizeof(recs), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (n_hits) *n_hits = (int64_t)hits;
+  if (n_hits) *n_hits = (int64_t)(p->count_f && hits <= (unsigned long long)p->max_hits ? kept : hits);
   if ((int64_t)hits > p->max_hits) {
     *n_records = (int64_t)hits;
     return PLAST_E_CAPACITY;

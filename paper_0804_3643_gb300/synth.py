@@ -251,11 +251,12 @@ def dna_bank(rng: np.random.Generator, total_nt: int, proteins: SynthBank | None
             if all(en <= a or st >= b for a, b in used[c]):
                 used[c].append((st, en))
                 nt[off[c] + st:off[c] + en] = region
-                placed.append((j, c, st, strand))
+                placed.append((j, c, st, strand, len(region)))
                 break
     bank = SynthBank(nt.view(np.int8), off)
     bank.codes = nt
-    bank.planted = {"regions": np.array(placed, dtype=np.int64).reshape(-1, 4)}
+    # (source protein, contig, first nt, strand (1: reverse complement), nt)
+    bank.planted = {"regions": np.array(placed, dtype=np.int64).reshape(-1, 5)}
     return bank
 
 
@@ -292,6 +293,28 @@ def tplastn_workload(seed: int = 1, scale: float = 1.0):
     dna = dna_bank(rng, total, proteins=b1, n_planted=max(1, int(round(2000 * scale))),
                    max_contig=max(1000, min(100000, total // 4)))
     return b1, dna
+
+
+def plastx_workload(seed: int = 1, scale: float = 1.0):
+    """(query DNA bank, subject DNA bank) of the translated-vs-translated
+    workload: 1,000 sequences of 600-1,450 nt (mean about 1,024, the size of
+    the smallest query bank of the PLAST-X runs) against 50 Mbp in sequences
+    of 1-10 kbp (mean about 5.5 kbp, a third of their subject bank); both
+    carry back-translated homologs of 2,000 hidden source proteins of median
+    length 200 (200 planted in the queries, 2,000 in the subject)."""
+    rng = np.random.default_rng(seed)
+    n_src = max(2, int(round(2000 * scale)))
+    lens = protein_lengths(rng, n_src, median=200.0)
+    off = np.zeros(n_src + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    src = SynthBank(background_residues(rng, int(off[-1])), off)
+    n_q = max(2, int(round(1000 * scale)))
+    query = dna_bank(rng, n_q * 1024, proteins=src, n_planted=max(1, int(round(200 * scale))),
+                     min_contig=600, max_contig=1450)
+    total = max(12000, int(round(50_000_000 * scale)))
+    subject = dna_bank(rng, total, proteins=src, n_planted=max(1, int(round(2000 * scale))),
+                       min_contig=1000, max_contig=10000)
+    return query, subject
 
 
 def serving_requests(seed: int, n: int, rate_per_s: float, max_proteins: int = 500):

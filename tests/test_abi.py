@@ -38,7 +38,7 @@ def test_host_only_entry_points(lib):
     from paper_0804_3643_gb300 import binding as B
 
     p = B.plast_default_params()
-    assert p.as_dict() == dict(w=4, nl=22, nr=22, s1=38, lg=64, band=8, gap_open=11, gap_extend=1, s2=47)
+    assert p.as_dict() == dict(w=4, nl=22, nr=22, s1=38, lg=64, band=8, gap_open=11, gap_extend=1, s2=47, s0=0)
     assert B.plast_strerror(B.PLAST_E_CAPACITY) == "output capacity too small"
     assert B.plast_strerror(0) == "ok"
     B.plast_set_schedule(1)
@@ -66,4 +66,4 @@ def test_record_layouts_match_header():
     from paper_0804_3643_gb300 import binding as B
 
     assert B.HIT_DTYPE.itemsize == 20 and B.GAPPED_DTYPE.itemsize == 28
-    assert ctypes.sizeof(B.plast_params) == 36
+    assert ctypes.sizeof(B.plast_params) == 40

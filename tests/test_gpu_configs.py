@@ -3,6 +3,8 @@
 * batching stress: 50,000 x 50,000 proteins, 20 % with low-complexity runs
   (heavy-tailed key lists, 5.4e10 pairs);
 * TPLAST-N: 5,000 proteins vs 50 Mbp translated on the device (1e8 aa);
+* PLAST-X: 1,000 sequences of about 1 kbp vs 50 Mbp, both translated on the
+  device;
 * serving: a 1,000,000-protein resident bank against a 250-protein query.
 
 Each comparison runs the GPU on a random sample of keys (plast_*_keys, the
@@ -95,6 +97,23 @@ def test_tplastn_full_size(B):
     o1 = oracle.make_bank(b1.codes, b1.seq_off)
     o2 = oracle.make_bank(w_aa, w_so)
     keys, _ = sample_keys(o1, o2, np.random.default_rng(32), 40)
+    nh, ng = check_keys(B, g1, g2, o1, o2, keys)
+    assert nh > 1000
+
+
+def test_plastx_full_size(B):
+    q, subj = synth.plastx_workload(seed=1)
+    banks = []
+    for dna in (q, subj):
+        aa, so, meta = B.plast_translate6(torch.from_numpy(dna.codes).cuda(), torch.from_numpy(dna.seq_off).cuda())
+        w_aa, w_so, w_meta = oracle.translate6(dna.codes, dna.seq_off)
+        assert np.array_equal(aa.cpu().numpy(), w_aa)
+        assert np.array_equal(so.cpu().numpy(), w_so)
+        assert np.array_equal(meta.cpu().numpy(), w_meta)
+        banks.append((B.plast_index_bank(aa, so), oracle.make_bank(w_aa, w_so)))
+    (g1, o1), (g2, o2) = banks
+    assert B.plast_pair_count(g1, g2) > 10 ** 10
+    keys, _ = sample_keys(o1, o2, np.random.default_rng(33), 40)
     nh, ng = check_keys(B, g1, g2, o1, o2, keys)
     assert nh > 1000
 

@@ -252,6 +252,46 @@ def test_bank_built_on_another_stream(B):
         g3.free()
 
 
+def test_s0_filter(B, plain):
+    # Section 4.2's lossy filter: hits and records equal the oracle's
+    # filter-then-extend, at the calibrated S0 and at a harsher one
+    g1, o1, g2, o2 = plain
+    full = oracle.ungapped(o1, o2, threads=8)
+    for s0 in (B.PLAST_FILTER_S0, 70):
+        prm = B.plast_default_params(s0=s0)
+        want_h = oracle.ungapped(o1, o2, oracle.Params(s0=s0), threads=8)
+        assert 100 < len(want_h) < len(full)
+        assert same(B.hits_numpy(B.plast_ungapped(g1, g2, prm)), want_h)
+        recs, n_ung = B.plast_search(g1, g2, prm)
+        assert n_ung == len(want_h)
+        assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h))
+        keys = np.arange(0, B.NKEYS, 7, dtype=np.int32)
+        want_k = oracle.ungapped(o1, o2, oracle.Params(s0=s0), keys=keys, threads=8)
+        assert same(B.hits_numpy(B.plast_ungapped_keys(g1, g2, keys, prm)), want_k)
+    # a filter at or below S1 removes nothing (U <= F)
+    assert same(B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s0=38))), full)
+    with pytest.raises(B.PlastError):
+        B.plast_ungapped(g1, g2, B.plast_default_params(s0=-1))
+
+
+def test_plastx_both_translated(B):
+    # PLAST-X proper: two nucleotide banks, each translated in six frames
+    q, subj = synth.plastx_workload(seed=16, scale=0.02)
+    got, want = [], []
+    for dna in (q, subj):
+        aa, so, _ = B.plast_translate6(torch.from_numpy(dna.codes).cuda(), torch.from_numpy(dna.seq_off).cuda())
+        w_aa, w_so, _ = oracle.translate6(dna.codes, dna.seq_off)
+        assert np.array_equal(aa.cpu().numpy(), w_aa) and np.array_equal(so.cpu().numpy(), w_so)
+        got.append(B.plast_index_bank(aa, so))
+        want.append(oracle.make_bank(w_aa, w_so))
+    want_h = oracle.ungapped(want[0], want[1], threads=8)
+    assert len(want_h) > 1000
+    assert same(B.hits_numpy(B.plast_ungapped(got[0], got[1])), want_h)
+    recs, n_ung = B.plast_search(got[0], got[1])
+    assert n_ung == len(want_h)
+    assert same(B.gapped_numpy(recs), oracle.small_gapped(want[0], want[1], want_h))
+
+
 def test_plastx_translated_queries(B):
     # PLAST-X: a nucleotide query bank translated in six frames against a
     # protein bank (the queries as bank 1)

@@ -80,3 +80,29 @@ def test_plan_capacity_errors(B, banks):
     assert key == sorted(key)
     with pytest.raises(B.PlastError):
         B.Plan(g1, g2, max_hits=0, max_records=11)
+
+
+def test_plan_with_filter(B, banks):
+    # Section 4.2's filter inside a planned search and its graph replay
+    g1, g2, n_hits, _ = banks
+    b1, b2 = synth.workload("plastp_plain", seed=3, scale=0.5)
+    o1 = oracle.make_bank(b1.codes, b1.seq_off)
+    o2 = oracle.make_bank(b2.codes, b2.seq_off)
+    prm_o = oracle.Params(s0=B.PLAST_FILTER_S0)
+    hits = oracle.ungapped(o1, o2, prm_o, threads=16)
+    want = oracle.small_gapped(o1, o2, hits)
+    assert 0 < len(hits) < n_hits
+    prm = B.plast_default_params(s0=B.PLAST_FILTER_S0)
+    plan = B.Plan(g1, g2, max_hits=n_hits + 100, max_records=len(want) + 100, params=prm)
+    plan.run()
+    recs, nu = plan.result()
+    assert nu == len(hits)
+    assert np.array_equal(B.gapped_numpy(recs).view(np.uint8), want.view(np.uint8))
+    s = torch.cuda.Stream()
+    plan.capture(s)
+    for _ in range(2):
+        plan.launch(s)
+        s.synchronize()
+        recs, nu = plan.result(s)
+        assert nu == len(hits)
+        assert np.array_equal(B.gapped_numpy(recs).view(np.uint8), want.view(np.uint8))
