@@ -58,7 +58,9 @@ typedef struct plast_bank plast_bank;
  *   lg         residues per side of the small gapped extension; must be 64
  *   band       half width of the diagonal band; must be 8
  *   gap_open, gap_extend  a gap of length k costs gap_open + k*gap_extend
- *              (both >= 0)
+ *              (gap_open 0..1000, gap_extend 0..400: the small gapped
+ *              extension keeps row i's values offset by i*gap_extend in
+ *              int16)
  *   s2         small gapped threshold: kept if the score >= s2
  *   s0         filter threshold of Section 4.2, 0 = no filter (0..30000):
  *              a pair is kept by stage 2 only if, besides its ungapped

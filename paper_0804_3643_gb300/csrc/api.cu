@@ -91,7 +91,7 @@ struct Scratch {
 bool params_ok(const plast_params* p) {
   if (!p) return true;
   return p->w == 4 && p->nl == LEFT && p->nr == RIGHT - 4 && p->lg == LG && p->band == BAND && p->gap_open >= 0 &&
-         p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 1000 && p->s1 >= -30000 &&
+         p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 400 && p->s1 >= -30000 &&
          p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000 && p->s0 >= 0 && p->s0 <= 30000;
 }
 

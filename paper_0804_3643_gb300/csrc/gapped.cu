@@ -9,18 +9,22 @@
 // sides with shuffles.  CTAs stride over the hits.
 //
 // Per cell (two hits): two byte loads of B_j from the thread's shared
-// segments, two IMADs and two loads of s(A_i, B_j) from a lane-replicated
+// segments, two IMADs and two loads of s(A_i, B_j) - go from a lane-replicated
 // table (entry (a, b) of lane l at word (b * 23 + a) * 32 + l: the lanes of a
-// warp never share a bank), one IMAD packing the two scores, then
-//   F  = max(H_up - go - ge, F_up - ge)           __viaddmax_s16x2
-//   DF = max(H_diag + s, F)                       __viaddmax_s16x2
-//   H  = max(DF, E)                               __vmaxs2
-//   E' = max(E - ge, DF - go - ge)                __vsub2, __viaddmax_s16x2
-// (F is kept as F - ge, so F_up - ge needs no instruction.)
-// E' is E of the next cell: since go >= 0, H - go - ge is never above E - ge
-// when H = E, so only DF feeds the next E and the chain along the row is a
-// single instruction per cell.  Values are exact in int16 (|H| <= 64 * 11 on
-// the grid; cells off the grid stay above -16000 - 64 * 12).
+// warp never share a bank), one IMAD packing the two entries, then four
+// three-operand maxima.  Row i's values are kept offset by i * ge, and F and
+// DF also shifted down by goe = go + ge:
+//   H'  = H + i ge,  E' = E + i ge,  Gg = F + i ge - goe,  DFg = DF + i ge - goe
+// so that, with up = (i - 1, j) and diag = (i - 1, j - 1),
+//   Gg  = max(H'_up - go - goe, Gg_up)            __viaddmax_s16x2
+//   DFg = max(H'_diag + (s - go), Gg)             __viaddmax_s16x2
+//   H'  = max(DFg + goe, E')                      __viaddmax_s16x2
+//   E'  = max(E' - ge, DFg)   (E' of the next cell)  __viaddmax_s16x2
+// which restate F = max(H_up - go - ge, F_up - ge), DF = max(H_diag + s, F),
+// H = max(DF, E), E_next = max(E - ge, DF - go - ge) with no other operation.
+// Only DF feeds the next E: since go >= 0, H - go - ge is never above E - ge
+// when H = E.  Values are exact in int16 (|H| <= 64 * 11 on the grid; cells
+// off the grid stay below -14000 and above -16000 - 64 * 24).
 //
 // The A residues of a side reach the thread four rows at a time: aligned
 // 32-bit loads of pad1 (byte-reversed for the left side) funnel-shifted into
@@ -58,48 +62,58 @@ constexpr int GAP_SMEM = TAB_WORDS * 4 + GAP_THREADS * SEG_T;  // 110848 bytes
 __device__ __forceinline__ uint32_t x2(int v) { return ((uint32_t)(uint16_t)v << 16) | (uint16_t)v; }
 
 struct Band {
-  uint32_t H[BW], Fm[BW], bestH[BW];  // H and F - ge of the previous row, best row
-  uint32_t best, bi;                 // per half
+  uint32_t H[BW], Gg[BW], bestH[BW];  // H' and Gg of the previous row, H' of the best row
+  uint32_t best, bi;                 // per half (best without the row offset)
+};
+
+struct GapConst {
+  uint32_t nge2, goe2, ngg2;  // -ge, go + ge, -(go + goe) in both halves
+  int ge;
 };
 
 // Cell JB of row i for both hits.
 template <int JB>
 __device__ __forceinline__ uint32_t band_cell(Band& B, const unsigned char* row0, const unsigned char* row1,
-                                              uint32_t sb0, uint32_t sb1, uint32_t& E, uint32_t nge2,
-                                              uint32_t goe2) {
-  const uint32_t ngoe2 = __vsub2(0u, goe2);
+                                              uint32_t sb0, uint32_t sb1, uint32_t& E, const GapConst& k) {
   const uint32_t b0 = lds_u8<JB>(sb0), b1 = lds_u8<JB>(sb1);  // B_{i - BAND + JB} of each hit
   const uint32_t s0 = *reinterpret_cast<const uint32_t*>(row0 + b0 * (TAB_A * 128));
   const uint32_t s1 = *reinterpret_cast<const uint32_t*>(row1 + b1 * (TAB_A * 128));
-  const uint32_t sc = s1 * 65536u + s0;  // entries are zero-extended int16
+  const uint32_t sc = s1 * 65536u + s0;  // entries are zero-extended int16 s - go
   const uint32_t up_h = JB + 1 < BW ? B.H[JB + 1 < BW ? JB + 1 : 0] : x2(NEG16);
-  const uint32_t up_fm = JB + 1 < BW ? B.Fm[JB + 1 < BW ? JB + 1 : 0] : x2(NEG16);
-  const uint32_t f = __viaddmax_s16x2(up_h, ngoe2, up_fm);  // max(H_up - go - ge, F_up - ge)
-  const uint32_t df = __viaddmax_s16x2(B.H[JB], sc, f);     // max(H_diag + s, F)
-  const uint32_t h = __vmaxs2(df, E);
-  E = __viaddmax_s16x2(E, nge2, __vsub2(df, goe2));
+  const uint32_t up_g = JB + 1 < BW ? B.Gg[JB + 1 < BW ? JB + 1 : 0] : x2(NEG16);
+  const uint32_t gg = __viaddmax_s16x2(up_h, k.ngg2, up_g);  // Gg
+  const uint32_t dfg = __viaddmax_s16x2(B.H[JB], sc, gg);    // DFg
+  const uint32_t h = __viaddmax_s16x2(dfg, k.goe2, E);        // H'
+  E = __viaddmax_s16x2(E, k.nge2, dfg);                        // E' of the next cell
   B.H[JB] = h;
-  B.Fm[JB] = __vadd2(f, nge2);
+  B.Gg[JB] = gg;
   return h;
 }
 
-template <int JB, int JLIM>
+template <int JB>
 __device__ __forceinline__ void band_cells(Band& B, const unsigned char* row0, const unsigned char* row1,
-                                           uint32_t sb0, uint32_t sb1, uint32_t& E, uint32_t nge2,
-                                           uint32_t goe2, uint32_t& rmax) {
+                                           uint32_t sb0, uint32_t sb1, uint32_t& E, const GapConst& k) {
   if constexpr (JB < BW) {
-    const uint32_t h = band_cell<JB>(B, row0, row1, sb0, sb1, E, nge2, goe2);
-    if constexpr (JB <= JLIM) rmax = JB == 0 ? h : __vmaxs2(rmax, h);
-    band_cells<JB + 1, JLIM>(B, row0, row1, sb0, sb1, E, nge2, goe2, rmax);
+    band_cell<JB>(B, row0, row1, sb0, sb1, E, k);
+    band_cells<JB + 1>(B, row0, row1, sb0, sb1, E, k);
   }
+}
+
+// Maximum of H'[0 .. JLIM], three at a time.
+template <int JB, int JLIM>
+__device__ __forceinline__ uint32_t row_max(const Band& B, uint32_t m) {
+  if constexpr (JB + 1 <= JLIM) return row_max<JB + 2, JLIM>(B, __vimax3_s16x2(m, B.H[JB], B.H[JB + 1]));
+  else if constexpr (JB <= JLIM) return __vmaxs2(m, B.H[JB]);
+  else return m;
 }
 
 // Row i; columns jb > JLIM have j > LG and stay out of the maximum.
 template <int JLIM>
 __device__ __forceinline__ void gapped_row(Band& B, int i, const unsigned char* row0, const unsigned char* row1,
-                                           uint32_t sb0, uint32_t sb1, uint32_t nge2, uint32_t goe2) {
-  uint32_t E = x2(NEG16), rmax = 0;
-  band_cells<0, JLIM>(B, row0, row1, sb0 + i, sb1 + i, E, nge2, goe2, rmax);
+                                           uint32_t sb0, uint32_t sb1, const GapConst& k) {
+  uint32_t E = x2(NEG16);
+  band_cells<0>(B, row0, row1, sb0 + i, sb1 + i, E, k);
+  const uint32_t rmax = __vsub2(row_max<1, JLIM>(B, B.H[0]), x2(i * k.ge));  // without the row offset
   const uint32_t up = __vcmpgts2(rmax, B.best);  // 0xffff in the halves that improve
   B.best = __vmaxs2(B.best, rmax);
   B.bi = (x2(i) & up) | (B.bi & ~up);
@@ -108,10 +122,10 @@ __device__ __forceinline__ void gapped_row(Band& B, int i, const unsigned char* 
 }
 
 // First column of the best row holding the best value, for half q.
-__device__ __forceinline__ int end_column(const Band& B, int q) {
+__device__ __forceinline__ int end_column(const Band& B, int q, int ge) {
   const int sh = 16 * q;
-  const int best = (int16_t)(B.best >> sh);
   const int bi = (int16_t)(B.bi >> sh);
+  const int best = (int16_t)(B.best >> sh) + bi * ge;  // with the best row's offset
   const int jlim = min(BW - 1, LG + BAND - bi);
   int found = -1;
 #pragma unroll
@@ -171,14 +185,18 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   unsigned char* seg = gsm + TAB_WORDS * 4 + threadIdx.x * SEG_T;
   const uint32_t seg_s = (uint32_t)__cvta_generic_to_shared(seg);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int go = a.gap_open, ge = a.gap_extend, goe = go + ge;
   for (int e = warp; e < NCODE * TAB_A; e += GAP_THREADS / 32) {
     const int b = e / TAB_A, aa = e - b * TAB_A;
-    tab32[e * 32 + lane] = aa < NCODE ? (uint32_t)(uint16_t)(int16_t)c_score[aa * NCODE + b] : 0u;
+    tab32[e * 32 + lane] = aa < NCODE ? (uint32_t)(uint16_t)(int16_t)(c_score[aa * NCODE + b] - go) : 0u;
   }
   __syncthreads();
   const unsigned char* tlane = reinterpret_cast<const unsigned char*>(tab32) + lane * 4;
-  const int go = a.gap_open, ge = a.gap_extend, goe = go + ge;
-  const uint32_t nge2 = x2(-ge), goe2 = x2(goe);
+  GapConst kc;
+  kc.nge2 = x2(-ge);
+  kc.goe2 = x2(goe);
+  kc.ngg2 = x2(-(go + goe));
+  kc.ge = ge;
   const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
   const int64_t npairs = (n + 1) / 2;  // hits 2p and 2p+1 share a thread
   const int64_t total = 2 * npairs;      // (pair, side) threads
@@ -206,7 +224,7 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
         const int j = jb - BAND;
         const int v = j < 0 ? NEG16 : (j == 0 ? 0 : -(go + j * ge));
         B.H[jb] = x2(v);
-        B.Fm[jb] = x2(NEG16);
+        B.Gg[jb] = x2(NEG16);
         B.bestH[jb] = B.H[jb];
       }
       B.best = 0;
@@ -222,7 +240,7 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   {                                                                                                    \
     const unsigned char* r0 = tlane + __byte_perm(c0, 0u, 0x4440u + (R)) * 128u;                       \
     const unsigned char* r1 = tlane + __byte_perm(c1, 0u, 0x4440u + (R)) * 128u;                       \
-    gapped_row<JLIM>(B, (I), r0, r1, sb0, sb1, nge2, goe2);                                            \
+    gapped_row<JLIM>(B, (I), r0, r1, sb0, sb1, kc);                                                    \
   }
       for (int g = 0; g < (LG - BAND) / 4; g++) {  // rows 1 .. 56: the whole band on the grid
         const uint32_t c0 = aw0, c1 = aw1;
@@ -261,9 +279,9 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
     int bi0 = 0, bj0 = 0, bi1 = 0, bj1 = 0;
     if (active) {
       bi0 = (int16_t)(B.bi & 0xffff);
-      bj0 = end_column(B, 0);
+      bj0 = end_column(B, 0, ge);
       bi1 = (int16_t)(B.bi >> 16);
-      bj1 = end_column(B, 1);
+      bj1 = end_column(B, 1, ge);
     }
     const uint32_t ob = __shfl_xor_sync(0xffffffffu, B.best, 1);
     const int obi0 = __shfl_xor_sync(0xffffffffu, bi0, 1), obj0 = __shfl_xor_sync(0xffffffffu, bj0, 1);

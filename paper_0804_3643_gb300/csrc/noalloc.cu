@@ -85,7 +85,7 @@ extern "C" int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank
   plast_default_params(&prm);
   if (params) prm = *params;
   if (prm.w != 4 || prm.nl != LEFT || prm.nr != RIGHT - 4 || prm.lg != LG || prm.band != BAND ||
-      prm.gap_open < 0 || prm.gap_extend < 0 || prm.gap_open > 1000 || prm.gap_extend > 1000 ||
+      prm.gap_open < 0 || prm.gap_extend < 0 || prm.gap_open > 1000 || prm.gap_extend > 400 ||
       prm.s2 < -30000 || prm.s2 > 30000)
     return PLAST_E_INVALID;
   *n_out = 0;

@@ -104,13 +104,23 @@ def test_small_gapped_on_given_hits(B, plain):
 
 def test_thresholds_and_gap_costs(B, plain):
     g1, o1, g2, o2 = plain
-    for s1, s2, go, ge in [(25, 30, 11, 1), (45, 60, 10, 2), (38, 47, 5, 3)]:
+    # the edges of the gap costs the int16 row offsets allow: no gap cost at
+    # all, free opening, costly opening, the largest extension
+    for s1, s2, go, ge in [(25, 30, 11, 1), (45, 60, 10, 2), (38, 47, 5, 3), (38, 47, 0, 0), (38, 47, 0, 4),
+                           (38, 40, 1000, 1), (38, 40, 7, 400)]:
         prm = oracle.Params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
         gp = B.plast_default_params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
         recs, n_ung = B.plast_search(g1, g2, gp)
         want_h = oracle.ungapped(o1, o2, prm)
         assert n_ung == len(want_h)
         assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h, prm))
+
+
+def test_gap_cost_limits(B, plain):
+    g1, _, g2, _ = plain
+    for go, ge in [(1001, 1), (11, 401), (-1, 1), (11, -1)]:
+        with pytest.raises(B.PlastError):
+            B.plast_search(g1, g2, B.plast_default_params(gap_open=go, gap_extend=ge))
 
 
 def test_plain_schedule_matches_persistent(B):
