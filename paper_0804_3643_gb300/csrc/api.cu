@@ -636,19 +636,19 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     if ((rc = ck(cudaMemcpyAsync(d_seq_off, seq_off, ((size_t)n_seqs + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToDevice, st))))
       return fail(rc);
-    if ((rc = ck(launch_check_codes(codes, n_res, 0, 20, d_bad, st)))) return fail(rc);
-    if ((rc = ck(launch_build_pad(codes, d_seq_off, n_seqs, n_res, b->pad, n_pad, st)))) return fail(rc);
-    int32_t *d_key, *d_flag;
-    int64_t *d_at, *d_total;
-    if ((rc = ck(sc.get(&d_key, n_pad)))) return fail(rc);
-    if ((rc = ck(sc.get(&d_flag, n_pad)))) return fail(rc);
-    if ((rc = ck(sc.get(&d_at, n_pad)))) return fail(rc);
+    if ((rc = ck(launch_build_pad(codes, d_seq_off, n_seqs, n_res, 20, b->pad, d_bad, st)))) return fail(rc);
+    const int64_t ix_tile = index_tile(n_pad), n_tiles = (n_pad + ix_tile - 1) / ix_tile;
+    const int64_t n_cells = (int64_t)NKEYS * n_tiles;
+    int32_t* d_hist;
+    int64_t *d_off, *d_total;
+    if ((rc = ck(sc.get(&d_hist, n_cells)))) return fail(rc);
+    if ((rc = ck(sc.get(&d_off, n_cells)))) return fail(rc);
     if ((rc = ck(sc.get(&d_total, 1)))) return fail(rc);
-    if ((rc = ck(launch_word_keys(b->pad, n_pad, d_key, d_flag, st)))) return fail(rc);
+    if ((rc = ck(launch_index_hist(b->pad, n_pad, ix_tile, n_tiles, d_hist, st)))) return fail(rc);
     void* stmp;
-    size_t stb = scan_tmp_bytes(n_pad);
+    size_t stb = scan_tmp_bytes(n_cells);
     if ((rc = ck(sc.get((char**)&stmp, stb)))) return fail(rc);
-    if ((rc = ck(scan_exclusive(d_flag, d_at, n_pad, d_total, stmp, stb, st)))) return fail(rc);
+    if ((rc = ck(scan_exclusive(d_hist, d_off, n_cells, d_total, stmp, stb, st)))) return fail(rc);
     int64_t n_idx = 0;
     int h_bad = 0;
     if ((rc = ck(cudaMemcpyAsync(&n_idx, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st)))) return fail(rc);
@@ -656,28 +656,13 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
     if (h_bad) return fail(PLAST_E_INVALID);
     b->n_idx = n_idx;
-    uint64_t *k0, *k1;
-    uint32_t* v1;
-    if ((rc = ck(sc.get(&k0, n_idx)))) return fail(rc);
-    if ((rc = ck(sc.get(&k1, n_idx)))) return fail(rc);
     if ((rc = ck(cudaMallocAsync((void**)&b->pos, (size_t)std::max<int64_t>(n_idx, 1) * sizeof(uint32_t), st))))
       return fail(rc);
-    if ((rc = ck(sc.get(&v1, n_idx)))) return fail(rc);
-    if ((rc = ck(launch_compact_words(d_key, d_at, n_pad, k0, b->pos, st)))) return fail(rc);
-    sc.release(d_key);
-    sc.release(d_flag);
-    sc.release(d_at);
-    void* rtmp;
-    size_t rtb = radix_tmp_bytes(n_idx);
-    if ((rc = ck(sc.get((char**)&rtmp, rtb)))) return fail(rc);
-    bool alt = false;
-    if ((rc = ck(radix_sort_pairs(k0, b->pos, k1, v1, n_idx, 14, rtmp, rtb, st, &alt)))) return fail(rc);
-    uint64_t* skey = alt ? k1 : k0;
-    if (alt && n_idx > 0) {
-      if ((rc = ck(cudaMemcpyAsync(b->pos, v1, n_idx * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st))))
-        return fail(rc);
-    }
-    if ((rc = ck(launch_key_offsets(skey, n_idx, b->key_off, st)))) return fail(rc);
+    int64_t* d_offT;
+    if ((rc = ck(sc.get(&d_offT, n_cells)))) return fail(rc);
+    if ((rc = ck(launch_index_finish(b->pad, n_pad, ix_tile, n_tiles, d_off, d_offT, d_total, b->key_off, b->pos,
+                                     st))))
+      return fail(rc);
     b->h_key_off.resize(NKEYS + 1);
     if ((rc = ck(cudaMemcpyAsync(b->h_key_off.data(), b->key_off, (NKEYS + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st))))
