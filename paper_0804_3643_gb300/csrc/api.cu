@@ -184,6 +184,15 @@ struct TileList {
 // pieces re-sorted costliest first.  v[lo, hi) is one launch's tile list.
 void split_long_tiles(const plast_tile_costs& c, std::vector<int4>& v, int64_t lo, int64_t hi, int64_t ctas) {
   if (hi <= lo || ctas <= 0) return;
+  // the list is costliest first: a tile above twice the target exists only if
+  // the first one is above it, and the target is at most the first tile's
+  // cost times the tile count over 4 * ctas
+  if (hi - lo > 8 * ctas) {
+    const double c0 = tile_cost(c, tile_shape(v[lo]), (int64_t)v[lo].w - v[lo].z);
+    double total = 0;
+    for (int64_t i = lo; i < hi; i++) total += tile_cost(c, tile_shape(v[i]), (int64_t)v[i].w - v[i].z);
+    if (c0 <= 2 * total / (4.0 * (double)ctas)) return;
+  }
   auto cost = [&](const int4& t) { return tile_cost(c, tile_shape(t), (int64_t)t.w - t.z); };
   double total = 0;
   for (int64_t i = lo; i < hi; i++) total += cost(v[i]);
@@ -242,9 +251,11 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
   if (largest_first) {
     // counting sort by decreasing ceil(n2 / 128), the quantity every tile
     // cost depends on (monotonically), stable in key order
-    constexpr int NB = 1 << 16;
+    int64_t bmax = 0;
+    for (const int k : keys) bmax = std::max<int64_t>(bmax, ko2[k + 1] - ko2[k]);
+    const int NB = (int)std::min<int64_t>(round_up(bmax, WIDE_PASS) / WIDE_PASS + 1, 1 << 20);
     static thread_local std::vector<int32_t> count;
-    count.assign(NB + 1, 0);
+    count.assign((size_t)NB + 1, 0);
     auto bucket = [&](int k) {
       const int64_t b = round_up(ko2[k + 1] - ko2[k], WIDE_PASS) / WIDE_PASS;
       return NB - 1 - (int)std::min<int64_t>(b, NB - 1);
@@ -262,8 +273,14 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
   std::vector<int4> wide;
   std::vector<std::pair<float, int4>> by_shape[4];
   std::vector<int4>* out = largest_first ? nullptr : &tl->tiles;  // plain schedule: key by key
-  if (out) out->reserve((size_t)(rows_total / UNG_T1 + 4 * keys.size()));
-  else wide.reserve((size_t)(rows_total / UNG_T1 + keys.size()));
+  if (out) {
+    out->reserve((size_t)(rows_total / UNG_T1 + 4 * keys.size()));
+  } else {
+    wide.reserve((size_t)(rows_total / UNG_T1 + keys.size()));
+    by_shape[UNG_NARROW].reserve((size_t)(std::min<int64_t>(rows_total / UNG_NT1, 16 * (int64_t)keys.size()) + 16));
+    by_shape[UNG_NARROW4].reserve(keys.size());
+    by_shape[UNG_NARROW2].reserve(keys.size());
+  }
   double cost_now[4] = {0, 0, 0, 0};  // tile costs of the current key's n2
   int32_t n2_now = 0;
   auto emit = [&](int k, int64_t first, int64_t rows, int shape) {

@@ -74,6 +74,15 @@ def test_index_edge_banks(B):
         check_index(B, g, ob)
 
 
+def test_index_many_tiles_low_complexity(B):
+    # a bank cut into many index tiles, with low-complexity runs (keys repeated
+    # many times within one warp's 32 positions and across tile borders)
+    _, b2 = synth.workload("batching_stress", seed=5, scale=0.05)
+    g, o = both(B, b2.codes, b2.seq_off)
+    assert len(b2.codes) > 500_000
+    check_index(B, g, o)
+
+
 def test_ungapped_parity_plain(B, plain):
     g1, o1, g2, o2 = plain
     got = B.hits_numpy(B.plast_ungapped(g1, g2))
