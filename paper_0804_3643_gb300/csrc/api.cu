@@ -17,6 +17,7 @@
 
 #include "bank.cuh"
 #include "common.cuh"
+#include "gapped.cuh"
 #include "filter.cuh"
 #include "index.cuh"
 #include "ungapped.cuh"
@@ -581,7 +582,8 @@ void plast_bank_free(plast_bank* b) {
     cudaEventDestroy(b->ready);
   }
   // pool memory, returned in order with the legacy default stream
-  for (void* p : {(void*)b->pad_alloc, (void*)b->pad_off, (void*)b->key_off, (void*)b->pos, (void*)b->nb})
+  for (void* p : {(void*)b->pad_alloc, (void*)b->pad_off, (void*)b->blk_seq, (void*)b->key_off, (void*)b->pos,
+                  (void*)b->nb})
     if (p) cudaFreeAsync(p, 0);
   delete b;
 }
@@ -649,6 +651,9 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     if ((rc = ck(cudaMemcpyAsync(b->pad_off, b->h_pad_off.data(), b->h_pad_off.size() * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st))))
       return fail(rc);
+    if ((rc = ck(cudaMallocAsync((void**)&b->blk_seq, ((size_t)(n_pad / SEQ_BLK) + 1) * sizeof(int32_t), st))))
+      return fail(rc);
+    if ((rc = ck(launch_block_seq(b->pad_off, n_seqs, n_pad, b->blk_seq, st)))) return fail(rc);
     if ((rc = ck(sc.get(&d_seq_off, (size_t)n_seqs + 1)))) return fail(rc);
     if ((rc = ck(cudaMemcpyAsync(d_seq_off, seq_off, ((size_t)n_seqs + 1) * sizeof(int64_t),
                                  cudaMemcpyDeviceToDevice, st))))
@@ -750,8 +755,7 @@ static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast
   int* d_bad;
   CK(sc.get(&d_bad, 1));
   CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
-  CK(launch_expand_hits(sv.key, sv.val, sv.n, sv.sh, b1->pad, b1->pad_off, b1->n_seqs, b2->pad, b2->pad_off,
-                        b2->n_seqs, out, d_bad, st));
+  CK(launch_expand_hits(sv.key, sv.val, sv.n, sv.sh, b1->pad, seq_map(b1), b2->pad, seq_map(b2), out, d_bad, st));
   int h_bad = 0;
   if ((rc = check_bad(d_bad, st, &h_bad))) return rc;
   return h_bad ? PLAST_E_CUDA : PLAST_OK;
@@ -793,7 +797,7 @@ int run_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params& p
   if (m > cap) return PLAST_E_CAPACITY;
   if (m == 0) return PLAST_OK;
   if (!out) return PLAST_E_INVALID;
-  CK(launch_gapped_compact(g, at, b1->pad_off, b1->n_seqs, b2->pad_off, b2->n_seqs, out, st));
+  CK(launch_gapped_compact(g, at, seq_map(b1), seq_map(b2), out, st));
   t_timer.mark(5, st);
   CK(cudaStreamSynchronize(st));
   return PLAST_OK;
@@ -818,39 +822,37 @@ int run_gapped_search(const plast_bank* b1, const plast_bank* b2, const plast_pa
   g.gap_open = prm.gap_open;
   g.gap_extend = prm.gap_extend;
   g.s2 = prm.s2;
-  int64_t *at, *total;
+  // the passing hits come out of stage 3.1 as (key, hit index), in any order
+  uint64_t *rk0, *rk1;
+  uint32_t *ri0, *ri1;
   CK(sc.get(&g.score, n));
   CK(sc.get(&g.ends, n));
   CK(sc.get(&g.pass, n));
-  CK(sc.get(&at, n));
-  CK(sc.get(&total, 1));
+  CK(sc.get(&rk0, n));
+  CK(sc.get(&ri0, n));
+  CK(sc.get(&g.rcount, 1));
+  g.rkey = rk0;
+  g.ridx = ri0;
+  CK(cudaMemsetAsync(g.rcount, 0, sizeof(unsigned long long), st));
   CK(launch_small_gapped(g, st));
   t_timer.mark(4, st);
-  void* stmp;
-  size_t stb = scan_tmp_bytes(n);
-  CK(sc.get((char**)&stmp, stb));
-  CK(scan_exclusive(g.pass, at, n, total, stmp, stb, st));
-  int64_t m = 0;
-  CK(cudaMemcpyAsync(&m, total, sizeof(m), cudaMemcpyDeviceToHost, st));
+  CK(launch_compact_pass(g, st));
+  unsigned long long mc = 0;
+  CK(cudaMemcpyAsync(&mc, g.rcount, sizeof(mc), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  const int64_t m = (int64_t)mc;
   *n_out = m;
   if (m > cap) return PLAST_E_CAPACITY;
   if (m == 0) return PLAST_OK;
   if (!out) return PLAST_E_INVALID;
-  uint64_t *rk0, *rk1;
-  uint32_t *ri0, *ri1;
-  CK(sc.get(&rk0, m));
   CK(sc.get(&rk1, m));
-  CK(sc.get(&ri0, m));
   CK(sc.get(&ri1, m));
   void* rtmp;
   size_t rtb = radix_tmp_bytes(m);
   CK(sc.get((char**)&rtmp, rtb));
-  CK(launch_gather_pass(g, at, rk0, ri0, st));
   bool alt = false;
   CK(radix_sort_pairs(rk0, ri0, rk1, ri1, m, b1->pad_bits + sv.sh, rtmp, rtb, st, &alt));
-  CK(launch_write_sorted(g, alt ? rk1 : rk0, alt ? ri1 : ri0, m, nullptr, b1->pad_off, b1->n_seqs, b2->pad_off,
-                         b2->n_seqs, out, st));
+  CK(launch_write_sorted(g, alt ? rk1 : rk0, alt ? ri1 : ri0, m, nullptr, seq_map(b1), seq_map(b2), out, st));
   t_timer.mark(5, st);
   CK(cudaStreamSynchronize(st));
   return PLAST_OK;
@@ -1012,10 +1014,7 @@ struct plast_plan {
   int32_t* score = nullptr;
   uint32_t* ends = nullptr;
   int32_t* pass = nullptr;
-  int64_t* at = nullptr;
-  int64_t* total = nullptr;
-  void* stmp = nullptr;
-  size_t stb = 0;
+  int64_t* total = nullptr;   // passing hits (an unsigned long long counter)
   plast_gapped* out = nullptr;  // caller's buffer
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1029,7 +1028,7 @@ void plast_plan_free(plast_plan* p) {
   if (p->graph) cudaGraphDestroy(p->graph);
   for (void* q : {(void*)p->tiles, (void*)p->counter, (void*)p->count, (void*)p->n_dev, (void*)p->m_dev,
                   (void*)p->k0, (void*)p->v0, (void*)p->rk0, (void*)p->rk1, (void*)p->ri0, (void*)p->ri1, p->rtmp,
-                  (void*)p->score, (void*)p->ends, (void*)p->pass, (void*)p->at, (void*)p->total, p->stmp,
+                  (void*)p->score, (void*)p->ends, (void*)p->pass, (void*)p->total,
                   (void*)p->kf, (void*)p->vf, (void*)p->count_f})
     if (q) cudaFree(q);
   delete p;
@@ -1068,7 +1067,6 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   cudaError_t e;
   auto alloc = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes < 16 ? 16 : bytes); };
   p->rtb = radix_tmp_bytes(max_records);
-  p->stb = scan_tmp_bytes(max_hits);
   if ((e = alloc((void**)&p->tiles, sizeof(int4) * (size_t)std::max<int64_t>(p->n_tiles, 1))) ||
       (e = alloc((void**)&p->counter, 2 * sizeof(int32_t))) ||
       (e = alloc((void**)&p->count, sizeof(unsigned long long))) ||
@@ -1078,8 +1076,8 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
       (e = alloc((void**)&p->ri0, 4 * (size_t)max_records)) || (e = alloc((void**)&p->ri1, 4 * (size_t)max_records)) ||
       (e = alloc(&p->rtmp, p->rtb)) ||
       (e = alloc((void**)&p->score, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->ends, 4 * (size_t)max_hits)) ||
-      (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) || (e = alloc((void**)&p->at, 8 * (size_t)max_hits)) ||
-      (e = alloc((void**)&p->total, sizeof(int64_t))) || (e = alloc(&p->stmp, p->stb)))
+      (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) ||
+      (e = alloc((void**)&p->total, sizeof(unsigned long long))))
     return fail(e);
   if (p->prm.s0 > 0 &&
       ((e = alloc((void**)&p->kf, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->vf, 4 * (size_t)max_hits)) ||
@@ -1149,14 +1147,16 @@ int plast_plan_run(plast_plan* p, void* stream) {
   g.pass = p->pass;
   g.n_dev = p->n_dev;
   g.out_cap = p->max_records;
+  g.rkey = p->rk0;  // the passing hits, appended in any order (sorted below)
+  g.ridx = p->ri0;
+  g.rcount = reinterpret_cast<unsigned long long*>(p->total);
   CK(launch_small_gapped(g, st));
-  CK(scan_exclusive(g.pass, p->at, p->max_hits, p->total, p->stmp, p->stb, st, p->n_dev));
-  CK(launch_clamp_total(p->total, p->max_records, p->m_dev, st));
-  CK(launch_gather_pass(g, p->at, p->rk0, p->ri0, st));
+  CK(launch_compact_pass(g, st));
+  CK(launch_clamp_count(g.rcount, p->max_records, p->m_dev, st));
   bool alt = false;
   CK(radix_sort_pairs(p->rk0, p->ri0, p->rk1, p->ri1, p->max_records, p->bits, p->rtmp, p->rtb, st, &alt, p->m_dev));
-  CK(launch_write_sorted(g, alt ? p->rk1 : p->rk0, alt ? p->ri1 : p->ri0, p->max_records, p->m_dev, p->b1->pad_off,
-                         p->b1->n_seqs, p->b2->pad_off, p->b2->n_seqs, p->out, st));
+  CK(launch_write_sorted(g, alt ? p->rk1 : p->rk0, alt ? p->ri1 : p->ri0, p->max_records, p->m_dev, seq_map(p->b1),
+                         seq_map(p->b2), p->out, st));
   return PLAST_OK;
 }
 

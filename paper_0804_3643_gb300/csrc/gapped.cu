@@ -45,8 +45,9 @@
 // ends.  Columns j < 0 start at -16000 and stay far below zero.  Columns
 // j > LG (rows i > LG - BAND) lie outside the grid; they feed no cell of the
 // grid and are kept out of the maximum (compile-time column limits).
+#include "gapped.cuh"
+
 #include "common.cuh"
-#include "ungapped.cuh"
 
 namespace plast {
 
@@ -301,6 +302,63 @@ __global__ void __launch_bounds__(GAP_THREADS, 2) k_small_gapped(GapArgs a) {
   }
 }
 
+// The passing hits as (key, hit index) appended to rkey / ridx (slots below
+// out_cap written), their number added to *rcount.  A CTA takes 4,096
+// consecutive hits, 16 per thread; a block-wide scan of the per-thread
+// counts places them behind one atomic per CTA (a single counter taking one
+// atomic per warp would serialise on it).
+constexpr int CP_THREADS = 256;
+constexpr int CP_PER = 16;
+__global__ void __launch_bounds__(CP_THREADS) k_compact_pass(GapArgs a) {
+  __shared__ int wsum[CP_THREADS / 32];
+  __shared__ unsigned long long block_at;
+  const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = (int64_t)blockIdx.x * CP_THREADS * CP_PER; base < n;
+       base += (int64_t)gridDim.x * CP_THREADS * CP_PER) {
+    const int64_t h0 = base + (int64_t)threadIdx.x * CP_PER;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int j = 0; j < CP_PER; j++)
+      if (h0 + j < n && a.pass[h0 + j]) bits |= 1u << j;
+    const int c = __popc(bits);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < CP_THREADS / 32; w++) t += wsum[w];
+      block_at = t ? atomicAdd(a.rcount, (unsigned long long)t) : 0;
+    }
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; w++) before += wsum[w];
+    unsigned long long at = block_at + before + x - c;
+    for (; bits; bits &= bits - 1, at++) {
+      const int64_t h = h0 + __ffs(bits) - 1;
+      if ((int64_t)at < a.out_cap) {
+        a.rkey[at] = a.key[h];
+        a.ridx[at] = (uint32_t)h;
+      }
+    }
+    __syncthreads();  // wsum and block_at are reused
+  }
+}
+
+cudaError_t launch_compact_pass(const GapArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  int64_t b = (a.n + CP_THREADS * CP_PER - 1) / (CP_THREADS * CP_PER);
+  if (b > 152 * 16) b = 152 * 16;
+  note_launch();
+  k_compact_pass<<<(unsigned)b, CP_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st) {
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -321,21 +379,12 @@ cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ int32_t find_seq_g(const int64_t* off, int32_t n, int64_t p) {
-  int32_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int32_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ plast_gapped make_record(const GapArgs& a, int64_t h, uint64_t key,
-                                                    const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
-                                                    int32_t n2) {
+__device__ __forceinline__ plast_gapped make_record(const GapArgs& a, int64_t h, uint64_t key, const SeqMap& s1,
+                                                    const SeqMap& s2) {
   const int64_t p1 = (int64_t)(key >> a.sh), p2 = (int64_t)(key & ((1ull << a.sh) - 1));
-  const int32_t q1 = find_seq_g(pad_off1, n1, p1), q2 = find_seq_g(pad_off2, n2, p2);
+  const int32_t q1 = seq_of(s1, p1), q2 = seq_of(s2, p2);
+  const int64_t* pad_off1 = s1.pad_off;
+  const int64_t* pad_off2 = s2.pad_off;
   const uint32_t e = a.ends[h];
   plast_gapped r;
   r.seq1 = q1;
@@ -351,43 +400,30 @@ __device__ __forceinline__ plast_gapped make_record(const GapArgs& a, int64_t h,
   return r;
 }
 
-__global__ void k_gapped_compact(GapArgs a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
-                                 const int64_t* pad_off2, int32_t n2, plast_gapped* out) {
+__global__ void k_gapped_compact(GapArgs a, const int64_t* at, SeqMap s1, SeqMap s2, plast_gapped* out) {
   const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
   for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
     if (!a.pass[h] || at[h] >= a.out_cap) continue;
-    out[at[h]] = make_record(a, h, a.key[h], pad_off1, n1, pad_off2, n2);
-  }
-}
-
-// Passing hits h (record slot at[h] below out_cap): rkey[at[h]] = key[h],
-// ridx[at[h]] = h, for the record sort.
-__global__ void k_gather_pass(GapArgs a, const int64_t* at, uint64_t* rkey, uint32_t* ridx) {
-  const int64_t n = a.n_dev ? min(a.n, max(*a.n_dev, (int64_t)0)) : a.n;
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
-    if (!a.pass[h] || at[h] >= a.out_cap) continue;
-    rkey[at[h]] = a.key[h];
-    ridx[at[h]] = (uint32_t)h;
+    out[at[h]] = make_record(a, h, a.key[h], s1, s2);
   }
 }
 
 // Records in key order: out[r] from hit sidx[r] (key skey[r]), r < m (or
 // < *m_dev, at most m).
 __global__ void k_write_sorted(GapArgs a, const uint64_t* skey, const uint32_t* sidx, int64_t m, const int64_t* m_dev,
-                               const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2, int32_t n2,
-                               plast_gapped* out) {
+                               SeqMap s1, SeqMap s2, plast_gapped* out) {
   if (m_dev) m = min(m, max(*m_dev, (int64_t)0));
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x)
-    out[r] = make_record(a, sidx[r], skey[r], pad_off1, n1, pad_off2, n2);
+    out[r] = make_record(a, sidx[r], skey[r], s1, s2);
 }
 
-cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
-                                  const int64_t* pad_off2, int32_t n2, plast_gapped* out, cudaStream_t st) {
+cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const SeqMap& s1, const SeqMap& s2,
+                                  plast_gapped* out, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   int64_t b = (a.n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
   note_launch();
-  k_gapped_compact<<<(unsigned)b, 256, 0, st>>>(a, at, pad_off1, n1, pad_off2, n2, out);
+  k_gapped_compact<<<(unsigned)b, 256, 0, st>>>(a, at, s1, s2, out);
   return cudaGetLastError();
 }
 
@@ -413,23 +449,14 @@ cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_pass(const GapArgs& a, const int64_t* at, uint64_t* rkey, uint32_t* ridx, cudaStream_t st) {
-  if (a.n <= 0) return cudaSuccess;
-  int64_t b = (a.n + 255) / 256;
-  if (b > 152 * 32) b = 152 * 32;
-  note_launch();
-  k_gather_pass<<<(unsigned)b, 256, 0, st>>>(a, at, rkey, ridx);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_write_sorted(const GapArgs& a, const uint64_t* skey, const uint32_t* sidx, int64_t m,
-                                const int64_t* m_dev, const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
-                                int32_t n2, plast_gapped* out, cudaStream_t st) {
+                                const int64_t* m_dev, const SeqMap& s1, const SeqMap& s2, plast_gapped* out,
+                                cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   int64_t b = (m + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
   note_launch();
-  k_write_sorted<<<(unsigned)b, 256, 0, st>>>(a, skey, sidx, m, m_dev, pad_off1, n1, pad_off2, n2, out);
+  k_write_sorted<<<(unsigned)b, 256, 0, st>>>(a, skey, sidx, m, m_dev, s1, s2, out);
   return cudaGetLastError();
 }
 
@@ -466,6 +493,67 @@ cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* p
   if (b > 152 * 32) b = 152 * 32;
   note_launch();
   k_hits_to_keys<<<(unsigned)b, 256, 0, st>>>(in, n, pad_off1, n1, pad_off2, n2, sh, key, val, bad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Survivor expansion: padded coordinates -> (sequence, local position), and
+// the exact scalar ungapped score with its extents, recomputed per survivor
+// as a self-check of the packed kernel (a mismatch raises *bad).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ungapped_exact(const int8_t* pad1, int64_t p1, const int8_t* pad2, int64_t p2,
+                                              int* rl, int* ll) {
+  int sum = 0, best = 0, r = 0, l = 0;
+  for (int t = 0; t < RIGHT; t++) {
+    sum += c_score[pad1[p1 + t] * NCODE + pad2[p2 + t]];
+    if (sum > best) {
+      best = sum;
+      r = t + 1;
+    }
+  }
+  sum = best;
+  for (int t = 1; t <= LEFT; t++) {
+    sum += c_score[pad1[p1 - t] * NCODE + pad2[p2 - t]];
+    if (sum > best) {
+      best = sum;
+      l = t;
+    }
+  }
+  *rl = r;
+  *ll = l;
+  return best;
+}
+
+__global__ void k_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
+                              SeqMap s1, const int8_t* pad2, SeqMap s2, plast_hit* out, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p1 = (int64_t)(key[i] >> sh), p2 = (int64_t)(key[i] & ((1ull << sh) - 1));
+    int rl, ll;
+    int u = ungapped_exact(pad1, p1, pad2, p2, &rl, &ll);
+    if (u != (int)(int16_t)(val[i] & 0xffffu)) atomicOr(bad, 2);
+    const int32_t q1 = seq_of(s1, p1), q2 = seq_of(s2, p2);
+    const int64_t* pad_off1 = s1.pad_off;
+    const int64_t* pad_off2 = s2.pad_off;
+    plast_hit h;
+    h.seq1 = q1;
+    h.pos1 = (int32_t)(p1 - pad_off1[q1]);
+    h.seq2 = q2;
+    h.pos2 = (int32_t)(p2 - pad_off2[q2]);
+    h.score = (int16_t)u;
+    h.rlen = (int8_t)rl;
+    h.llen = (int8_t)ll;
+    out[i] = h;
+  }
+}
+
+cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
+                               const SeqMap& s1, const int8_t* pad2, const SeqMap& s2, plast_hit* out, int* bad,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  note_launch();
+  k_expand_hits<<<(unsigned)b, 256, 0, st>>>(key, val, n, sh, pad1, s1, pad2, s2, out, bad);
   return cudaGetLastError();
 }
 

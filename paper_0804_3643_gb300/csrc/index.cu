@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gapped.cuh"
 #include "index.cuh"
 
 namespace plast {
@@ -301,6 +302,11 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbourhoods(const int8_t* pad
   }
 }
 
+__global__ void k_block_seq(const int64_t* pad_off, int32_t n_seqs, int64_t n_blk, int32_t* blk) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_blk; i += (int64_t)gridDim.x * blockDim.x)
+    blk[i] = n_seqs > 0 ? find_seq(pad_off, n_seqs, i * SEQ_BLK) : 0;
+}
+
 __global__ void k_export_pos(const uint32_t* pos, int64_t n, const int64_t* pad_off, int32_t n_seqs, int32_t* out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t p = pos[i];
@@ -424,6 +430,13 @@ cudaError_t launch_neighbourhoods(const int8_t* pad, const uint32_t* pos, int64_
     note_launch();
     k_neighbourhoods<<<grid_for(n, NB_THREADS), NB_THREADS, 0, st>>>(pad, pos, n, nb);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_seq(const int64_t* pad_off, int32_t n_seqs, int64_t n_pad, int32_t* blk, cudaStream_t st) {
+  const int64_t n_blk = n_pad / SEQ_BLK + 1;
+  note_launch();
+  k_block_seq<<<grid_for(n_blk, 256), 256, 0, st>>>(pad_off, n_seqs, n_blk, blk);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,8 @@ cudaError_t launch_index_finish(const int8_t* pad, int64_t n_pad, int64_t tile, 
                                 int64_t* offT, const int64_t* total, int64_t* key_off, uint32_t* pos,
                                 cudaStream_t st);
 cudaError_t launch_neighbourhoods(const int8_t* pad, const uint32_t* pos, int64_t n, int8_t* nb, cudaStream_t st);
+// blk[i] = the sequence at padded position i * SEQ_BLK, i <= n_pad / SEQ_BLK
+cudaError_t launch_block_seq(const int64_t* pad_off, int32_t n_seqs, int64_t n_pad, int32_t* blk, cudaStream_t st);
 cudaError_t launch_export_pos(const uint32_t* pos, int64_t n, const int64_t* pad_off, int32_t n_seqs, int32_t* out,
                               cudaStream_t st);
 cudaError_t launch_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, const int64_t* seq_off,

@@ -16,6 +16,7 @@
 
 #include "bank.cuh"
 #include "common.cuh"
+#include "gapped.cuh"
 #include "ungapped.cuh"
 
 namespace {
@@ -139,7 +140,7 @@ extern "C" int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank
   if (m > cap) return PLAST_E_CAPACITY;
   if (m == 0) return PLAST_OK;
   if (!out) return PLAST_E_INVALID;
-  CKN(launch_gapped_compact(g, at, b1->pad_off, b1->n_seqs, b2->pad_off, b2->n_seqs, out, st));
+  CKN(launch_gapped_compact(g, at, seq_map(b1), seq_map(b2), out, st));
   CKN(cudaStreamSynchronize(st));
   return PLAST_OK;
 }

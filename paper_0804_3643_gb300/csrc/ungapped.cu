@@ -718,74 +718,4 @@ cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// Survivor expansion: padded coordinates -> (sequence, local position), and
-// the exact scalar ungapped score with its extents, recomputed per survivor
-// as a self-check of the packed kernel (a mismatch raises *bad).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int32_t find_seq_u(const int64_t* off, int32_t n, int64_t p) {
-  int32_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int32_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int ungapped_exact(const int8_t* pad1, int64_t p1, const int8_t* pad2, int64_t p2,
-                                              int* rl, int* ll) {
-  int sum = 0, best = 0, r = 0, l = 0;
-  for (int t = 0; t < RIGHT; t++) {
-    sum += c_score[pad1[p1 + t] * NCODE + pad2[p2 + t]];
-    if (sum > best) {
-      best = sum;
-      r = t + 1;
-    }
-  }
-  sum = best;
-  for (int t = 1; t <= LEFT; t++) {
-    sum += c_score[pad1[p1 - t] * NCODE + pad2[p2 - t]];
-    if (sum > best) {
-      best = sum;
-      l = t;
-    }
-  }
-  *rl = r;
-  *ll = l;
-  return best;
-}
-
-__global__ void k_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
-                              const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
-                              int32_t n2, plast_hit* out, int* bad) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t p1 = (int64_t)(key[i] >> sh), p2 = (int64_t)(key[i] & ((1ull << sh) - 1));
-    int rl, ll;
-    int u = ungapped_exact(pad1, p1, pad2, p2, &rl, &ll);
-    if (u != (int)(int16_t)(val[i] & 0xffffu)) atomicOr(bad, 2);
-    int32_t q1 = find_seq_u(pad_off1, n1, p1), q2 = find_seq_u(pad_off2, n2, p2);
-    plast_hit h;
-    h.seq1 = q1;
-    h.pos1 = (int32_t)(p1 - pad_off1[q1]);
-    h.seq2 = q2;
-    h.pos2 = (int32_t)(p2 - pad_off2[q2]);
-    h.score = (int16_t)u;
-    h.rlen = (int8_t)rl;
-    h.llen = (int8_t)ll;
-    out[i] = h;
-  }
-}
-
-cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
-                               const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
-                               int32_t n2, plast_hit* out, int* bad, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  int64_t b = (n + 255) / 256;
-  if (b > 152 * 32) b = 152 * 32;
-  note_launch();
-  k_expand_hits<<<(unsigned)b, 256, 0, st>>>(key, val, n, sh, pad1, pad_off1, n1, pad2, pad_off2, n2, out, bad);
-  return cudaGetLastError();
-}
-
 }  // namespace plast

@@ -51,40 +51,4 @@ cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st);
 constexpr int UNG_NARROW_CTAS_PER_SM = 2;
 constexpr int UNG_NARROW_PASS = 512;  // bank-2 windows a narrow CTA scores per pass
-cudaError_t launch_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
-                               const int64_t* pad_off1, int32_t n1, const int8_t* pad2, const int64_t* pad_off2,
-                               int32_t n2, plast_hit* out, int* bad, cudaStream_t st);
-
-// gapped.cu
-struct GapArgs {
-  const int8_t* pad1;
-  const int8_t* pad2;
-  const uint64_t* key;      // (padded pos1 << sh | padded pos2) per hit
-  const uint32_t* val;      // stage-2 score per hit in the low 16 bits
-  int64_t n;
-  int32_t sh;
-  int32_t gap_open, gap_extend, s2;
-  int32_t* score;           // out: small gapped score per hit
-  uint32_t* ends;           // out: r_i | r_j << 8 | l_i << 16 | l_j << 24
-  int32_t* pass;            // out: score >= s2
-  const int64_t* n_dev = nullptr;  // optional device copy of the hit count (<= n)
-  int64_t out_cap = INT64_MAX;     // records written only below this index
-};
-cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st);
-cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const int64_t* pad_off1, int32_t n1,
-                                  const int64_t* pad_off2, int32_t n2, plast_gapped* out, cudaStream_t st);
-// *n_dev = min(*count, cap): the hit count a planned chain feeds forward.
-cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st);
-cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev, cudaStream_t st);
-// Record sort of a search: the passing hits' keys and indexes gathered into
-// record slots, then (after sorting the pairs by key) the records written in
-// key order.
-cudaError_t launch_gather_pass(const GapArgs& a, const int64_t* at, uint64_t* rkey, uint32_t* ridx, cudaStream_t st);
-cudaError_t launch_write_sorted(const GapArgs& a, const uint64_t* skey, const uint32_t* sidx, int64_t m,
-                                const int64_t* m_dev, const int64_t* pad_off1, int32_t n1, const int64_t* pad_off2,
-                                int32_t n2, plast_gapped* out, cudaStream_t st);
-cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* pad_off1, int32_t n1,
-                                const int64_t* pad_off2, int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad,
-                                cudaStream_t st);
-
 }  // namespace plast
