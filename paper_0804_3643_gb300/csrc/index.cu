@@ -322,27 +322,44 @@ __global__ void k_export_pos(const uint32_t* pos, int64_t n, const int64_t* pad_
 __constant__ char c_code[65] = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF";
 __constant__ int8_t c_aa_of_letter[26];
 
+// One thread per 16 consecutive translated residues: one binary search for
+// the sequence (contig, frame) of the first, then a walk forward.
+constexpr int TR_PER = 16;
 __global__ void k_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, const int64_t* seq_off,
                              int64_t n_aa, int8_t* aa) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_aa; t += (int64_t)gridDim.x * blockDim.x) {
-    int32_t s = find_seq(seq_off, 6 * n_contigs, t);
+  // codon -> residue code, in shared memory (lanes read different entries,
+  // which constant memory would serialise)
+  __shared__ int8_t code_of[64];
+  if (threadIdx.x < 64) {
+    const char letter = c_code[threadIdx.x];
+    code_of[threadIdx.x] = letter == '*' ? (int8_t)STOP : c_aa_of_letter[letter - 'A'];
+  }
+  __syncthreads();
+  const int32_t n_seqs = 6 * n_contigs;
+  const int64_t n_chunks = (n_aa + TR_PER - 1) / TR_PER;
+  for (int64_t ch = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks;
+       ch += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t0 = ch * TR_PER, t1 = min(t0 + TR_PER, n_aa);
     // the last sequence with seq_off[s] <= t that is not empty holds t
-    int32_t c = s / 6, f = s % 6;
-    int64_t i = t - seq_off[s];
-    int64_t c0 = contig_off[c], L = contig_off[c + 1] - c0;
-    int64_t q = (f % 3) + 3 * i;
-    int n1, n2, n3;
-    if (f < 3) {
-      n1 = dna[c0 + q];
-      n2 = dna[c0 + q + 1];
-      n3 = dna[c0 + q + 2];
-    } else {
-      n1 = 3 - dna[c0 + L - 1 - q];
-      n2 = 3 - dna[c0 + L - 2 - q];
-      n3 = 3 - dna[c0 + L - 3 - q];
+    int32_t s = find_seq(seq_off, n_seqs, t0);
+    for (int64_t t = t0; t < t1; t++) {
+      while (s + 1 < n_seqs && seq_off[s + 1] <= t) s++;
+      const int32_t c = s / 6, f = s % 6;
+      const int64_t i = t - seq_off[s];
+      const int64_t c0 = contig_off[c], L = contig_off[c + 1] - c0;
+      const int64_t q = (f % 3) + 3 * i;
+      int n1, n2, n3;
+      if (f < 3) {
+        n1 = dna[c0 + q];
+        n2 = dna[c0 + q + 1];
+        n3 = dna[c0 + q + 2];
+      } else {
+        n1 = 3 - dna[c0 + L - 1 - q];
+        n2 = 3 - dna[c0 + L - 2 - q];
+        n3 = 3 - dna[c0 + L - 3 - q];
+      }
+      aa[t] = code_of[n1 * 16 + n2 * 4 + n3];
     }
-    char letter = c_code[n1 * 16 + n2 * 4 + n3];
-    aa[t] = letter == '*' ? (int8_t)STOP : c_aa_of_letter[letter - 'A'];
   }
 }
 
@@ -455,7 +472,8 @@ cudaError_t launch_translate6(const uint8_t* dna, const int64_t* contig_off, int
   if (e != cudaSuccess) return e;
   if (n_aa > 0) {
     note_launch();
-    k_translate6<<<grid_for(n_aa, 256), 256, 0, st>>>(dna, contig_off, n_contigs, seq_off, n_aa, aa);
+    k_translate6<<<grid_for((n_aa + TR_PER - 1) / TR_PER, 256), 256, 0, st>>>(dna, contig_off, n_contigs, seq_off,
+                                                                              n_aa, aa);
   }
   return cudaGetLastError();
 }

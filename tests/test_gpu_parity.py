@@ -249,6 +249,12 @@ def test_errors(B):
     with pytest.raises(B.PlastError) as e:
         B.plast_translate6(dna, torch.tensor([0, 3], dtype=torch.int64, device="cuda"))
     assert e.value.code == B.PLAST_E_INVALID
+    # a bank whose padded length reaches 2^31 is refused before any kernel
+    # reads its codes (the offsets alone are checked on the host)
+    big = torch.tensor([0, 2 ** 31 - 100], dtype=torch.int64, device="cuda")
+    with pytest.raises(B.PlastError) as e:
+        B.plast_index_bank(torch.zeros(16, dtype=torch.int8, device="cuda"), big)
+    assert e.value.code == B.PLAST_E_INVALID
 
 
 def test_bank_built_on_another_stream(B):
