@@ -501,11 +501,11 @@ cudaError_t launch_hits_to_keys(const plast_hit* in, int64_t n, const int64_t* p
 // the exact scalar ungapped score with its extents, recomputed per survivor
 // as a self-check of the packed kernel (a mismatch raises *bad).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int ungapped_exact(const int8_t* pad1, int64_t p1, const int8_t* pad2, int64_t p2,
-                                              int* rl, int* ll) {
+__device__ __forceinline__ int ungapped_exact(const int8_t* tab, const int8_t* pad1, int64_t p1, const int8_t* pad2,
+                                              int64_t p2, int* rl, int* ll) {
   int sum = 0, best = 0, r = 0, l = 0;
   for (int t = 0; t < RIGHT; t++) {
-    sum += c_score[pad1[p1 + t] * NCODE + pad2[p2 + t]];
+    sum += tab[pad1[p1 + t] * NCODE + pad2[p2 + t]];
     if (sum > best) {
       best = sum;
       r = t + 1;
@@ -513,7 +513,7 @@ __device__ __forceinline__ int ungapped_exact(const int8_t* pad1, int64_t p1, co
   }
   sum = best;
   for (int t = 1; t <= LEFT; t++) {
-    sum += c_score[pad1[p1 - t] * NCODE + pad2[p2 - t]];
+    sum += tab[pad1[p1 - t] * NCODE + pad2[p2 - t]];
     if (sum > best) {
       best = sum;
       l = t;
@@ -526,10 +526,13 @@ __device__ __forceinline__ int ungapped_exact(const int8_t* pad1, int64_t p1, co
 
 __global__ void k_expand_hits(const uint64_t* key, const uint32_t* val, int64_t n, int sh, const int8_t* pad1,
                               SeqMap s1, const int8_t* pad2, SeqMap s2, plast_hit* out, int* bad) {
+  __shared__ int8_t tab[NCODE * NCODE];  // lanes look up different entries
+  for (int i = threadIdx.x; i < NCODE * NCODE; i += blockDim.x) tab[i] = c_score[i];
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t p1 = (int64_t)(key[i] >> sh), p2 = (int64_t)(key[i] & ((1ull << sh) - 1));
     int rl, ll;
-    int u = ungapped_exact(pad1, p1, pad2, p2, &rl, &ll);
+    int u = ungapped_exact(tab, pad1, p1, pad2, p2, &rl, &ll);
     if (u != (int)(int16_t)(val[i] & 0xffffu)) atomicOr(bad, 2);
     const int32_t q1 = seq_of(s1, p1), q2 = seq_of(s2, p2);
     const int64_t* pad_off1 = s1.pad_off;
