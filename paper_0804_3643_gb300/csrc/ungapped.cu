@@ -232,6 +232,30 @@ __device__ __forceinline__ void narrow_pairs(uint32_t row, const unsigned char* 
   }
 }
 
+// The same with the lane's window in registers (cell k = byte k of win).
+template <int K, int NW>
+__device__ __forceinline__ void narrow_pairs_reg(const uint32_t (&win)[12], const unsigned char* plane,
+                                                 uint32_t (&s)[NW], uint32_t (&m)[NW]) {
+  if constexpr (K < WIN) {
+    const uint32_t b0 = (win[K >> 2] >> (8 * (K & 3))) & 0xffu;
+    const uint32_t b1 = (win[(K + 1) >> 2] >> (8 * ((K + 1) & 3))) & 0xffu;
+    uint32_t u0[NW], u1[NW];
+    narrow_scores<NW>(plane, K, b0, u0);
+    narrow_scores<NW>(plane, K + 1, b1, u1);
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+      const uint32_t t0 = __vadd2(s[w], u0[w]);
+      s[w] = __vadd2(t0, u1[w]);
+      m[w] = __vimax3_s16x2(m[w], t0, s[w]);
+    }
+    if constexpr (K + 1 == RIGHT - 1) {
+#pragma unroll
+      for (int w = 0; w < NW; w++) s[w] = m[w];
+    }
+    narrow_pairs_reg<K + 2, NW>(win, plane, s, m);
+  }
+}
+
 // Records the rows of this lane whose score reaches s1 against bank-2
 // occurrence v: rows r0 + i for i < 2 * NW (row 2w in the low half of m[w],
 // row 2w + 1 in the high half), of which the first valid_rows exist.
@@ -406,6 +430,48 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
   }
   __syncthreads();
 
+  // window indexes relative to the key's first (32-bit arithmetic)
+  if constexpr (NW <= 2) {
+    // 2 or 4 rows: few operations per cell, so the lane's own window stays in
+    // registers (three 16-byte loads, one iteration ahead) and each cell's
+    // residue is a byte of it, not a shared-memory load
+    const int n2 = (int)(v1 - v0);
+    const uint4* src = reinterpret_cast<const uint4*>(a.nb2 + v0 * WIN);
+    uint4 cur[3];
+    {
+      const int v = warp * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < 3; j++) cur[j] = v < n2 ? __ldg(src + (int64_t)v * 3 + j) : sent16;
+    }
+    for (int vb = warp * 32; vb < n2; vb += NT_WARPS * 32) {
+      const bool vok = vb + lane < n2;
+      uint4 nxt[3];
+      {
+        const int vn = vb + NT_WARPS * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < 3; j++) nxt[j] = vn < n2 ? __ldg(src + (int64_t)vn * 3 + j) : sent16;
+      }
+      const uint32_t win[12] = {cur[0].x, cur[0].y, cur[0].z, cur[0].w, cur[1].x, cur[1].y,
+                                cur[1].z, cur[1].w, cur[2].x, cur[2].y, cur[2].z, cur[2].w};
+      uint32_t s[NW], m[NW];
+      {  // cells 0-3 from the folded seed planes
+        const uint32_t bs1 = (win[0] >> 8) & 0xffu, bs2 = (win[0] >> 16) & 0xffu;
+        uint32_t up[NW], uq[NW];
+        narrow_scores<NW>(nprof, 0, bs1, up);
+        narrow_scores<NW>(nprof, 2, bs2, uq);
+#pragma unroll
+        for (int w = 0; w < NW; w++) s[w] = __vadd2(up[w], uq[w]);
+        narrow_scores<NW>(nprof, 1, bs1, up);
+#pragma unroll
+        for (int w = 0; w < NW; w++) m[w] = __vmaxs2(up[w], s[w]);
+      }
+      narrow_pairs_reg<FIRST_CELL, NW>(win, nprof, s, m);
+      emit_hits<NW>(m, vok, rows, u0, v0 + vb + lane, a, s1x2, lane, my_wk, my_wv, wcnt);
+#pragma unroll
+      for (int j = 0; j < 3; j++) cur[j] = nxt[j];
+    }
+    return;
+  }
   // the warp's 32 windows are 96 consecutive 16-byte items; lane l moves
   // items l, l + 32, l + 64 (window q / 3, part q % 3), one iteration ahead
   int nw[3], np[3];
