@@ -39,7 +39,8 @@ extern "C" {
 #define PLAST_E_OOM (-2)      /* a device allocation failed */
 #define PLAST_E_CAPACITY (-3) /* output buffer too small; *n_out = needed */
 #define PLAST_E_CUDA (-4)     /* a CUDA runtime call or kernel failed */
-#define PLAST_E_TIMEOUT (-5)  /* a bounded device-side wait expired */
+#define PLAST_E_TIMEOUT (-5)  /* a bounded device-side wait expired (reserved: no
+                                 kernel of this library waits on another CTA) */
 
 #define PLAST_NKEYS 8800 /* subset-seed keys: 20 * 2 * 11 * 20 */
 #define PLAST_MAX_STAGES 5 /* stage intervals reported by plast_stage_times */
@@ -272,6 +273,15 @@ int plast_plan_capture(plast_plan* plan, void* stream);
 int plast_plan_launch(plast_plan* plan, void* stream);
 int plast_plan_result(const plast_plan* plan, int64_t* n_records, int64_t* n_hits, void* stream);
 void plast_plan_free(plast_plan* plan);
+
+/*
+ * Fault injection for the failure paths (tests): from now on every device
+ * allocation the library makes larger than `bytes` fails as if the device
+ * were out of memory, and the call reports PLAST_E_OOM with everything it had
+ * allocated freed; 0 removes the limit.  PLAST_E_INVALID if bytes < 0.
+ * Applies to later calls in this process.
+ */
+int plast_set_alloc_limit(int64_t bytes);
 
 /*
  * Scheduling of stage 2.  0 (default): one persistent launch, CTAs pull

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
         L.plast_default_params.restype = None
         L.plast_strerror.argtypes = [ctypes.c_int]
         L.plast_strerror.restype = ctypes.c_char_p
+        L.plast_set_alloc_limit.argtypes = [i64]
+        L.plast_set_alloc_limit.restype = ctypes.c_int
         L.plast_set_schedule.argtypes = [ctypes.c_int]
         L.plast_set_schedule.restype = ctypes.c_int
         L.plast_translate6.argtypes = [P, P, i32, P, i64, P, P, pI64, P]
@@ -168,6 +170,14 @@ def plast_default_params(**overrides) -> plast_params:
     for k, v in overrides.items():
         setattr(p, k, int(v))
     return p
+
+
+def plast_set_alloc_limit(nbytes: int) -> None:
+    """Fault injection: device allocations of the library above ``nbytes``
+    fail with PLAST_E_OOM (0: no limit)."""
+    rc = lib().plast_set_alloc_limit(int(nbytes))
+    if rc:
+        raise PlastError("plast_set_alloc_limit", rc)
 
 
 def plast_set_schedule(mode: int) -> None:

@@ -15,6 +15,8 @@
 #include <string.h>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bank.cuh"
 #include "common.cuh"
 #include "gapped.cuh"
@@ -45,6 +47,32 @@ struct StageTimer {
 };
 thread_local StageTimer t_timer;
 
+// NVTX range over a scope (host timeline of the calls and their stages, for
+// profilers; header-only, inert without one).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Fault injection for the failure paths: any single device allocation of
+// the library above this many bytes fails as if the device were out of
+// memory (0: no limit).
+std::atomic<int64_t> g_alloc_limit{0};
+
+cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t st) {
+  const int64_t lim = g_alloc_limit.load(std::memory_order_relaxed);
+  if (lim > 0 && (int64_t)bytes > lim) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  const int64_t lim = g_alloc_limit.load(std::memory_order_relaxed);
+  if (lim > 0 && (int64_t)bytes > lim) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
 int rc_of(cudaError_t e) {
   if (e == cudaSuccess) return PLAST_OK;
   if (e == cudaErrorMemoryAllocation) {
@@ -73,7 +101,7 @@ struct Scratch {
     void* p = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&p, (bytes + 255) & ~(size_t)255, st);
+    cudaError_t e = dev_alloc_async(&p, (bytes + 255) & ~(size_t)255, st);
     if (e != cudaSuccess) return e;
     ptrs.push_back(p);
     *out = (T*)p;
@@ -425,6 +453,7 @@ struct Survivors {
 // when `sort`, else in the order the kernel wrote them.
 int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, cudaStream_t st, Scratch& sc,
                  Survivors* sv, const std::vector<char>* key_mask = nullptr, bool sort = true) {
+  NvtxRange nvtx_("stage 2: tiles, ungapped kernels, survivors");
   sv->n = 0;
   sv->sh = b2->pad_bits;
   TileList tl;
@@ -569,6 +598,12 @@ int plast_stage_times(double* ms, int n) {
 
 long long plast_kernel_launches(void) { return plast::launch_total(); }
 
+int plast_set_alloc_limit(int64_t bytes) {
+  if (bytes < 0) return PLAST_E_INVALID;
+  g_alloc_limit.store(bytes);
+  return PLAST_OK;
+}
+
 int plast_set_schedule(int mode) {
   if (mode != 0 && mode != 1) return PLAST_E_INVALID;
   g_schedule.store(mode);
@@ -606,6 +641,7 @@ int64_t plast_pair_count(const plast_bank* b1, const plast_bank* b2) {
 
 int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs, const plast_params* params,
                      void* stream, plast_bank** out) {
+  NvtxRange nvtx_("plast_index_bank (stage 0)");
   if (!out || !seq_off || n_seqs < 0 || !params_ok(params)) return PLAST_E_INVALID;
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
@@ -643,15 +679,15 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     int64_t* d_seq_off;
     if ((rc = ck(sc.get(&d_bad, 1)))) return fail(rc);
     if ((rc = ck(cudaMemsetAsync(d_bad, 0, sizeof(int), st)))) return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->pad_alloc, (size_t)(n_pad + 2 * PAD_SLACK), st)))) return fail(rc);
+    if ((rc = ck(dev_alloc_async((void**)&b->pad_alloc, (size_t)(n_pad + 2 * PAD_SLACK), st)))) return fail(rc);
     b->pad = b->pad_alloc + PAD_SLACK;
     if ((rc = ck(cudaMemsetAsync(b->pad_alloc, SENTINEL, (size_t)(n_pad + 2 * PAD_SLACK), st)))) return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->pad_off, ((size_t)n_seqs + 1) * sizeof(int64_t), st)))) return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->key_off, (NKEYS + 1) * sizeof(int64_t), st)))) return fail(rc);
+    if ((rc = ck(dev_alloc_async((void**)&b->pad_off, ((size_t)n_seqs + 1) * sizeof(int64_t), st)))) return fail(rc);
+    if ((rc = ck(dev_alloc_async((void**)&b->key_off, (NKEYS + 1) * sizeof(int64_t), st)))) return fail(rc);
     if ((rc = ck(cudaMemcpyAsync(b->pad_off, b->h_pad_off.data(), b->h_pad_off.size() * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st))))
       return fail(rc);
-    if ((rc = ck(cudaMallocAsync((void**)&b->blk_seq, ((size_t)(n_pad / SEQ_BLK) + 1) * sizeof(int32_t), st))))
+    if ((rc = ck(dev_alloc_async((void**)&b->blk_seq, ((size_t)(n_pad / SEQ_BLK) + 1) * sizeof(int32_t), st))))
       return fail(rc);
     if ((rc = ck(launch_block_seq(b->pad_off, n_seqs, n_pad, b->blk_seq, st)))) return fail(rc);
     if ((rc = ck(sc.get(&d_seq_off, (size_t)n_seqs + 1)))) return fail(rc);
@@ -678,7 +714,7 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
     if (h_bad) return fail(PLAST_E_INVALID);
     b->n_idx = n_idx;
-    if ((rc = ck(cudaMallocAsync((void**)&b->pos, (size_t)std::max<int64_t>(n_idx, 1) * sizeof(uint32_t), st))))
+    if ((rc = ck(dev_alloc_async((void**)&b->pos, (size_t)std::max<int64_t>(n_idx, 1) * sizeof(uint32_t), st))))
       return fail(rc);
     int64_t* d_offT;
     if ((rc = ck(sc.get(&d_offT, n_cells)))) return fail(rc);
@@ -692,7 +728,7 @@ int plast_index_bank(const int8_t* codes, const int64_t* seq_off, int32_t n_seqs
     if ((rc = ck(cudaStreamSynchronize(st)))) return fail(rc);
     // the windows are laid out while the caller goes on (later calls wait on
     // b->ready)
-    if ((rc = ck(cudaMallocAsync((void**)&b->nb, (size_t)std::max<int64_t>(n_idx, 1) * WIN, st)))) return fail(rc);
+    if ((rc = ck(dev_alloc_async((void**)&b->nb, (size_t)std::max<int64_t>(n_idx, 1) * WIN, st)))) return fail(rc);
     if ((rc = ck(launch_neighbourhoods(b->pad, b->pos, n_idx, b->nb, st)))) return fail(rc);
     if ((rc = ck(cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming)))) return fail(rc);
     if ((rc = ck(cudaEventRecord(b->ready, st)))) return fail(rc);
@@ -736,6 +772,7 @@ int plast_ungapped_keys(const plast_bank* b1, const plast_bank* b2, const plast_
 
 static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
                          const std::vector<char>* mask, plast_hit* out, int64_t cap, int64_t* n_out, void* stream) {
+  NvtxRange nvtx_("plast_ungapped (stages 1-2)");
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
@@ -808,6 +845,7 @@ int run_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params& p
 // in canonical order.
 int run_gapped_search(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, const Survivors& sv,
                       plast_gapped* out, int64_t cap, int64_t* n_out, cudaStream_t st, Scratch& sc) {
+  NvtxRange nvtx_("stage 3.1 and the record sort");
   *n_out = 0;
   const int64_t n = sv.n;
   if (n == 0) return PLAST_OK;
@@ -862,6 +900,7 @@ int run_gapped_search(const plast_bank* b1, const plast_bank* b2, const plast_pa
 
 int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const plast_hit* in,
                        int64_t n_in, plast_gapped* out, int64_t cap, int64_t* n_out, void* stream) {
+  NvtxRange nvtx_("plast_small_gapped (stage 3.1)");
   if (!b1 || !b2 || !n_out || n_in < 0 || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
   if (n_in > 0 && !in) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
@@ -893,6 +932,7 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
 static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
                        int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
                        void* stream) {
+  NvtxRange nvtx_("plast_search");
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
   std::vector<char> mask;
   if (keys) {
@@ -936,6 +976,7 @@ int plast_search_keys(const plast_bank* b1, const plast_bank* b2, const plast_pa
 int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,
                      int64_t aa_cap, int64_t* seq_off_out, int32_t* frame_meta_out, int64_t* n_aa_out,
                      void* stream) {
+  NvtxRange nvtx_("plast_translate6");
   if (!contig_off || n_contigs < 0 || !n_aa_out) return PLAST_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   *n_aa_out = 0;
@@ -1065,7 +1106,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   build_tiles(b1, b2, true, &tl);
   p->n_tiles = (int64_t)tl.tiles.size();
   cudaError_t e;
-  auto alloc = [&](void** q, size_t bytes) { return cudaMalloc(q, bytes < 16 ? 16 : bytes); };
+  auto alloc = [&](void** q, size_t bytes) { return dev_alloc(q, bytes < 16 ? 16 : bytes); };
   p->rtb = radix_tmp_bytes(max_records);
   if ((e = alloc((void**)&p->tiles, sizeof(int4) * (size_t)std::max<int64_t>(p->n_tiles, 1))) ||
       (e = alloc((void**)&p->counter, 2 * sizeof(int32_t))) ||
@@ -1099,6 +1140,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
 }
 
 int plast_plan_run(plast_plan* p, void* stream) {
+  NvtxRange nvtx_("plast_plan_run");
   if (!p) return PLAST_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemsetAsync(p->counter, 0, 2 * sizeof(int32_t), st));

@@ -62,6 +62,15 @@ def test_host_only_entry_points(lib):
     B.plast_set_tile_costs(c)
 
 
+def test_alloc_limit_setter(lib):
+    from paper_0804_3643_gb300 import binding as B
+
+    with pytest.raises(B.PlastError):
+        B.plast_set_alloc_limit(-1)
+    B.plast_set_alloc_limit(1 << 20)
+    B.plast_set_alloc_limit(0)
+
+
 def test_record_layouts_match_header():
     from paper_0804_3643_gb300 import binding as B
 

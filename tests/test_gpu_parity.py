@@ -257,6 +257,30 @@ def test_errors(B):
     assert e.value.code == B.PLAST_E_INVALID
 
 
+def test_allocation_failure_injection(B, plain):
+    # host-side fault injection: allocations above the limit fail as out of
+    # memory; every call reports PLAST_E_OOM, frees what it took, and the
+    # library works again once the limit is lifted
+    g1, o1, g2, o2 = plain
+    want, n_want = B.plast_search(g1, g2)
+    b1, _ = synth.workload("plastp_plain", seed=1)
+    d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
+    try:
+        B.plast_set_alloc_limit(4096)
+        for call in (lambda: B.plast_search(g1, g2), lambda: B.plast_ungapped(g1, g2),
+                     lambda: B.plast_index_bank(d1.codes, d1.seq_off),
+                     lambda: B.Plan(g1, g2, max_hits=10 ** 6, max_records=10 ** 5)):
+            with pytest.raises(B.PlastError) as e:
+                call()
+            assert e.value.code == B.PLAST_E_OOM
+    finally:
+        B.plast_set_alloc_limit(0)
+    got, n_got = B.plast_search(g1, g2)
+    assert n_got == n_want and torch.equal(got, want)
+    g3 = B.plast_index_bank(d1.codes, d1.seq_off)
+    check_index(B, g3, o1)
+
+
 def test_bank_built_on_another_stream(B):
     # the index call returns while its last kernel may still run on its
     # stream; a search on another stream must wait for it, and a free right
