@@ -438,17 +438,6 @@ cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int
   return cudaGetLastError();
 }
 
-__global__ void k_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev) {
-  const int64_t c = *total;
-  *n_dev = c > cap ? cap : (c < 0 ? 0 : c);
-}
-
-cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev, cudaStream_t st) {
-  note_launch();
-  k_clamp_total<<<1, 1, 0, st>>>(total, cap, n_dev);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_write_sorted(const GapArgs& a, const uint64_t* skey, const uint32_t* sidx, int64_t m,
                                 const int64_t* m_dev, const SeqMap& s1, const SeqMap& s2, plast_gapped* out,
                                 cudaStream_t st) {

@@ -54,7 +54,6 @@ cudaError_t launch_gapped_compact(const GapArgs& a, const int64_t* at, const Seq
                                   plast_gapped* out, cudaStream_t st);
 // *n_dev = min(*count, cap): the hit count a planned chain feeds forward.
 cudaError_t launch_clamp_count(const unsigned long long* count, int64_t cap, int64_t* n_dev, cudaStream_t st);
-cudaError_t launch_clamp_total(const int64_t* total, int64_t cap, int64_t* n_dev, cudaStream_t st);
 // Record sort of a search: the passing hits' keys and indexes compacted,
 // then (after sorting the pairs by key) the records written in key order.
 cudaError_t launch_compact_pass(const GapArgs& a, cudaStream_t st);
