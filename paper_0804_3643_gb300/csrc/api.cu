@@ -841,7 +841,7 @@ int run_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params& p
 }
 
 // Stage 3.1 of a search: the survivors in any order; the passing ones are
-// gathered, sorted by key (fewer than the survivors) and written as records
+// compacted, sorted by key (fewer than the survivors) and written as records
 // in canonical order.
 int run_gapped_search(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, const Survivors& sv,
                       plast_gapped* out, int64_t cap, int64_t* n_out, cudaStream_t st, Scratch& sc) {
