@@ -32,18 +32,21 @@
 //    window (32 per warp) against the R rows: the profile holds one word per
 //    (k, b) and 4 rows (two planes for R = 8), or one halfword per (k, b) and
 //    2 rows; the 22 entries of a cell lie in distinct banks, so 32 lanes with
-//    any residues read them in one wavefront.  It serves short lists (a small
-//    query bank against a large one, the remainder of a long list), where a
-//    wide tile would mostly score padding rows.
+//    any residues read them in one wavefront.  8-row tiles take the lanes'
+//    windows through shared memory; 4- and 2-row tiles, which do too little
+//    arithmetic per cell to hide a shared byte load, keep each lane's window
+//    in registers.  Narrow tiles serve short lists (a small query bank
+//    against a large one, the remainder of a long list), where a wide tile
+//    would mostly score padding rows.
 // The host picks the shape per key from measured per-cell and per-tile costs.
 //
 // Pipe balance on sm_103: byte and vector loads go to the LSU, IMAD and
 // __vadd2 to the FMA pipe, prmt and the 3-input maxima to the ALU pipe, which
 // is the bound.
 //
-// Hits (score >= s1) are staged in a per-warp shared buffer and flushed with
-// one global atomic per 64 records, as (padded pos1 << sh | padded pos2,
-// score).  Tiles come from a device counter (persistent launches, costliest
+// Hits (score >= s1) are staged in a per-warp shared buffer of 32 records
+// and flushed with one global atomic per buffer, as (padded pos1 << sh |
+// padded pos2, score).  Tiles come from a device counter (persistent launches, costliest
 // tile first) or, in the plain schedule, one launch per key and shape.
 #include <atomic>
 
