@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the hot path: one step = stage 0 indexing of both banks,
-stages 1-2 (ungapped extension of every pair of every shared key), survivor
-sort and stage 3.1 (small gapped extension), on the 10,000 x 100,000
-synthetic protein workload, through the C ABI.
+stages 1-2 (ungapped extension of every pair of every shared key), stage
+3.1 (small gapped extension of the survivors) and the sort of the passing
+records, on the 10,000 x 100,000 synthetic protein workload, through the C
+ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
