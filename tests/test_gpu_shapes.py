@@ -1,7 +1,8 @@
 """Stage-2 tile shapes: wide-only, narrow-only (8, 4, 2 rows) and by-cost work lists give the
 oracle's hits and records bit for bit (shapes change the schedule, never the
 results), on the plain workload, a small query bank against a large bank
-(ragged narrow tiles), the low-complexity mix and the every-pair-passes case
+(ragged narrow tiles), a two-protein query whose wide tiles are cut along
+their bank-2 lists, the low-complexity mix and the every-pair-passes case
 (per-warp buffer overflow in narrow tiles); the calibration returns usable
 costs."""
 import numpy as np
@@ -86,6 +87,33 @@ def test_small_query_large_bank(B):
     want_sw = oracle.ungapped(ob, oq, threads=16)
     for h in each_shape(B, lambda: B.hits_numpy(B.plast_ungapped(gb, gq))):
         assert same(h, want_sw)
+
+
+def test_wide_tiles_cut(B):
+    # a two-protein query against a large bank: a few hundred keys, fewer
+    # tiles than CTAs; with the shape forced wide the costliest wide tiles
+    # are cut along their bank-2 lists into pieces of whole 128-window passes
+    rng = np.random.default_rng(21)
+    bank = synth.protein_bank(rng, 12000)
+    c, o = bank_from([synth.mutate(rng, bank.seq(int(rng.integers(0, bank.n_seqs))), 0.6) for _ in range(2)])
+    gq, oq = both(B, c, o)
+    gb, ob = both(B, bank.codes, bank.seq_off)
+    n_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    try:
+        B.plast_set_tile_shape(1)
+        whole = B.plast_stage2_tiles(oq.idx.key_off, ob.idx.key_off)
+        cut = B.plast_stage2_tiles(oq.idx.key_off, ob.idx.key_off, n_sms=n_sms)
+    finally:
+        B.plast_set_tile_shape(0)
+    assert (whole[:, 3] == 0).all() and (cut[:, 3] == 0).all() and len(cut) > len(whole)
+    assert ((cut[:, 5] - cut[:, 4]) % 128 != 0).any()   # ragged last pieces
+    want_h = oracle.ungapped(oq, ob, threads=16)
+    want = oracle.small_gapped(oq, ob, want_h)
+    assert len(want_h) > 100
+    for h in each_shape(B, lambda: B.hits_numpy(B.plast_ungapped(gq, gb))):
+        assert same(h, want_h)
+    for r, n in each_shape(B, lambda: B.plast_search(gq, gb)):
+        assert n == len(want_h) and same(B.gapped_numpy(r), want)
 
 
 def test_shapes_low_complexity(B):
