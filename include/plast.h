@@ -24,6 +24,12 @@
  *   0 1 2 3.  Any other code is PLAST_E_INVALID.
  * - Positions in records are 0-based and local to their sequence; seq1 /
  *   seq2 index the sequences of bank 1 / bank 2.
+ * - Calls may come from several host threads at once, each on its own
+ *   stream: a call's scratch and stage timers are its own, and a bank is
+ *   only read once plast_index_bank has returned (it must outlive the calls
+ *   that use it).  Exceptions: plast_small_gapped_noalloc (one static array
+ *   per device) and the plast_set_* switches, which are process-wide and
+ *   apply to the calls that start after them in every thread.
  */
 #ifndef PLAST_H
 #define PLAST_H
@@ -343,9 +349,10 @@ int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t
 /*
  * Instrumentation (no effect on results).
  * plast_set_timing(1) makes later plast_ungapped / plast_small_gapped /
- * plast_search calls of the calling thread record CUDA events on their stream
+ * plast_search calls (of every thread) record CUDA events on their stream
  * at the stage boundaries; plast_stage_times then fills ms[0 .. n) with the
- * device time of the last call's intervals (-1 where not recorded):
+ * device time of the intervals of the calling thread's last such call (-1
+ * where not recorded):
  *   ms[0] work list upload   ms[1] stage-2 kernel   ms[2] survivor count read
  *   (and, for plast_ungapped, the survivor sort)   ms[3] stage-3.1 kernel
  *   ms[4] threshold scan, record sort (plast_search) and write-out.

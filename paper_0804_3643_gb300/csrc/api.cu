@@ -137,14 +137,17 @@ int bits_for(int64_t v) {
 }
 
 int num_sms() {
-  static int sms[64] = {0};
+  static std::atomic<int> sms[64];  // per device, 0 until first asked (calls may come from several threads)
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && sms[dev]) return sms[dev];
+  if (dev >= 0 && dev < 64) {
+    const int v = sms[dev].load(std::memory_order_relaxed);
+    if (v) return v;
+  }
   int n = 0;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   if (n <= 0) n = 1;
-  if (dev < 64) sms[dev] = n;
+  if (dev >= 0 && dev < 64) sms[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 

@@ -45,6 +45,8 @@
 // ends.  Columns j < 0 start at -16000 and stay far below zero.  Columns
 // j > LG (rows i > LG - BAND) lie outside the grid; they feed no cell of the
 // grid and are kept out of the maximum (compile-time column limits).
+#include <atomic>
+
 #include "gapped.cuh"
 
 #include "common.cuh"
@@ -360,7 +362,7 @@ cudaError_t launch_compact_pass(const GapArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_small_gapped(const GapArgs& a, cudaStream_t st) {
-  static bool attr_set[64] = {false};
+  static std::atomic<bool> attr_set[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {

@@ -11,6 +11,7 @@
 //            rightwards, then the 22 residues left of it walking leftwards
 //            (Section 3.3.2's neighbourhood blocks, built once per bank).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "gapped.cuh"
@@ -364,7 +365,7 @@ __global__ void k_translate6(const uint8_t* dna, const int64_t* contig_off, int3
 }
 
 cudaError_t upload_code_letters_once() {
-  static bool done[64] = {false};
+  static std::atomic<bool> done[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && done[dev]) return cudaSuccess;
@@ -421,7 +422,7 @@ cudaError_t launch_index_finish(const int8_t* pad, int64_t n_pad, int64_t tile, 
                                 cudaStream_t st) {
   // one-warp CTAs with 35 KB of shared memory each: ask for the largest
   // shared-memory carveout so that six of them share an SM
-  static bool carveout_set[64] = {false};
+  static std::atomic<bool> carveout_set[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !carveout_set[dev]) {

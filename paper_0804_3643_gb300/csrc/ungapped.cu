@@ -734,7 +734,7 @@ constexpr int UNG_DEFAULT_VARIANT = 1;
 
 template <int N16>
 cudaError_t launch_variant(const UngArgs& a, int grid, cudaStream_t st) {
-  static bool attr_set[64] = {false};
+  static std::atomic<bool> attr_set[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
@@ -760,7 +760,7 @@ int ungapped_variant_n16(int v) { return v >= 0 && v < UNG_VARIANTS ? UNG_N16[v]
 void set_ungapped_variant(int v) { g_variant.store(v); }
 
 cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st) {
-  static bool attr_set[64] = {false};
+  static std::atomic<bool> attr_set[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
