@@ -219,7 +219,7 @@ def committed_traffic():
 def setup_tiles(args, B) -> dict:
     """Stage-2 tile shape policy and its cost constants (measured on this
     device by the library's calibration unless --no-autotune)."""
-    B.plast_set_tile_shape({"auto": 0, "wide": 1, "narrow": 2, "narrow4": 3, "narrow2": 4}[args.tile_shape])
+    B.plast_set_tile_shape({"auto": 0, "wide": 1, "narrow": 2, "narrow4": 3, "narrow2": 4, "narrow16": 5}[args.tile_shape])
     if args.no_autotune:
         c = dict(B.plast_get_tile_costs(), source="defaults")
     else:
@@ -662,7 +662,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-threads", type=int, default=None, help="oracle threads (default: every host core)")
-    ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow", "narrow4", "narrow2"],
+    ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow", "narrow4", "narrow2", "narrow16"],
                     help="stage-2 tile shapes: by measured cost (default) or forced")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile costs")
     ap.add_argument("--wide-int16-cells", type=int, default=None, choices=[0, 12, 14, 16],

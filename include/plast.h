@@ -299,12 +299,13 @@ int plast_set_schedule(int mode);
 /*
  * Stage-2 tile shapes.  The work of a key is cut into tiles of consecutive
  * bank-1 occurrences: wide tiles of 128 rows, whose profile serves 4 bank-2
- * windows per warp, and narrow tiles of 8, 4 or 2 rows, one bank-2 window
- * per lane, for short lists (a small query bank against a large one, the end
- * of a long list).  After the full wide tiles of a key, the library covers
- * the remainder either with one wide tile or with narrow tiles (8 rows while
- * 8 or more remain, the last 1-7 rows by the cheapest cover with 8, 4 and 2
- * rows), from a cost model: a tile of shape S costs
+ * windows per warp, and narrow tiles of 16, 8, 4 or 2 rows, one bank-2
+ * window per lane, for short lists (a small query bank against a large one,
+ * the end of a long list).  After the full wide tiles of a key, the library
+ * covers the remainder either with one wide tile or with narrow tiles (16
+ * rows while 16 or more remain, or 8 if those cost less per row, the last
+ * rows by the cheapest cover with 16, 8, 4 and 2 rows), from a cost model: a
+ * tile of shape S costs
  * S_slot x (rows of S) x ceil(n2 / P_S) x P_S + S_tile SM-nanoseconds, n2 the
  * key's bank-2 occurrences, P_S the bank-2 windows a CTA scores per pass
  * (128 wide, 512 narrow).  plast_autotune measures the constants on the
@@ -317,7 +318,7 @@ int plast_set_schedule(int mode);
  * variant (for a cached calibration; PLAST_E_INVALID unless the slot costs
  * are positive, the tile costs non-negative and wide_int16_cells one of the
  * variants).  plast_set_tile_shape forces the shape of every tile (1 wide;
- * 2, 3, 4 narrow of 8, 4, 2 rows; 0, the default, by cost).  Shapes change
+ * 2, 3, 4, 5 narrow of 8, 4, 2, 16 rows; 0, the default, by cost).  Shapes change
  * the schedule, never the results.  Settings are process-wide and apply to
  * later calls.
  */
@@ -328,6 +329,7 @@ typedef struct plast_tile_costs {
   double narrow2_slot, narrow2_tile; /* 2 rows */
   int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14 or 16) */
   int32_t reserved;         /* 0 */
+  double narrow16_slot, narrow16_tile; /* 16 rows */
 } plast_tile_costs;
 int plast_autotune(void* stream, plast_tile_costs* out);
 int plast_get_tile_costs(plast_tile_costs* out);
@@ -338,8 +340,8 @@ int plast_set_tile_shape(int mode);
  * CSR key offsets (host arrays of PLAST_NKEYS + 1 entries each, as
  * plast_bank_export_index returns) on a GPU of n_sms SMs (0: no splitting of
  * long lists): host-only, no device needed.  Fills tiles[6 * t ..] with (key,
- * first bank-1 CSR index, rows, shape: 0 wide, 1, 2, 3 narrow of 8, 4, 2
- * rows, first and end offset of its bank-2 windows in the key's list) in
+ * first bank-1 CSR index, rows, shape: 0 wide, 1, 2, 3, 4 narrow of 8, 4, 2,
+ * 16 rows, first and end offset of its bank-2 windows in the key's list) in
  * launch order for t < *n_tiles; PLAST_E_CAPACITY if more than `cap` tiles
  * (then *n_tiles = needed), PLAST_E_INVALID on decreasing offsets.
  */

@@ -47,12 +47,13 @@ class plast_params(ctypes.Structure):
 
 
 COST_FIELDS = ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile", "narrow4_slot", "narrow4_tile",
-               "narrow2_slot", "narrow2_tile")
+               "narrow2_slot", "narrow2_tile", "narrow16_slot", "narrow16_tile")
 
 
 class plast_tile_costs(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in COST_FIELDS] + \
-        [("wide_int16_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [(n, ctypes.c_double) for n in COST_FIELDS[:8]] + \
+        [("wide_int16_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+        [(n, ctypes.c_double) for n in COST_FIELDS[8:]]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
@@ -228,8 +229,8 @@ def plast_set_tile_costs(costs: dict) -> None:
 
 
 def plast_set_tile_shape(mode: int) -> None:
-    """0: by cost (default), 1: every tile wide, 2 / 3 / 4: every tile narrow
-    of 8 / 4 / 2 rows."""
+    """0: by cost (default), 1: every tile wide, 2 / 3 / 4 / 5: every tile
+    narrow of 8 / 4 / 2 / 16 rows."""
     rc = lib().plast_set_tile_shape(int(mode))
     if rc:
         raise PlastError("plast_set_tile_shape", rc)

@@ -158,8 +158,8 @@ int num_sms() {
 // rounded up to that granularity.  Defaults from a GB300; plast_autotune
 // measures them on the current device.
 std::mutex g_cost_mu;
-plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1090.0, 12, 0};
-// 0: by cost; 1: wide only; 2, 3, 4: narrow tiles of 8, 4, 2 rows only
+plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1090.0, 12, 0, 0.416, 314.0};
+// 0: by cost; 1: wide only; 2, 3, 4, 5: narrow tiles of 8, 4, 2, 16 rows only
 std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
 constexpr int64_t NARROW_PASS = UNG_NARROW_PASS;           // narrow tiles
@@ -174,6 +174,8 @@ int shape_rows(int shape) {
       return UNG_NT1;
     case UNG_NARROW4:
       return UNG_NT1 / 2;
+    case UNG_NARROW16:
+      return 2 * UNG_NT1;
     default:
       return UNG_NT1 / 4;
   }
@@ -192,6 +194,8 @@ double tile_cost(const plast_tile_costs& c, int shape, int64_t n2) {
       return c.narrow_slot * slots + c.narrow_tile;
     case UNG_NARROW4:
       return c.narrow4_slot * slots + c.narrow4_tile;
+    case UNG_NARROW16:
+      return c.narrow16_slot * slots + c.narrow16_tile;
     default:
       return c.narrow2_slot * slots + c.narrow2_tile;
   }
@@ -200,9 +204,9 @@ double tile_cost(const plast_tile_costs& c, int shape, int64_t n2) {
 // Stage-2 work list: for every key present in both banks, tiles of
 // consecutive bank-1 occurrences.  Full wide tiles of UNG_T1 rows; the
 // remainder (or a short list) goes to one wide tile or to narrow tiles,
-// whichever the cost model says is cheaper: narrow tiles of 8 rows while 8
-// or more rows remain, the last 1-7 rows by the cheapest cover with tiles of
-// 8, 4 and 2 rows.
+// whichever the cost model says is cheaper: narrow tiles of 16 rows while 16
+// or more rows remain (of 8 if those cost less per row), the last rows by the
+// cheapest cover with tiles of 16, 8, 4 and 2 rows.
 struct TileList {
   std::vector<int4> tiles;        // (key, first CSR index of bank 1, rows, shape)
   int64_t n_wide = 0;             // persistent order: the wide tiles come first
@@ -298,23 +302,31 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     for (const int k : keys) sorted[count[bucket(k)]++] = k;
     keys.swap(sorted);
   }
-  // wide tiles, then narrow tiles of 8, 4 and 2 rows, each in key order
+  // wide tiles, then narrow tiles of 16, 8, 4 and 2 rows, each in key order
   // (narrow tiles with their cost, for the merge)
   int64_t rows_total = 0;
   for (const int k : keys) rows_total += ko1[k + 1] - ko1[k];
   std::vector<int4> wide;
-  std::vector<std::pair<float, int4>> by_shape[4];
+  std::vector<std::pair<float, int4>> by_shape[UNG_SHAPES];
   std::vector<int4>* out = largest_first ? nullptr : &tl->tiles;  // plain schedule: key by key
   if (out) {
     out->reserve((size_t)(rows_total / UNG_T1 + 4 * keys.size()));
   } else {
     wide.reserve((size_t)(rows_total / UNG_T1 + keys.size()));
-    by_shape[UNG_NARROW].reserve((size_t)(std::min<int64_t>(rows_total / UNG_NT1, 16 * (int64_t)keys.size()) + 16));
+    by_shape[UNG_NARROW16].reserve((size_t)(std::min<int64_t>(rows_total / 16, 8 * (int64_t)keys.size()) + 16));
+    by_shape[UNG_NARROW].reserve(keys.size());
     by_shape[UNG_NARROW4].reserve(keys.size());
     by_shape[UNG_NARROW2].reserve(keys.size());
   }
-  double cost_now[4] = {0, 0, 0, 0};  // tile costs of the current key's n2
+  double cost_now[UNG_SHAPES] = {};  // tile costs of the current key's n2
   int32_t n2_now = 0;
+  // cheapest cover of the last t < 16 rows of a key by narrow tiles (a tile
+  // may hold fewer rows than its shape); the costs, hence the cover, depend
+  // on n2 only through its pass count, so it is kept while that repeats
+  constexpr int TAIL = 16;
+  double best[TAIL];
+  int pick[TAIL];
+  int64_t cover_passes = -1;
   auto emit = [&](int k, int64_t first, int64_t rows, int shape) {
     const int4 t = make_tile(k, (int)first, (int)rows, shape, 0, n2_now);
     if (out) out->push_back(t);
@@ -326,7 +338,7 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     const int64_t n2 = ko2[k + 1] - ko2[k];
     tl->pairs += n1 * n2;
     n2_now = (int32_t)n2;
-    for (int shape = UNG_NARROW; shape <= UNG_NARROW2; shape++) cost_now[shape] = tile_cost(c, shape, n2);
+    for (int shape = UNG_NARROW; shape < UNG_SHAPES; shape++) cost_now[shape] = tile_cost(c, shape, n2);
     int64_t u = ko1[k];
     const int64_t end = ko1[k + 1];
     if (mode >= 2) {  // one narrow shape only
@@ -341,27 +353,31 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
       emit(k, u, rem, UNG_WIDE);
       continue;
     }
-    // cheapest cover of the last t rows (t < 8) by narrow tiles of 8, 4, 2
-    const double c8 = cost_now[UNG_NARROW], c4 = cost_now[UNG_NARROW4], c2 = cost_now[UNG_NARROW2];
-    double best[UNG_NT1];
-    int pick[UNG_NT1];
-    best[0] = 0;
-    pick[0] = 0;
-    for (int t = 1; t < UNG_NT1; t++) {
-      best[t] = c8;
-      pick[t] = UNG_NARROW;
-      const double v4 = c4 + best[std::max(t - 4, 0)], v2 = c2 + best[std::max(t - 2, 0)];
-      if (v4 < best[t]) best[t] = v4, pick[t] = UNG_NARROW4;
-      if (v2 < best[t]) best[t] = v2, pick[t] = UNG_NARROW2;
+    if (round_up(n2, NARROW_PASS) != cover_passes) {
+      cover_passes = round_up(n2, NARROW_PASS);
+      best[0] = 0;
+      pick[0] = 0;
+      for (int t = 1; t < TAIL; t++) {
+        best[t] = 0;
+        pick[t] = -1;
+        for (const int shape : {UNG_NARROW16, UNG_NARROW, UNG_NARROW4, UNG_NARROW2}) {
+          const double v = cost_now[shape] + best[std::max(t - shape_rows(shape), 0)];
+          if (pick[t] < 0 || v < best[t]) best[t] = v, pick[t] = shape;
+        }
+      }
     }
-    const int64_t full8 = rem / UNG_NT1;
-    const int tail = (int)(rem % UNG_NT1);
-    const double narrow_cost = (double)full8 * c8 + best[tail];
+    // full tiles of 16 rows (or of 8 where those cost less per row), then
+    // the cheapest cover of the rest; against one wide tile for it all
+    const int bulk = cost_now[UNG_NARROW16] <= 2 * cost_now[UNG_NARROW] ? UNG_NARROW16 : UNG_NARROW;
+    const int br = shape_rows(bulk);
+    const int64_t full = rem / br;
+    const int tail = (int)(rem % br);
+    const double narrow_cost = (double)full * cost_now[bulk] + best[tail];
     if (!(narrow_cost < tile_cost(c, UNG_WIDE, n2))) {
       emit(k, u, rem, UNG_WIDE);
       continue;
     }
-    for (int64_t i = 0; i < full8; i++, u += UNG_NT1) emit(k, u, UNG_NT1, UNG_NARROW);
+    for (int64_t i = 0; i < full; i++, u += br) emit(k, u, br, bulk);
     for (int t = tail; t > 0;) {
       const int shape = pick[t], r = std::min(shape_rows(shape), t);
       emit(k, u, r, shape);
@@ -374,17 +390,17 @@ void build_tiles_from(const int64_t* ko1, const int64_t* ko2, bool largest_first
     return;
   }
   // wide tiles (one launch), then the narrow ones (another), costliest first:
-  // a three-way merge of the per-shape lists, each already in cost order
+  // a merge of the per-shape narrow lists, each already in cost order
   size_t total = wide.size();
   for (const auto& v : by_shape) total += v.size();
   tl->tiles.reserve(total);
   tl->tiles.insert(tl->tiles.end(), wide.begin(), wide.end());
   tl->n_wide = (int64_t)wide.size();
-  size_t at[4] = {0, 0, 0, 0};
+  size_t at[UNG_SHAPES] = {};
   for (;;) {
     int pickd = -1;
     float bestc = 0;
-    for (int shape = UNG_NARROW; shape <= UNG_NARROW2; shape++) {
+    for (int shape = UNG_NARROW; shape < UNG_SHAPES; shape++) {
       if (at[shape] >= by_shape[shape].size()) continue;
       const float v = by_shape[shape][at[shape]].first;
       if (pickd < 0 || v > bestc) pickd = shape, bestc = v;
@@ -1382,9 +1398,9 @@ int plast_get_tile_costs(plast_tile_costs* out) {
 
 int plast_set_tile_costs(const plast_tile_costs* c) {
   if (!c) return PLAST_E_INVALID;
-  const double slot[4] = {c->wide_slot, c->narrow_slot, c->narrow4_slot, c->narrow2_slot};
-  const double tile[4] = {c->wide_tile, c->narrow_tile, c->narrow4_tile, c->narrow2_tile};
-  for (int i = 0; i < 4; i++)
+  const double slot[UNG_SHAPES] = {c->wide_slot, c->narrow_slot, c->narrow4_slot, c->narrow2_slot, c->narrow16_slot};
+  const double tile[UNG_SHAPES] = {c->wide_tile, c->narrow_tile, c->narrow4_tile, c->narrow2_tile, c->narrow16_tile};
+  for (int i = 0; i < UNG_SHAPES; i++)
     if (!(slot[i] > 0) || !(tile[i] >= 0) || slot[i] > 1e6 || tile[i] > 1e12) return PLAST_E_INVALID;
   int variant = -1;
   for (int v = 0; v < UNG_VARIANTS; v++)
@@ -1423,7 +1439,7 @@ int plast_stage2_tiles(const int64_t* key_off1, const int64_t* key_off2, int32_t
 }
 
 int plast_set_tile_shape(int mode) {
-  if (mode < 0 || mode > 4) return PLAST_E_INVALID;
+  if (mode < 0 || mode > UNG_SHAPES) return PLAST_E_INVALID;
   g_shape.store(mode);
   return PLAST_OK;
 }
@@ -1478,6 +1494,7 @@ int plast_autotune(void* stream, plast_tile_costs* out) {
   if (rc == PLAST_OK) rc = fit(2, &c.narrow_slot, &c.narrow_tile, &t_long);
   if (rc == PLAST_OK) rc = fit(3, &c.narrow4_slot, &c.narrow4_tile, &t_long);
   if (rc == PLAST_OK) rc = fit(4, &c.narrow2_slot, &c.narrow2_tile, &t_long);
+  if (rc == PLAST_OK) rc = fit(5, &c.narrow16_slot, &c.narrow16_tile, &t_long);
   plast_bank_free(b1);
   plast_bank_free(b2l);
   plast_bank_free(b2s);

@@ -28,12 +28,12 @@
 //    - N16 of the cells are stored as int16 (two 16-byte loads, no
 //      sign extension), trading shared-memory bandwidth, which has headroom,
 //      for ALU-pipe work, which has none; the rest are int8.
-//  * narrow: up to R = 8, 4 or 2 rows.  Every lane scores its own bank-2
+//  * narrow: up to R = 16, 8, 4 or 2 rows.  Every lane scores its own bank-2
 //    window (32 per warp) against the R rows: the profile holds one word per
-//    (k, b) and 4 rows (two planes for R = 8), or one halfword per (k, b) and
-//    2 rows; the 22 entries of a cell lie in distinct banks, so 32 lanes with
-//    any residues read them in one wavefront.  8-row tiles take the lanes'
-//    windows through shared memory; 4- and 2-row tiles, which do too little
+//    (k, b) and 4 rows (R / 4 planes for R >= 8), or one halfword per (k, b)
+//    and 2 rows; the 22 entries of a cell lie in distinct banks, so 32 lanes
+//    with any residues read them in one wavefront.  16- and 8-row tiles take
+//    the lanes' windows through shared memory; 4- and 2-row tiles, which do too little
 //    arithmetic per cell to hide a shared byte load, keep each lane's window
 //    in registers.  Narrow tiles serve short lists (a small query bank
 //    against a large one, the remainder of a long list), where a wide tile
@@ -90,8 +90,9 @@ struct Wide {
 // narrow tiles (their own kernel)
 constexpr int NSTRIDE = 52;                                // staged window stride: 13 words, conflict-free bytes
 constexpr int NPLANE = WIN * NCODE * 4;                     // 4224: one plane of 4 rows
-constexpr int NPROF_BYTES = 2 * NPLANE;                     // 8448
-constexpr int NROWS_BYTES = WIN * UNG_NT1;                 // 384, cell-major
+constexpr int NR_MAX = 16;                                  // rows of the largest narrow tile
+constexpr int NPROF_BYTES = (NR_MAX / 4) * NPLANE;          // 16896
+constexpr int NROWS_BYTES = WIN * NR_MAX;                   // 768, cell-major
 constexpr int NT_THREADS = 512;                            // narrow kernel: 2 CTAs of 16 warps per SM
 constexpr int NT_WARPS = NT_THREADS / 32;
 constexpr int NSTAGE_BYTES = NT_WARPS * 32 * NSTRIDE;      // 26624: one window per lane
@@ -188,10 +189,10 @@ __device__ __forceinline__ void wide_pairs(uint32_t row, const unsigned char* pl
   }
 }
 
-// Cells K and K+1 of the lane's bank-2 window against its 2 * NW narrow rows,
-// then the following pairs (K = 0, 2, .., 46).  NW = 4: rows 0-3 the word at
-// plane + (k * NCODE + b) * 4, rows 4-7 the word NPLANE bytes further; NW = 2:
-// the word alone; NW = 1: rows 0-1 the halfword at plane + (k * NCODE + b) * 2.
+// The lane's 2 * NW narrow row scores of cell k against bank-2 residue b,
+// as NW int16x2 words.  NW >= 2: rows 4p .. 4p+3 the word at
+// plane + p * NPLANE + (k * NCODE + b) * 4, p < NW / 2; NW = 1: rows 0-1 the
+// halfword at plane + (k * NCODE + b) * 2.
 template <int NW>
 __device__ __forceinline__ void narrow_scores(const unsigned char* plane, int k, uint32_t b, uint32_t (&u)[NW]) {
   if constexpr (NW == 1) {
@@ -202,13 +203,11 @@ __device__ __forceinline__ void narrow_scores(const unsigned char* plane, int k,
     u[0] = sext_pair(h, 0);
   } else {
     const unsigned char* e = plane + (k * NCODE + b) * 4;
-    const uint32_t lo = *reinterpret_cast<const uint32_t*>(e);
-    u[0] = sext_pair(lo, 0);
-    u[1] = sext_pair(lo, 1);
-    if constexpr (NW == 4) {
-      const uint32_t hi = *reinterpret_cast<const uint32_t*>(e + NPLANE);
-      u[2] = sext_pair(hi, 0);
-      u[3] = sext_pair(hi, 1);
+#pragma unroll
+    for (int p = 0; p < NW / 2; p++) {
+      const uint32_t x = *reinterpret_cast<const uint32_t*>(e + p * NPLANE);
+      u[2 * p] = sext_pair(x, 0);
+      u[2 * p + 1] = sext_pair(x, 1);
     }
   }
 }
@@ -380,21 +379,22 @@ __device__ __forceinline__ uint32_t pack4(uint32_t src, const int8_t* tab, int b
   return x;
 }
 
-// A narrow tile of 2 * NW rows: rows cell-major (nrows[k][r], stride 8),
-// the profile (NW = 4: planes nprof[p][k][b] of rows 4p .. 4p+3; NW = 2: one
-// plane; NW = 1: halfwords of rows 0-1; cells 0-3 folded into P1, M1, P2 as
-// in the wide tiles), then every bank-2 window of the key against it, one per
-// lane.
+// A narrow tile of 2 * NW rows: rows cell-major (nrows[k][r], stride
+// NR_MAX), the profile (NW >= 2: planes nprof[p][k][b] of rows 4p .. 4p+3,
+// p < NW / 2; NW = 1: halfwords of rows 0-1; cells 0-3 folded into P1, M1,
+// P2 as in the wide tiles), then every bank-2 window of the key against it,
+// one per lane.
 template <int NW>
 __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t u0, int64_t v0, int64_t v1,
                                             uint8_t* nrows, unsigned char* nprof, const int8_t* tab,
                                             unsigned char* my_nstage, uint32_t my_nrow, uint32_t s1x2,
                                             uint64_t* my_wk, uint32_t* my_wv, int& wcnt) {
+  constexpr int NQ = NW >= 2 ? NW / 2 : 1;  // 4-row words per (cell, residue)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
-  for (int i = tid; i < NROWS_BYTES; i += NT_THREADS) {
-    const int r = i & (UNG_NT1 - 1), k = i / UNG_NT1;
-    nrows[i] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
+  for (int i = tid; i < WIN * 4 * NQ; i += NT_THREADS) {
+    const int r = i % (4 * NQ), k = i / (4 * NQ);
+    nrows[k * NR_MAX + r] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;
   }
   __syncthreads();
   // cells 4 .. 47 at their own slots; slots 0, 1, 2 hold the folded seed
@@ -402,16 +402,17 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
   for (int e = tid; e < WIN * NCODE; e += NT_THREADS) {
     const int k = e / NCODE, b = e - k * NCODE;
     if (k == 3) continue;
-    uint32_t w[2];
-    const uint2 c8 = *reinterpret_cast<const uint2*>(nrows + (k < 3 ? (k == 2 ? 2 : 1) : k) * UNG_NT1);
+    const uint4 cx = *reinterpret_cast<const uint4*>(nrows + (k < 3 ? (k == 2 ? 2 : 1) : k) * NR_MAX);
+    const uint32_t sx[4] = {cx.x, cx.y, cx.z, cx.w};
+    uint32_t w[NQ];
     if (k >= FIRST_CELL) {
-      w[0] = pack4(c8.x, tab, b);
-      w[1] = pack4(c8.y, tab, b);
-    } else {
-      const uint2 cd = *reinterpret_cast<const uint2*>(nrows + (k == 2 ? 3 : 0) * UNG_NT1);
-      const uint32_t sx[2] = {c8.x, c8.y}, sd[2] = {cd.x, cd.y};
 #pragma unroll
-      for (int q = 0; q < 2; q++) {
+      for (int q = 0; q < NQ; q++) w[q] = pack4(sx[q], tab, b);
+    } else {
+      const uint4 cd = *reinterpret_cast<const uint4*>(nrows + (k == 2 ? 3 : 0) * NR_MAX);
+      const uint32_t sd[4] = {cd.x, cd.y, cd.z, cd.w};
+#pragma unroll
+      for (int q = 0; q < NQ; q++) {
         uint32_t x = 0;
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -427,8 +428,8 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
     if constexpr (NW == 1) {
       *reinterpret_cast<uint16_t*>(nprof + e * 2) = (uint16_t)(w[0] & 0xffffu);
     } else {
-      *reinterpret_cast<uint32_t*>(nprof + e * 4) = w[0];
-      if constexpr (NW == 4) *reinterpret_cast<uint32_t*>(nprof + NPLANE + e * 4) = w[1];
+#pragma unroll
+      for (int q = 0; q < NQ; q++) *reinterpret_cast<uint32_t*>(nprof + q * NPLANE + e * 4) = w[q];
     }
   }
   __syncthreads();
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   }
 }
 
-// Narrow tiles (8, 4 or 2 rows) in their own persistent kernel, so that the
+// Narrow tiles (16, 8, 4 or 2 rows) in their own persistent kernel, so that the
 // wide kernel's registers and schedule are its own; two CTAs of 512 threads
 // per SM, so that one CTA's tile changes (profile build, barriers) overlap
 // the other's scoring.
@@ -713,7 +714,9 @@ __global__ void __launch_bounds__(NT_THREADS, 2) k_ungapped_narrow(UngArgs a) {
     const int rows = tile_rows(tile);
     const int64_t u0 = (int64_t)(uint32_t)tile.y;
     const int shape = tile_shape(tile);
-    if (shape == UNG_NARROW)
+    if (shape == UNG_NARROW16)
+      narrow_tile<8>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
+    else if (shape == UNG_NARROW)
       narrow_tile<4>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);
     else if (shape == UNG_NARROW4)
       narrow_tile<2>(a, rows, u0, v0, v1, nrows, nprof, tab, my_nstage, my_nrow, s1x2, my_wk, my_wv, wcnt);

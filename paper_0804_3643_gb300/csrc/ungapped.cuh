@@ -4,21 +4,23 @@
 
 namespace plast {
 
-// tile shapes (ungapped.cu): UNG_T1 rows (wide), UNG_NT1 = 8, 4 or 2 rows (narrow)
+// tile shapes (ungapped.cu): UNG_T1 rows (wide); 8, 4, 2 or 16 rows (narrow)
 constexpr int UNG_WIDE = 0;
 constexpr int UNG_NARROW = 1;
 constexpr int UNG_NARROW4 = 2;
 constexpr int UNG_NARROW2 = 3;
+constexpr int UNG_NARROW16 = 4;
+constexpr int UNG_SHAPES = 5;
 
-// A stage-2 tile: x = key | shape << 14 | rows << 16, y = first bank-1 CSR
+// A stage-2 tile: x = key | shape << 14 | rows << 17, y = first bank-1 CSR
 // index of its rows, [z, w) = the bank-2 windows it scores, as offsets in
 // the key's list (a long list may be cut over several tiles).
 __host__ __device__ inline int4 make_tile(int key, int first, int rows, int shape, int vlo, int vhi) {
-  return make_int4(key | (shape << 14) | (rows << 16), first, vlo, vhi);
+  return make_int4(key | (shape << 14) | (rows << 17), first, vlo, vhi);
 }
 __host__ __device__ inline int tile_key(const int4& t) { return t.x & 0x3fff; }
-__host__ __device__ inline int tile_shape(const int4& t) { return (t.x >> 14) & 3; }
-__host__ __device__ inline int tile_rows(const int4& t) { return (t.x >> 16) & 0xff; }
+__host__ __device__ inline int tile_shape(const int4& t) { return (t.x >> 14) & 7; }
+__host__ __device__ inline int tile_rows(const int4& t) { return (t.x >> 17) & 0xff; }
 
 struct UngArgs {
   const int8_t* nb1;        // bank-1 windows [n_idx1][48]
@@ -26,7 +28,7 @@ struct UngArgs {
   const int8_t* nb2;        // bank-2 windows [n_idx2][48]
   const uint32_t* pos2;     // bank-2 padded positions, CSR order
   const int64_t* key_off2;  // bank-2 CSR offsets [8801]
-  const int4* tiles;        // (key, first bank-1 CSR index, rows, shape UNG_WIDE / UNG_NARROW)
+  const int4* tiles;        // make_tile: key, first bank-1 CSR index, rows, shape, bank-2 range
   int32_t n_tiles;          // tiles handled by this launch
   int32_t tile_base;        // first tile of this launch in `tiles`
   int32_t* tile_counter;    // persistent schedule: next tile to take

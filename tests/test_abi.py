@@ -45,8 +45,9 @@ def test_host_only_entry_points(lib):
     B.plast_set_schedule(0)
     with pytest.raises(B.PlastError):
         B.plast_set_schedule(7)
+    B.plast_set_tile_shape(5)
     with pytest.raises(B.PlastError):
-        B.plast_set_tile_shape(5)
+        B.plast_set_tile_shape(6)
     B.plast_set_tile_shape(0)
     c = B.plast_get_tile_costs()
     assert c["wide_slot"] > 0 and c["narrow_slot"] > 0
@@ -76,3 +77,4 @@ def test_record_layouts_match_header():
 
     assert B.HIT_DTYPE.itemsize == 20 and B.GAPPED_DTYPE.itemsize == 28
     assert ctypes.sizeof(B.plast_params) == 40
+    assert ctypes.sizeof(B.plast_tile_costs) == 88

@@ -1,4 +1,4 @@
-"""Stage-2 tile shapes: wide-only, narrow-only (8, 4, 2 rows) and by-cost work lists give the
+"""Stage-2 tile shapes: wide-only, narrow-only (16, 8, 4, 2 rows) and by-cost work lists give the
 oracle's hits and records bit for bit (shapes change the schedule, never the
 results), on the plain workload, a small query bank against a large bank
 (ragged narrow tiles), a two-protein query whose wide tiles are cut along
@@ -41,7 +41,7 @@ def same(a, b):
 def each_shape(B, f):
     out = []
     try:
-        for shape in (1, 2, 3, 4, 0):
+        for shape in (1, 2, 3, 4, 5, 0):
             B.plast_set_tile_shape(shape)
             out.append(f())
     finally:
@@ -144,6 +144,7 @@ def test_autotune(B):
         assert c["wide_tile"] >= 0 and c["narrow_tile"] >= 0
         # a row slot of either shape costs 48 cells: between 0.01 and 10 SM-ns
         assert 0.01 < c["wide_slot"] < 10 and 0.01 < c["narrow_slot"] < 10
+        assert 0.01 < c["narrow16_slot"] < 10 and c["narrow16_tile"] >= 0
         assert B.plast_get_tile_costs() == c
     finally:
         B.plast_set_tile_costs(saved)

@@ -1,7 +1,8 @@
 """Stage-2 work list (host logic, no GPU): every bank-1 occurrence of every
 key shared by both banks lies in exactly one tile; full wide tiles first,
-the remainder one wide tile or narrow tiles (8 rows while 8 remain, the last
-1-7 rows by the cheapest cover with 8, 4 and 2) by the cost model; in the
+the remainder one wide tile or narrow tiles (16 rows while 16 remain, or 8
+where those cost less per row, the last rows by the cheapest cover with 16,
+8, 4 and 2) by the cost model; in the
 persistent schedule wide tiles (one launch) before narrow tiles (another),
 each costliest first; key order in the plain one."""
 import math
@@ -12,9 +13,10 @@ import pytest
 from paper_0804_3643_gb300 import binding as B
 
 NK = B.NKEYS
-WIDE, NARROW, NARROW4, NARROW2 = 0, 1, 2, 3
-ROWS = {WIDE: 128, NARROW: 8, NARROW4: 4, NARROW2: 2}
-T1, NT1 = 128, 8
+WIDE, NARROW, NARROW4, NARROW2, NARROW16 = 0, 1, 2, 3, 4
+ROWS = {WIDE: 128, NARROW: 8, NARROW4: 4, NARROW2: 2, NARROW16: 16}
+NAME = {WIDE: "wide", NARROW: "narrow", NARROW4: "narrow4", NARROW2: "narrow2", NARROW16: "narrow16"}
+T1 = 128
 
 
 def offsets(counts):
@@ -28,7 +30,8 @@ def costs():
     B.lib()
     saved = B.plast_get_tile_costs()
     c = dict(wide_slot=0.5, wide_tile=4000.0, narrow_slot=0.6, narrow_tile=1000.0, narrow4_slot=0.8,
-             narrow4_tile=900.0, narrow2_slot=1.1, narrow2_tile=800.0, wide_int16_cells=12)
+             narrow4_tile=900.0, narrow2_slot=1.1, narrow2_tile=800.0, narrow16_slot=0.5, narrow16_tile=1200.0,
+             wide_int16_cells=12)
     B.plast_set_tile_costs(c)
     yield c
     B.plast_set_tile_costs(saved)
@@ -37,7 +40,7 @@ def costs():
 
 
 def random_counts(rng):
-    n1 = rng.choice([0, 1, 3, 7, 8, 9, 15, 40, 100, 127, 128, 129, 255, 256, 300, 1000], size=NK)
+    n1 = rng.choice([0, 1, 3, 7, 8, 9, 15, 16, 17, 24, 40, 100, 127, 128, 129, 255, 256, 300, 1000], size=NK)
     n2 = rng.choice([0, 1, 5, 50, 500, 5000, 50000], size=NK)
     return n1.astype(np.int64), n2.astype(np.int64)
 
@@ -48,25 +51,25 @@ def round_up(n, g):
 
 def tile_cost(c, shape, n2):
     # a CTA scores 128 (wide) or 512 (narrow) bank-2 windows per pass
-    name = {WIDE: "wide", NARROW: "narrow", NARROW4: "narrow4", NARROW2: "narrow2"}[shape]
+    name = NAME[shape]
     return c[name + "_slot"] * ROWS[shape] * round_up(n2, 128 if shape == WIDE else 512) + c[name + "_tile"]
 
 
 def tail_cover(c, t, n2):
-    """Cheapest cover of t < 8 rows by narrow tiles of 8, 4, 2 rows, by brute
-    force over multisets: (cost, sorted list of shapes)."""
-    best = (0.0, [])
+    """Cost of the cheapest cover of t < 16 rows by narrow tiles of 16, 8, 4
+    and 2 rows, by brute force over multisets."""
     if t == 0:
-        return best
+        return 0.0
     best = None
-    for a in range(0, 2):          # tiles of 8
-        for b in range(0, 3):      # tiles of 4
-            for d in range(0, 5):  # tiles of 2
-                if 8 * a + 4 * b + 2 * d < t or a + b + d == 0:
-                    continue
-                cost = a * tile_cost(c, NARROW, n2) + b * tile_cost(c, NARROW4, n2) + d * tile_cost(c, NARROW2, n2)
-                if best is None or cost < best[0] - 1e-9:
-                    best = (cost, sorted([NARROW] * a + [NARROW4] * b + [NARROW2] * d))
+    for a in range(0, 2):                  # tiles of 16
+        for e in range(0, 3):              # tiles of 8
+            for b in range(0, 5):          # tiles of 4
+                for d in range(0, 9):      # tiles of 2
+                    if 16 * a + 8 * e + 4 * b + 2 * d < t or a + e + b + d == 0:
+                        continue
+                    cost = (a * tile_cost(c, NARROW16, n2) + e * tile_cost(c, NARROW, n2)
+                            + b * tile_cost(c, NARROW4, n2) + d * tile_cost(c, NARROW2, n2))
+                    best = cost if best is None else min(best, cost)
     return best
 
 
@@ -115,13 +118,16 @@ def test_cover_and_shapes_by_cost(costs):
         if rem == 0:
             assert not rest
             continue
-        tail_cost, tail_shapes = tail_cover(costs, rem % NT1, n2[k])
-        narrow_cost = (rem // NT1) * tile_cost(costs, NARROW, n2[k]) + tail_cost
+        # full tiles of 16 rows (of 8 where those cost less per row), then the
+        # cheapest cover of the rest
+        bulk = NARROW16 if tile_cost(costs, NARROW16, n2[k]) <= 2 * tile_cost(costs, NARROW, n2[k]) else NARROW
+        br = ROWS[bulk]
+        narrow_cost = (rem // br) * tile_cost(costs, bulk, n2[k]) + tail_cover(costs, rem % br, n2[k])
         if narrow_cost < tile_cost(costs, WIDE, n2[k]):
             shapes = [s_ for _, _, s_ in rest]
-            assert shapes[: rem // NT1] == [NARROW] * (rem // NT1)
-            assert all(r == NT1 for _, r, _ in rest[: rem // NT1])
-            assert sorted(shapes[rem // NT1:]) == tail_shapes
+            assert shapes[: rem // br] == [bulk] * (rem // br)
+            assert all(r == br for _, r, _ in rest[: rem // br])
+            assert all(s_ != WIDE for s_ in shapes)
             assert abs(sum(tile_cost(costs, s_, n2[k]) for s_ in shapes) - narrow_cost) < 1e-6
         else:
             assert len(rest) == 1 and rest[0][2] == WIDE and rest[0][1] == rem
@@ -137,7 +143,7 @@ def test_cover_and_shapes_by_cost(costs):
         assert (tiles[:, 3] == shape).any(), shape
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
 def test_forced_shapes(costs, shape):
     rng = np.random.default_rng(6)
     n1, n2 = random_counts(rng)
@@ -163,7 +169,7 @@ def test_plain_schedule_keeps_key_order(costs):
 def test_small_query_goes_narrow(costs):
     # a query bank with a few occurrences per key against a large bank
     n2 = np.full(NK, 40000, dtype=np.int64)
-    for n, shape in [(1, NARROW2), (2, NARROW2), (4, NARROW4), (8, NARROW)]:
+    for n, shape in [(1, NARROW2), (2, NARROW2), (4, NARROW4), (8, NARROW), (16, NARROW16)]:
         tiles = B.plast_stage2_tiles(offsets(np.full(NK, n, dtype=np.int64)), offsets(n2))
         assert (tiles[:, 3] == shape).all() and len(tiles) == NK, n
 
