@@ -41,6 +41,8 @@ from paper_0804_3643_gb300 import synth  # noqa: E402
 WORKLOAD = "plastp_full"
 CELLS_PER_PAIR = 48        # ungapped window: 26 right + 22 left cells
 CELLS_PER_CLK_SM = 128     # int16 cells per clock per SM on the ALU / FMA-heavy pipes
+BAND_CELLS_PER_HIT = 2 * 64 * 17  # stage 3.1: two sides x LG rows x (2 x band + 1) columns
+ALU_LANES_PER_CLK_SM = 64  # ALU-pipe lanes per clock per SM (every integer max issues there)
 METRIC = "ungapped pairs/s and GCUPS at 1 GB300 (bit-exact), % of int/HBM roofline"
 
 
@@ -133,11 +135,18 @@ def oracle_sample_keys(o1, o2, target_pairs: float, seed: int = 7):
 def oracle_step(oracle, o1, o2, keys, threads, prm):
     """Stages 1-2 over the sampled keys, then stage 3.1 of their hits."""
     h = oracle.ungapped(o1, o2, prm, keys=keys, threads=threads)
-    oracle.small_gapped(o1, o2, h, prm)
+    oracle.small_gapped(o1, o2, h, prm, threads=threads)
     return len(h)
 
 
-def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads: int | None = None, s0: int = 0):
+# One fixed sample of keys for both CPU arms (the cpu_baseline leg and the
+# --impl reference line): the keys drawn with this seed until they hold
+# this many pairs, so the two arms time the same work.
+SAMPLE_SEED = 7
+SAMPLE_PAIRS = 1.2e8
+
+
+def run_oracle(b1, b2, steps: int, warmup: int, threads: int | None = None, s0: int = 0):
     import oracle
 
     prm = oracle.Params(s0=s0)
@@ -146,12 +155,7 @@ def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads
     o1 = oracle.make_bank(b1.codes, b1.seq_off)
     o2 = oracle.make_bank(b2.codes, b2.seq_off)
     t_index = time.time() - t0
-    # calibrate the sample: a small probe, then scale to the time budget
-    probe_keys, probe_pairs = oracle_sample_keys(o1, o2, 2e7, seed=3)
-    t0 = time.time()
-    oracle_step(oracle, o1, o2, probe_keys, threads, prm)
-    rate = probe_pairs / max(time.time() - t0, 1e-3)
-    keys, pairs = oracle_sample_keys(o1, o2, rate * seconds_per_step)
+    keys, pairs = oracle_sample_keys(o1, o2, SAMPLE_PAIRS, seed=SAMPLE_SEED)
     for _ in range(warmup):
         oracle_step(oracle, o1, o2, keys, threads, prm)
     times = []
@@ -160,14 +164,33 @@ def run_oracle(b1, b2, seconds_per_step: float, steps: int, warmup: int, threads
         oracle_step(oracle, o1, o2, keys, threads, prm)
         times.append(time.time() - t0)
     per = sum(times) / len(times)
+    total_pairs = float((np.diff(o1.idx.key_off) * np.diff(o2.idx.key_off)).sum())
     return {
         "value": pairs / per, "unit": "pairs/s", "cores": threads, "kind": "oracle",
-        "sample": f"{len(keys)} of 8800 keys drawn at random ({pairs:.3e} of "
-                  f"{float((np.diff(o1.idx.key_off) * np.diff(o2.idx.key_off)).sum()):.3e} pairs): stages 1-2 "
-                  f"and 3.1 of those keys per step, plain C -O2 with {threads} threads; stage-0 indexing "
-                  f"of the full banks took {t_index:.2f} s once, outside the timed steps",
-        "seconds_per_step": per,
+        "sample": f"{len(keys)} of 8800 keys drawn at random (seed {SAMPLE_SEED}, until {SAMPLE_PAIRS:.2g} pairs: "
+                  f"{pairs:.4e} of {total_pairs:.4e} pairs): stages 1-2 and 3.1 of those keys per step, "
+                  f"{steps} timed steps, plain C -O2 with {threads} threads; stage-0 indexing of the full "
+                  f"banks took {t_index:.2f} s once, outside the timed steps",
+        "seconds_per_step": per, "total_pairs": int(total_pairs),
     }
+
+
+def headline_config(b1, b2, pairs: int, scale: float, bank2_proteins, s0: int, world: int) -> dict:
+    """The workload the metric is quoted on (the same dict in both arms' lines)."""
+    full = scale == 1.0 and not bank2_proteins
+    d = {
+        "workload": f"PLAST-P {'full scale' if full else 'reduced'}: {b1.n_seqs} x {b2.n_seqs} synthetic proteins "
+                    f"({len(b1.codes)} / {len(b2.codes)} residues), 5% planted homologs, seed 1",
+        "step": "index both banks + ungapped all pairs + small gapped + sort of the records"
+                + (f" (Section 4.2 filter on, S0 = {s0}: lossy, fewer hits)" if s0 else ""),
+        "pairs_per_step": int(pairs),
+        "params": {"w": 4, "nl": 22, "nr": 22, "s1": 38, "lg": 64, "band": 8, "gap_open": 11, "gap_extend": 1,
+                   "s2": 47, "s0": s0},
+        "l2": "inputs larger than L2 (129 MB): 1.7 GB of neighbourhood arrays rebuilt and read every step, "
+              "no explicit flush",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+    return d
 
 
 # --------------------------------------------------------------------------
@@ -216,6 +239,35 @@ def committed_traffic():
     return t
 
 
+def stage31_roofline(hits: int, ms: float, n_sm: int, sm_max: float, sm_mhz) -> dict:
+    """Stage 3.1 against the integer ALU peak.  Unit: one band cell of the
+    small gapped extension (2 sides x 64 rows x 17 columns per stage-2
+    survivor, the cells off the grid included).  Per cell the affine
+    recurrence takes its maxima on the ALU pipe, two cells (two hits) per
+    int16x2 instruction; the peak counts three fused add-max instructions per
+    cell pair (the E, F and H updates), 64 lanes x 2 / 3 = 42.7 cells per clock
+    per SM.  The kernel issues four per cell pair, the fewest this instruction
+    set allows (H takes the maximum of three terms one of which needs an add of
+    a table value), so `frac_of_4op_floor` rates it against 32 cells per clock
+    per SM as well."""
+    cells = hits * BAND_CELLS_PER_HIT
+    achieved = cells / (ms / 1e3)
+    per_clk = ALU_LANES_PER_CLK_SM * 2 / 3
+    peak = n_sm * per_clk * sm_max * 1e6
+    floor4 = n_sm * ALU_LANES_PER_CLK_SM * 2 / 4 * sm_max * 1e6
+    return {
+        "bound": "alu",
+        "kernel": "stage 3.1: k_small_gapped (every survivor, scores) then k_gapped_ends (passing survivors, "
+                  "end cells), timed together",
+        "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tcell/s", "frac": achieved / peak,
+        "traffic": None, "cells_per_hit": BAND_CELLS_PER_HIT, "kernel_ms": ms,
+        "peak_basis": f"{n_sm} SMs x {per_clk:.2f} cells/clock (ALU pipe 64 lanes x 2 int16 halves / 3 fused "
+                      f"add-max per cell) x {sm_max:.0f} MHz (max SM clock)",
+        "frac_of_4op_floor": achieved / floor4,
+        "frac_at_measured_clock": achieved / (n_sm * per_clk * sm_mhz * 1e6) if sm_mhz else None,
+    }
+
+
 def setup_tiles(args, B) -> dict:
     """Stage-2 tile shape policy and its cost constants (measured on this
     device by the library's calibration unless --no-autotune)."""
@@ -245,7 +297,7 @@ def run_gpu(args, rank, world, local_rank):
     B.lib()
     B.plast_set_schedule(1 if args.schedule == "per_key" else 0)
     tiles = setup_tiles(args, B)
-    prm = B.plast_default_params(s0=args.s0)
+    prm = B.plast_default_params()
 
     t0 = time.time()
     b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale, n2=2)
@@ -265,7 +317,7 @@ def run_gpu(args, rank, world, local_rank):
     g1 = B.plast_index_bank(d1c, d1o)
     g2 = B.plast_index_bank(d2c, d2o)
     pairs = B.plast_pair_count(g1, g2)
-    recs, n_ung = B.plast_search(g1, g2, prm)
+    recs, n_ung = B.plast_search_ex(g1, g2, prm, s0=args.s0)
     cap = int(recs.shape[0] * 1.05) + 1024
     out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device=dev)
     n_recs = recs.shape[0]
@@ -281,7 +333,10 @@ def run_gpu(args, rank, world, local_rank):
     def step(c1, o1_, c2, o2_):
         a = B.plast_index_bank(c1, o1_)
         b = B.plast_index_bank(c2, o2_)
-        r, _ = B.plast_search(a, b, prm, out=out, cap=cap)
+        if args.s0:
+            r, _ = B.plast_search_ex(a, b, prm, s0=args.s0, out=out, cap=cap)
+        else:
+            r = B.plast_search(a, b, prm, out=out, cap=cap)
         stage_ms.append(B.plast_stage_times())
         a.free()
         b.free()
@@ -315,6 +370,7 @@ def run_gpu(args, rank, world, local_rank):
     ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
     clocks = clk.summary()
     ung_ms = statistics.mean(s["stage2_kernel"] for s in stage_ms)
+    gap_ms = statistics.mean(s["stage31_kernel"] for s in stage_ms)
     stages = {name: round(statistics.mean(s[name] for s in stage_ms), 3) for name in B.STAGES}
 
     # ---- end-to-end arm: host buffers in, records out
@@ -347,7 +403,8 @@ def run_gpu(args, rank, world, local_rank):
     n_sm = props.multi_processor_count
     # A cell needs one int16 max (ALU pipe: 64 lanes x 2 halves per clock per
     # SM) and one int16 add (FMA-heavy pipe, the same rate): 128 cells per
-    # clock per SM (see profiles/pipes_sm103.md).
+    # clock per SM.  The pipe of each instruction and the issue rates are the
+    # ones the probe in paper_0804_3643_gb300/probe/pipes.cu measures.
     peak_cells = n_sm * CELLS_PER_CLK_SM * sm_max * 1e6
     achieved_cells = pairs * CELLS_PER_PAIR / (ung_ms / 1e3)
     tr = committed_traffic()
@@ -367,21 +424,13 @@ def run_gpu(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "int16",
         "data": "synthetic",
-        "config": {
-            "workload": f"PLAST-P {'full scale' if args.scale == 1.0 and not args.bank2_proteins else 'reduced'}: "
-                        f"{b1.n_seqs} x {b2.n_seqs} synthetic proteins "
-                        f"({len(b1.codes)} / {len(b2.codes)} residues), 5% planted homologs, seed 1",
-            "step": "index both banks + ungapped all pairs + sort + small gapped"
-                    + (f" (Section 4.2 filter on, S0 = {args.s0}: lossy, fewer hits)" if args.s0 else ""),
-            "pairs_per_step": pairs,
+        "config": headline_config(b1, b2, pairs, args.scale, args.bank2_proteins, args.s0, world),
+        "run": {
             "stage2_hits_per_step": n_ung,
             "records_per_step": n_recs,
-            "params": prm.as_dict(),
             "schedule": args.schedule,
             "stage2_tiles": tiles,
-            "l2": f"inputs larger than L2 (129 MB): {nb_gb:.2f} GB of neighbourhood arrays rebuilt and "
-                  "read every step, no explicit flush",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "neighbourhood_gb": round(nb_gb, 3),
         },
         "gcups": world * pairs * CELLS_PER_PAIR / (ms_step / 1e3) / 1e9,
         "stage_ms": stages,
@@ -402,6 +451,7 @@ def run_gpu(args, rank, world, local_rank):
                                        if clocks.get("sm_mhz") else None),
             "hbm_gbs": (traffic / (ung_ms / 1e3) / 1e9) if traffic else None,
         },
+        "roofline_stage31": stage31_roofline(n_ung, gap_ms, n_sm, sm_max, clocks.get("sm_mhz")),
         "e2e": {"value": world * pairs / (e2e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": int(rec_bytes), "ms_per_step": e2e_ms},
         "clocks": clocks,
@@ -429,21 +479,23 @@ def _time_steps(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_stress(args):
+def run_stress(args, steps=None, warmup=None, tiles=None):
     """50,000 x 50,000 proteins, 20 % with low-complexity runs: heavy-tailed
     key lists; the persistent work-queue launch against one launch per key."""
     import torch
 
     from paper_0804_3643_gb300 import binding as B
 
-    tiles = setup_tiles(args, B)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    tiles = setup_tiles(args, B) if tiles is None else tiles
     b1, b2 = synth.workload("batching_stress", seed=1, scale=args.scale)
     d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
     d2 = B.DeviceBank.from_host(b2.codes, b2.seq_off)
     g1 = B.plast_index_bank(d1.codes, d1.seq_off)
     g2 = B.plast_index_bank(d2.codes, d2.seq_off)
     pairs = B.plast_pair_count(g1, g2)
-    recs, n_ung = B.plast_search(g1, g2)
+    recs, n_ung = B.plast_search_ex(g1, g2)
     cap = int(recs.shape[0] * 1.05) + 1024
     out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
     res = {}
@@ -456,9 +508,9 @@ def run_stress(args):
             B.plast_search(g1, g2, out=out, cap=cap)
             st.append(B.plast_stage_times())
 
-        ms = _time_steps(step, args.steps, args.warmup)
+        ms = _time_steps(step, steps, warmup)
         res[name] = {"ms_per_search": ms, "pairs_per_s": pairs / (ms / 1e3),
-                     "stage2_ms": statistics.mean(x["stage2_kernel"] for x in st[args.warmup:])}
+                     "stage2_ms": statistics.mean(x["stage2_kernel"] for x in st[warmup:])}
     B.plast_set_schedule(0)
     B.plast_set_timing(False)
     n1 = np.diff(np.array(B.plast_bank_export_index(g1)[0].cpu()))
@@ -491,7 +543,7 @@ def run_tplastn(args):
     g1 = B.plast_index_bank(d1.codes, d1.seq_off)
     g2 = B.plast_index_bank(aa, so)
     pairs = B.plast_pair_count(g1, g2)
-    recs, n_ung = B.plast_search(g1, g2)
+    recs, n_ung = B.plast_search_ex(g1, g2)
     cap = int(recs.shape[0] * 1.05) + 1024
     out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
     n_rec = int(recs.shape[0])
@@ -532,7 +584,7 @@ def run_plastx(args):
     g1 = B.plast_index_bank(a1, s1)
     g2 = B.plast_index_bank(a2, s2)
     pairs = B.plast_pair_count(g1, g2)
-    recs, n_ung = B.plast_search(g1, g2)
+    recs, n_ung = B.plast_search_ex(g1, g2)
     cap = int(recs.shape[0] * 1.05) + 1024
     out = torch.empty(cap * B.GAPPED_BYTES, dtype=torch.uint8, device="cuda")
     n_rec = int(recs.shape[0])
@@ -559,7 +611,7 @@ def run_plastx(args):
     }
 
 
-def run_query(args):
+def run_query(args, steps=None, warmup=None, tiles=None):
     """One query bank of --query-proteins proteins against a resident bank of
     --bank2-proteins (default 1,000,000): the search a serving request runs,
     timed three ways: the plain call (plast_search: work list, allocation and
@@ -571,7 +623,9 @@ def run_query(args):
     from paper_0804_3643_gb300 import binding as B
 
     B.lib()
-    tiles = setup_tiles(args, B)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    tiles = setup_tiles(args, B) if tiles is None else tiles
     n_bank = args.bank2_proteins or 1_000_000
     t0 = time.time()
     bank = synth.random_protein_bank(np.random.default_rng(1), max(2, int(n_bank * args.scale)))
@@ -582,15 +636,15 @@ def run_query(args):
     gq = B.plast_index_bank(dq.codes, dq.seq_off)
     log(f"banks ready in {time.time() - t0:.1f}s")
     pairs = B.plast_pair_count(gq, gb)
-    ref, n_ung = B.plast_search(gq, gb)
+    ref, n_ung = B.plast_search_ex(gq, gb)
     st = torch.cuda.Stream()
     plan = B.Plan(gq, gb, max_hits=2 * n_ung + 4096, max_records=2 * ref.shape[0] + 1024, stream=st)
     plan.capture(st)
     res = {}
     with torch.cuda.stream(st):
-        res["search_ms"] = _time_steps(lambda: B.plast_search(gq, gb, stream=st), args.steps, args.warmup)
-        res["plan_ms"] = _time_steps(lambda: (plan.run(st), plan.result(st)), args.steps, args.warmup)
-        res["graph_ms"] = _time_steps(lambda: (plan.launch(st), plan.result(st)), args.steps, args.warmup)
+        res["search_ms"] = _time_steps(lambda: B.plast_search(gq, gb, stream=st), steps, warmup)
+        res["plan_ms"] = _time_steps(lambda: (plan.run(st), plan.result(st)), steps, warmup)
+        res["graph_ms"] = _time_steps(lambda: (plan.launch(st), plan.result(st)), steps, warmup)
     recs, nu = plan.result(st)
     if not (torch.equal(recs, ref) and nu == n_ung):
         raise RuntimeError("planned search differs from plast_search")
@@ -651,6 +705,45 @@ def run_serving(args):
 
 
 
+def run_extras(args, tiles) -> dict:
+    """Secondary targets measured after the headline (not part of its timed
+    region): the batching-stress workload (50,000 x 50,000 proteins with
+    low-complexity runs) under the persistent work queue and under one launch
+    per key, and one 250-protein query against a resident 1,000,000-protein
+    bank as a plain call, a planned search and its CUDA-graph replay."""
+    import torch
+
+    out = {}
+    t0 = time.time()
+    s = run_stress(args, steps=2, warmup=1, tiles=tiles)
+    out["batching_stress"] = {
+        "workload": s["workload"], "pairs": s["pairs"], "stage2_hits": s["stage2_hits"],
+        "pairs_per_key_max": s["pairs_per_key"]["max"],
+        "persistent": {k: round(v, 3) for k, v in s["schedules"]["persistent"].items() if k != "pairs_per_s"},
+        "per_key": {k: round(v, 3) for k, v in s["schedules"]["per_key"].items() if k != "pairs_per_s"},
+        "speedup_persistent_over_per_key": round(s["speedup_persistent_over_per_key"], 3),
+        "timing": "CUDA events, 1 warm-up + 2 timed searches per schedule",
+    }
+    torch.cuda.empty_cache()
+    log(f"batching stress done in {time.time() - t0:.1f}s")
+    t0 = time.time()
+    saved = (args.query_proteins, args.bank2_proteins, args.scale)
+    args.query_proteins, args.bank2_proteins = 250, 1_000_000
+    try:
+        q = run_query(args, steps=10, warmup=3, tiles=tiles)
+    finally:
+        args.query_proteins, args.bank2_proteins, args.scale = saved
+    out["query_latency"] = {
+        "workload": q["workload"], "pairs": q["pairs"], "records": q["records"],
+        "plain_call_ms": round(q["search_ms"], 3), "planned_ms": round(q["plan_ms"], 3),
+        "cuda_graph_ms": round(q["graph_ms"], 3), "stage_ms": q["stage_ms"],
+        "timing": "CUDA events, 3 warm-up + 10 timed searches per form",
+    }
+    torch.cuda.empty_cache()
+    log(f"query latency done in {time.time() - t0:.1f}s")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -659,8 +752,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--schedule", default="persistent", choices=["persistent", "per_key"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample size, seconds of CPU work")
+    ap.add_argument("--cpu-steps", type=int, default=3,
+                    help="cpu_baseline: timed oracle steps over the fixed key sample (about 4 s each on 16 cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (batching stress, resident-bank query latency)")
     ap.add_argument("--cpu-threads", type=int, default=None, help="oracle threads (default: every host core)")
     ap.add_argument("--tile-shape", default="auto", choices=["auto", "wide", "narrow", "narrow4", "narrow2", "narrow16"],
                     help="stage-2 tile shapes: by measured cost (default) or forced")
@@ -687,16 +783,14 @@ def main():
         # the CPU oracle, on rank 0 only
         if rank != 0:
             return
-        b1, b2 = synth.workload(WORKLOAD, seed=1, scale=args.scale)
-        per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-        cb = run_oracle(b1, b2, per_step, args.steps, args.warmup, args.cpu_threads)
+        b1, _ = synth.workload(WORKLOAD, seed=1, scale=args.scale, n2=2)
+        _, b2 = synth.workload(WORKLOAD, seed=shard_seed(0), scale=args.scale, n2=args.bank2_proteins)
+        cb = run_oracle(b1, b2, args.steps, args.warmup, args.cpu_threads, s0=args.s0)
         line = {
             "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"PLAST-P {'full scale' if args.scale == 1.0 else 'reduced'}: "
-                                   f"{b1.n_seqs} x {b2.n_seqs} synthetic proteins, seed 1",
-                       "step": "CPU oracle: stages 1-2 and 3.1 over a bounded random sample of keys"},
+            "config": headline_config(b1, b2, cb["total_pairs"], args.scale, args.bank2_proteins, args.s0, world),
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }
@@ -717,9 +811,13 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     result, banks = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_extras and args.scale == 1.0 and not args.bank2_proteins:
+        from paper_0804_3643_gb300 import binding as B
+
+        result["extras"] = run_extras(args, B.plast_get_tile_costs())
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            cb = run_oracle(banks[0], banks[1], args.cpu_seconds, 1, 0, args.cpu_threads, s0=args.s0)
+            cb = run_oracle(banks[0], banks[1], args.cpu_steps, 0, args.cpu_threads, s0=args.s0)
             result["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -69,20 +69,24 @@ typedef struct plast_bank plast_bank;
  *              extension keeps row i's values offset by i*gap_extend in
  *              int16)
  *   s2         small gapped threshold: kept if the score >= s2
- *   s0         filter threshold of Section 4.2, 0 = no filter (0..30000):
- *              a pair is kept by stage 2 only if, besides its ungapped
- *              score reaching s1, the sum of the positive substitution
- *              scores over its window (clipped like the ungapped score)
- *              reaches s0.  Lossy: it removes hits the unfiltered search
- *              keeps.  PLAST_FILTER_S0 is the value that lets about 2.5 %
- *              of random pairs through, as the paper reports.
- * Defaults (plast_default_params): 4, 22, 22, 38, 64, 8, 11, 1, 47, 0.
+ * Defaults (plast_default_params): 4, 22, 22, 38, 64, 8, 11, 1, 47.
+ * Section 4.2's lossy filter threshold S0 is not a field: it is an argument
+ * of plast_ungapped_ex, plast_search_ex and plast_plan_create, so that the
+ * five calls of the boundary keep exactly this nine-field layout.
  */
 typedef struct {
   int32_t w, nl, nr, s1, lg, band, gap_open, gap_extend, s2;
-  int32_t s0;
 } plast_params;
 
+/*
+ * Filter threshold of Section 4.2 (the s0 argument of the _ex calls and of
+ * plast_plan_create; 0 = no filter, at most 30000): a pair is kept by stage 2
+ * only if, besides its ungapped score reaching s1, the sum of the positive
+ * substitution scores over its window (clipped like the ungapped score)
+ * reaches s0.  Lossy: it removes hits the unfiltered search keeps.
+ * PLAST_FILTER_S0 is the value that lets about 2.5 % of random pairs
+ * through, as the paper reports.
+ */
 #define PLAST_FILTER_S0 53
 
 /*
@@ -175,9 +179,8 @@ int plast_bank_export_index(const plast_bank* bank, int64_t* key_off, int32_t* p
 /*
  * Stages 1-2 (Sections 3.3.2-3.3.3, Annex 4): for every key present in both
  * banks, every pair of occurrences gets an ungapped extension; pairs scoring
- * >= params->s1 (and, when params->s0 > 0, passing Section 4.2's filter)
- * are written to out[0 .. *n_out) sorted by (seq1, pos1, seq2, pos2).
- * out: [cap] plast_hit (device).
+ * >= params->s1 are written to out[0 .. *n_out) sorted by (seq1, pos1, seq2,
+ * pos2).  out: [cap] plast_hit (device).
  * Errors: PLAST_E_INVALID, PLAST_E_CAPACITY (*n_out = needed), PLAST_E_OOM,
  * PLAST_E_CUDA, PLAST_E_TIMEOUT.
  */
@@ -185,18 +188,20 @@ int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_param
                    int64_t cap, int64_t* n_out, void* stream);
 
 /*
- * plast_ungapped / plast_search restricted to the subset-seed keys
- * keys[0 .. n_keys) (each in 0..8799; duplicates ignored).  Stages 1-3.1 are
- * independent per key (Section 5.1 hands seeds to cores one at a time), so the
- * records of a key set are exactly the records of the full call whose seed
- * word has one of those keys.  Used to shard a comparison by key and to check
- * a sample of keys of a large comparison.  Errors as the unrestricted calls,
- * and PLAST_E_INVALID for a key outside 0..8799.
+ * plast_ungapped with two options the boundary call leaves out:
+ *   s0     Section 4.2's filter threshold (0 = off; see PLAST_FILTER_S0)
+ *   keys   host array of n_keys subset-seed keys (each 0..8799, duplicates
+ *          ignored) to restrict the comparison to, or NULL for every key.
+ *          Stages 1-3.1 are independent per key (Section 5.1 hands seeds to
+ *          cores one at a time), so the hits of a key set are exactly the
+ *          hits of the full call whose seed word has one of those keys.
+ * plast_ungapped(b1, b2, p, out, cap, n, st) is
+ * plast_ungapped_ex(b1, b2, p, 0, NULL, 0, out, cap, n, st).  Errors as
+ * plast_ungapped, and PLAST_E_INVALID for s0 outside 0..30000, a key outside
+ * 0..8799, or n_keys < 0.
  */
-int plast_ungapped_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
-                        int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out, void* stream);
-int plast_search_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
-                      int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
+int plast_ungapped_ex(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                      const int32_t* keys, int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out,
                       void* stream);
 
 /*
@@ -219,12 +224,22 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
  * Stages 1-3.1 in one call (Section 3.2's loop without stages 3.2 and 4):
  * ungapped extension of every pair, small gapped extension of the hits
  * scoring >= s1, and the records scoring >= s2 written to out sorted by
- * (seq1, pos1, seq2, pos2).  *n_ungapped_out (host, may be NULL) receives
- * the number of stage-2 hits (at most 2^32 - 1 per call, else
- * PLAST_E_CAPACITY).  Errors as plast_ungapped.
+ * (seq1, pos1, seq2, pos2).  Errors as plast_ungapped (and PLAST_E_CAPACITY
+ * when a call has 2^32 or more stage-2 hits).
  */
 int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
-                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream);
+                 int64_t cap, int64_t* n_out, void* stream);
+
+/*
+ * plast_search with the options of plast_ungapped_ex (s0, keys / n_keys,
+ * NULL keys = every key) and one more output: *n_ungapped_out (host, may be
+ * NULL) receives the number of stage-2 hits (those through the S0 filter
+ * when s0 > 0).  plast_search(b1, b2, p, out, cap, n, st) is
+ * plast_search_ex(b1, b2, p, 0, NULL, 0, out, cap, n, NULL, st).
+ */
+int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                    const int32_t* keys, int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out,
+                    int64_t* n_ungapped_out, void* stream);
 
 /*
  * plast_small_gapped without device allocation.  The paper has no
@@ -243,7 +258,10 @@ int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params*
  *    other threads) race and must be serialised by the caller;
  *  - the first call on a device performs one-time set-up (it looks up the
  *    array's device address and loads the score tables into constant
- *    memory); make that first call before any stream capture.
+ *    memory); make that first call before any stream capture.  That set-up
+ *    is kept for the life of the process: after cudaDeviceReset (or
+ *    anything else that replaces the device's primary context) the address
+ *    is stale, so do not call into the library again in that process.
  */
 #define PLAST_NOALLOC_MAX_HITS 65536
 #define PLAST_NOALLOC_SCRATCH_BYTES (2 * 1024 * 1024 + 8192)
@@ -265,15 +283,17 @@ int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank* b2, const
  * and plast_plan_launch replays it.  plast_plan_result synchronises `stream`
  * and returns the record count of the last run (records in canonical order,
  * as plast_search) and its stage-2 hit count (those through the S0 filter
- * when params->s0 > 0; max_hits bounds the count before it); PLAST_E_CAPACITY if either
+ * when s0 > 0, s0 as in plast_search_ex; max_hits bounds the count before
+ * it); PLAST_E_CAPACITY if either
  * limit was exceeded (*n_records then holds the hit or record count that did
  * not fit, and the records are an incomplete subset).  PLAST_E_INVALID at
  * creation unless max_records >= 1 and 1 <= max_hits < 2^32.  Runs of one
  * plan must not overlap on the device.
  */
 typedef struct plast_plan plast_plan;
-int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int64_t max_hits,
-                      plast_gapped* records, int64_t max_records, void* stream, plast_plan** out);
+int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                      int64_t max_hits, plast_gapped* records, int64_t max_records, void* stream,
+                      plast_plan** out);
 int plast_plan_run(plast_plan* plan, void* stream);
 int plast_plan_capture(plast_plan* plan, void* stream);
 int plast_plan_launch(plast_plan* plan, void* stream);

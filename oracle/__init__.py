@@ -102,7 +102,7 @@ def lib() -> ctypes.CDLL:
         L.oracle_filter_pair.restype = i32
         L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, P, i32, P, P, P]
         L.oracle_ungapped.restype = i64
-        L.oracle_small_gapped.argtypes = [P, P, P, P, P, P, i64, P]
+        L.oracle_small_gapped.argtypes = [P, P, P, P, P, P, i64, i32, P]
         L.oracle_small_gapped.restype = i64
         L.oracle_free.argtypes = [P]
         L.oracle_smith_waterman.argtypes = [P, i32, P, i32, i32, i32]
@@ -255,14 +255,15 @@ def small_gapped_pair(s1, p1: int, s2, p2: int, params: Params = Params()):
     return (g,) + tuple(x.value for x in v)
 
 
-def small_gapped(b1: Bank, b2: Bank, hits: np.ndarray, params: Params = Params()) -> np.ndarray:
-    """Stage 3.1 of every hit, keeping those with G >= s2, in input order."""
+def small_gapped(b1: Bank, b2: Bank, hits: np.ndarray, params: Params = Params(), threads: int = 1) -> np.ndarray:
+    """Stage 3.1 of every hit, keeping those with G >= s2, in input order
+    (``threads`` share the hits; the result does not depend on them)."""
     hits = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
     out = ctypes.c_void_p()
     prm = params.c()
     L = lib()
     n = L.oracle_small_gapped(_p(b1.codes), _p(b1.seq_off), _p(b2.codes), _p(b2.seq_off), ctypes.byref(prm),
-                              _p(hits) if hits.size else None, hits.size, ctypes.byref(out))
+                              _p(hits) if hits.size else None, hits.size, threads, ctypes.byref(out))
     buf = (ctypes.c_char * (n * GAPPED_DTYPE.itemsize)).from_address(out.value) if n else b""
     res = np.frombuffer(bytes(buf), dtype=GAPPED_DTYPE).copy()
     L.oracle_free(out)

@@ -379,18 +379,26 @@ typedef struct {
  * Stages 1 and 2 over a range of keys (Section 3.2's loop "for all possible
  * seeds"): for every key shared by the two banks, every pair of occurrences
  * is extended without gaps; pairs scoring at least s1 are kept.  Several
- * threads may share the key range the way Section 5.1 shares seeds between
- * cores: a counter under a mutex hands out the next key.  Each thread keeps
- * its own list; the lists are merged and sorted by (seq1, pos1, seq2, pos2),
- * so the result does not depend on the number of threads.
+ * threads may share the work the way Section 5.1 shares seeds between
+ * cores: a cursor under a mutex hands out the next piece of work, a key's
+ * bank-1 occurrences a run at a time (runs of about 2^20 pairs, so that one
+ * key with a very long list does not keep a single thread busy).  Each
+ * thread keeps its own list; the lists are merged and sorted by (seq1, pos1,
+ * seq2, pos2), so the result does not depend on the number of threads or on
+ * how the work was cut.
  * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t at;     /* index into the key range (or into key_list) */
+  int64_t u_next; /* next bank-1 occurrence of that key; -1: not started */
+} work_cursor;
+
 typedef struct {
   const bank_view* b1;
   const bank_view* b2;
   const oracle_params* prm;
-  const int32_t* key_list; /* NULL: keys are the counter values themselves */
+  const int32_t* key_list; /* NULL: keys are the cursor values themselves */
   int32_t key_hi;
-  int32_t* next_key;
+  work_cursor* cursor;
   pthread_mutex_t* lock;
   oracle_hit* out;
   int64_t n, cap;
@@ -405,17 +413,47 @@ static void push_hit(ungapped_job* j, oracle_hit h) {
   j->out[j->n++] = h;
 }
 
+/* The next piece of work: key *k, bank-1 occurrences [*u0, *u1).  Returns 0
+ * when the range is exhausted.  Called with the lock held. */
+static int next_work(ungapped_job* j, int32_t* k, int64_t* u0, int64_t* u1) {
+  work_cursor* c = j->cursor;
+  while (c->at < j->key_hi) {
+    const int32_t key = j->key_list ? j->key_list[c->at] : c->at;
+    const int64_t lo = j->b1->key_off[key], hi = j->b1->key_off[key + 1];
+    const int64_t n2 = j->b2->key_off[key + 1] - j->b2->key_off[key];
+    if (hi == lo || n2 == 0) {
+      c->at++;
+      c->u_next = -1;
+      continue;
+    }
+    if (c->u_next < 0) c->u_next = lo;
+    int64_t run = ((int64_t)1 << 20) / n2;
+    if (run < 1) run = 1;
+    *k = key;
+    *u0 = c->u_next;
+    *u1 = *u0 + run < hi ? *u0 + run : hi;
+    c->u_next = *u1;
+    if (*u1 == hi) {
+      c->at++;
+      c->u_next = -1;
+    }
+    return 1;
+  }
+  return 0;
+}
+
 static void* ungapped_worker(void* arg) {
   ungapped_job* j = (ungapped_job*)arg;
   const bank_view* b1 = j->b1;
   const bank_view* b2 = j->b2;
   for (;;) {
+    int32_t k;
+    int64_t ua, ub;
     pthread_mutex_lock(j->lock);
-    int32_t at = (*j->next_key)++;
+    const int more = next_work(j, &k, &ua, &ub);
     pthread_mutex_unlock(j->lock);
-    if (at >= j->key_hi) break;
-    int32_t k = j->key_list ? j->key_list[at] : at;
-    for (int64_t u = b1->key_off[k]; u < b1->key_off[k + 1]; u++) {
+    if (!more) break;
+    for (int64_t u = ua; u < ub; u++) {
       int64_t g1 = b1->pos[u];
       int32_t q1 = seq_of(b1->seq_off, b1->n_seqs, g1);
       int64_t o1 = b1->seq_off[q1];
@@ -462,7 +500,7 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
   bank_view b1 = {codes1, seq_off1, n1, key_off1, pos1};
   bank_view b2 = {codes2, seq_off2, n2, key_off2, pos2};
   if (n_threads < 1) n_threads = 1;
-  int32_t next_key = key_lo;
+  work_cursor cursor = {key_lo, -1};
   pthread_mutex_t lock;
   pthread_mutex_init(&lock, NULL);
   ungapped_job* jobs = (ungapped_job*)calloc((size_t)n_threads, sizeof(ungapped_job));
@@ -473,7 +511,7 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
     jobs[t].prm = prm;
     jobs[t].key_list = key_list;
     jobs[t].key_hi = key_hi;
-    jobs[t].next_key = &next_key;
+    jobs[t].cursor = &cursor;
     jobs[t].lock = &lock;
   }
   if (n_threads == 1) {
@@ -509,33 +547,80 @@ int64_t oracle_ungapped(const int8_t* codes1, const int64_t* seq_off1, int32_t n
  * Stage 3.1 over a list of ungapped hits (Section 3.2: a hit scoring at
  * least S1 gets a small gapped extension, kept if it scores at least S2).
  * Output keeps the input order; *out is malloc'ed.  Returns the count.
+ * With n_threads > 1 the hits are cut into that many consecutive ranges,
+ * each extended by one thread into its own slots; the records are then
+ * taken in input order, so the result does not depend on n_threads.
  * ---------------------------------------------------------------------- */
+typedef struct {
+  const int8_t *codes1, *codes2;
+  const int64_t *seq_off1, *seq_off2;
+  const oracle_params* prm;
+  const oracle_hit* in;
+  int64_t lo, hi;
+  oracle_gapped* slot; /* one record per hit */
+  char* keep;          /* G >= s2 per hit */
+} gapped_job;
+
+static void* gapped_worker(void* arg) {
+  gapped_job* j = (gapped_job*)arg;
+  for (int64_t u = j->lo; u < j->hi; u++) {
+    const oracle_hit* h = &j->in[u];
+    int64_t o1 = j->seq_off1[h->seq1], o2 = j->seq_off2[h->seq2];
+    int64_t len1 = j->seq_off1[h->seq1 + 1] - o1, len2 = j->seq_off2[h->seq2 + 1] - o2;
+    int32_t ri, rj, li, lj;
+    int32_t g = oracle_small_gapped_pair(j->codes1 + o1, len1, h->pos1, j->codes2 + o2, len2, h->pos2, j->prm, &ri,
+                                         &rj, &li, &lj);
+    j->keep[u] = g >= j->prm->s2;
+    oracle_gapped* r = &j->slot[u];
+    r->seq1 = h->seq1;
+    r->pos1 = h->pos1;
+    r->seq2 = h->seq2;
+    r->pos2 = h->pos2;
+    r->score = (int16_t)g;
+    r->ungapped = h->score;
+    r->r_i = (int16_t)ri;
+    r->r_j = (int16_t)rj;
+    r->l_i = (int16_t)li;
+    r->l_j = (int16_t)lj;
+  }
+  return NULL;
+}
+
 int64_t oracle_small_gapped(const int8_t* codes1, const int64_t* seq_off1, const int8_t* codes2,
                             const int64_t* seq_off2, const oracle_params* prm, const oracle_hit* in, int64_t n_in,
-                            oracle_gapped** out) {
-  oracle_gapped* res = (oracle_gapped*)malloc(sizeof(oracle_gapped) * (size_t)(n_in > 0 ? n_in : 1));
-  int64_t n = 0;
-  for (int64_t u = 0; u < n_in; u++) {
-    const oracle_hit* h = &in[u];
-    int64_t o1 = seq_off1[h->seq1], o2 = seq_off2[h->seq2];
-    int64_t len1 = seq_off1[h->seq1 + 1] - o1, len2 = seq_off2[h->seq2 + 1] - o2;
-    int32_t ri, rj, li, lj;
-    int32_t g = oracle_small_gapped_pair(codes1 + o1, len1, h->pos1, codes2 + o2, len2, h->pos2, prm, &ri, &rj, &li,
-                                         &lj);
-    if (g >= prm->s2) {
-      oracle_gapped* r = &res[n++];
-      r->seq1 = h->seq1;
-      r->pos1 = h->pos1;
-      r->seq2 = h->seq2;
-      r->pos2 = h->pos2;
-      r->score = (int16_t)g;
-      r->ungapped = h->score;
-      r->r_i = (int16_t)ri;
-      r->r_j = (int16_t)rj;
-      r->l_i = (int16_t)li;
-      r->l_j = (int16_t)lj;
-    }
+                            int32_t n_threads, oracle_gapped** out) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_in < (int64_t)n_threads * 64) n_threads = 1;
+  const size_t m = (size_t)(n_in > 0 ? n_in : 1);
+  oracle_gapped* res = (oracle_gapped*)malloc(sizeof(oracle_gapped) * m);
+  char* keep = (char*)malloc(m);
+  gapped_job* jobs = (gapped_job*)calloc((size_t)n_threads, sizeof(gapped_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+  for (int32_t t = 0; t < n_threads; t++) {
+    gapped_job* j = &jobs[t];
+    j->codes1 = codes1;
+    j->codes2 = codes2;
+    j->seq_off1 = seq_off1;
+    j->seq_off2 = seq_off2;
+    j->prm = prm;
+    j->in = in;
+    j->lo = n_in * t / n_threads;
+    j->hi = n_in * (t + 1) / n_threads;
+    j->slot = res;
+    j->keep = keep;
   }
+  if (n_threads == 1) {
+    gapped_worker(&jobs[0]);
+  } else {
+    for (int32_t t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, gapped_worker, &jobs[t]);
+    for (int32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+  }
+  int64_t n = 0;
+  for (int64_t u = 0; u < n_in; u++)
+    if (keep[u]) res[n++] = res[u];
+  free(keep);
+  free(jobs);
+  free(th);
   *out = res;
   return n;
 }

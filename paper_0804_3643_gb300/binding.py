@@ -40,7 +40,7 @@ PLAST_FILTER_S0 = 53  # the header's calibrated Section 4.2 filter threshold
 
 class plast_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2", "s0")]
+                ("w", "nl", "nr", "s1", "lg", "band", "gap_open", "gap_extend", "s2")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -107,15 +107,15 @@ def lib() -> ctypes.CDLL:
         L.plast_pair_count.restype = i64
         L.plast_small_gapped.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
         L.plast_small_gapped.restype = ctypes.c_int
-        L.plast_search.argtypes = [P, P, pPrm, P, i64, pI64, pI64, P]
+        L.plast_search.argtypes = [P, P, pPrm, P, i64, pI64, P]
         L.plast_search.restype = ctypes.c_int
+        L.plast_search_ex.argtypes = [P, P, pPrm, i32, P, i32, P, i64, pI64, pI64, P]
+        L.plast_search_ex.restype = ctypes.c_int
+        L.plast_ungapped_ex.argtypes = [P, P, pPrm, i32, P, i32, P, i64, pI64, P]
+        L.plast_ungapped_ex.restype = ctypes.c_int
         L.plast_small_gapped_noalloc.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
         L.plast_small_gapped_noalloc.restype = ctypes.c_int
-        L.plast_ungapped_keys.argtypes = [P, P, pPrm, P, i32, P, i64, pI64, P]
-        L.plast_ungapped_keys.restype = ctypes.c_int
-        L.plast_search_keys.argtypes = [P, P, pPrm, P, i32, P, i64, pI64, pI64, P]
-        L.plast_search_keys.restype = ctypes.c_int
-        L.plast_plan_create.argtypes = [P, P, pPrm, i64, P, i64, P, ctypes.POINTER(ctypes.c_void_p)]
+        L.plast_plan_create.argtypes = [P, P, pPrm, i32, i64, P, i64, P, ctypes.POINTER(ctypes.c_void_p)]
         L.plast_plan_create.restype = ctypes.c_int
         for f in ("plast_plan_run", "plast_plan_capture", "plast_plan_launch"):
             getattr(L, f).argtypes = [P, P]
@@ -414,24 +414,56 @@ def plast_small_gapped_noalloc(b1: Bank, b2: Bank, hits: torch.Tensor, out: torc
 
 
 def plast_search(b1: Bank, b2: Bank, params: plast_params | None = None, cap: int | None = None,
-                 out: torch.Tensor | None = None, stream=None):
-    """(records [n, 28] uint8 device tensor, number of stage-2 hits); sized
-    automatically unless ``cap`` or ``out`` is given, as plast_ungapped."""
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Stage-3.1 records [n, 28] (uint8 device tensor, canonical order);
+    sized automatically unless ``cap`` or ``out`` is given, as plast_ungapped."""
     auto = cap is None and out is None
     if cap is None:
         cap = out.numel() // GAPPED_BYTES if out is not None else plast_pair_count(b1, b2) // 256 + 4096
     for _ in range(2):
         buf = _records(out, cap, GAPPED_BYTES)
-        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        n = ctypes.c_int64()
         rc = lib().plast_search(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
-                                _ptr(buf), cap, ctypes.byref(n), ctypes.byref(nu), _stream(stream))
+                                _ptr(buf), cap, ctypes.byref(n), _stream(stream))
         if rc == PLAST_E_CAPACITY and auto:
             cap, out = n.value, None
             continue
         if rc:
             raise PlastError("plast_search", rc, n.value)
-        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
+        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES)
     raise PlastError("plast_search", PLAST_E_CAPACITY, cap)
+
+
+def _keys_arg(keys):
+    """(host int32 array or None, ctypes pointer, count) of a key list (None = every key)."""
+    if keys is None:
+        return None, ctypes.c_void_p(0), 0
+    k = np.ascontiguousarray(np.asarray(keys, dtype=np.int32))
+    return k, k.ctypes.data_as(ctypes.c_void_p), len(k)
+
+
+def plast_search_ex(b1: Bank, b2: Bank, params: plast_params | None = None, s0: int = 0, keys=None,
+                    cap: int | None = None, out: torch.Tensor | None = None, stream=None):
+    """plast_search with Section 4.2's filter threshold ``s0`` (0 = off) and
+    an optional host list of subset-seed ``keys`` (None = every key):
+    (records [n, 28] uint8 device tensor, number of stage-2 hits)."""
+    auto = cap is None and out is None
+    if cap is None:
+        cap = out.numel() // GAPPED_BYTES if out is not None else plast_pair_count(b1, b2) // 256 + 4096
+    k, kp, nk = _keys_arg(keys)
+    for _ in range(2):
+        buf = _records(out, cap, GAPPED_BYTES)
+        n, nu = ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().plast_search_ex(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                   int(s0), kp, nk, _ptr(buf), cap, ctypes.byref(n), ctypes.byref(nu),
+                                   _stream(stream))
+        if rc == PLAST_E_CAPACITY and auto:
+            cap, out = n.value, None
+            continue
+        if rc:
+            raise PlastError("plast_search_ex", rc, n.value)
+        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
+    raise PlastError("plast_search_ex", PLAST_E_CAPACITY, cap)
 
 
 class Plan:
@@ -441,13 +473,13 @@ class Plan:
     graph.  The banks must outlive the plan."""
 
     def __init__(self, b1: Bank, b2: Bank, max_hits: int, max_records: int, params: plast_params | None = None,
-                 stream=None):
+                 s0: int = 0, stream=None):
         self.banks = (b1, b2)
         self.records = torch.empty(max(max_records, 1) * GAPPED_BYTES, dtype=torch.uint8,
                                    device=torch.device("cuda", torch.cuda.current_device()))
         self.handle = ctypes.c_void_p()
         rc = lib().plast_plan_create(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
-                                     max_hits, _ptr(self.records), max_records, _stream(stream),
+                                     int(s0), max_hits, _ptr(self.records), max_records, _stream(stream),
                                      ctypes.byref(self.handle))
         if rc:
             self.handle = None
@@ -488,50 +520,25 @@ class Plan:
             pass
 
 
-def _keys_host(keys) -> np.ndarray:
-    return np.ascontiguousarray(np.asarray(keys, dtype=np.int32))
-
-
-def plast_ungapped_keys(b1: Bank, b2: Bank, keys, params: plast_params | None = None, cap: int | None = None,
-                        stream=None) -> torch.Tensor:
-    """plast_ungapped over the subset-seed keys ``keys`` only (host list)."""
-    k = _keys_host(keys)
+def plast_ungapped_ex(b1: Bank, b2: Bank, params: plast_params | None = None, s0: int = 0, keys=None,
+                      cap: int | None = None, stream=None) -> torch.Tensor:
+    """plast_ungapped with Section 4.2's filter threshold ``s0`` (0 = off) and
+    an optional host list of subset-seed ``keys`` (None = every key)."""
+    k, kp, nk = _keys_arg(keys)
     if cap is None:
         cap = 1 << 20
     for _ in range(2):
         buf = _records(None, cap, HIT_BYTES)
         n = ctypes.c_int64()
-        rc = lib().plast_ungapped_keys(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
-                                       k.ctypes.data_as(ctypes.c_void_p), len(k), _ptr(buf), cap, ctypes.byref(n),
-                                       _stream(stream))
+        rc = lib().plast_ungapped_ex(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                     int(s0), kp, nk, _ptr(buf), cap, ctypes.byref(n), _stream(stream))
         if rc == PLAST_E_CAPACITY:
             cap = n.value
             continue
         if rc:
-            raise PlastError("plast_ungapped_keys", rc, n.value)
+            raise PlastError("plast_ungapped_ex", rc, n.value)
         return buf[: n.value * HIT_BYTES].view(-1, HIT_BYTES)
-    raise PlastError("plast_ungapped_keys", PLAST_E_CAPACITY, cap)
-
-
-def plast_search_keys(b1: Bank, b2: Bank, keys, params: plast_params | None = None, cap: int | None = None,
-                      stream=None):
-    """plast_search over the subset-seed keys ``keys`` only: (records, stage-2 hits)."""
-    k = _keys_host(keys)
-    if cap is None:
-        cap = 1 << 20
-    for _ in range(2):
-        buf = _records(None, cap, GAPPED_BYTES)
-        n, nu = ctypes.c_int64(), ctypes.c_int64()
-        rc = lib().plast_search_keys(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
-                                     k.ctypes.data_as(ctypes.c_void_p), len(k), _ptr(buf), cap, ctypes.byref(n),
-                                     ctypes.byref(nu), _stream(stream))
-        if rc == PLAST_E_CAPACITY:
-            cap = n.value
-            continue
-        if rc:
-            raise PlastError("plast_search_keys", rc, n.value)
-        return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES), nu.value
-    raise PlastError("plast_search_keys", PLAST_E_CAPACITY, cap)
+    raise PlastError("plast_ungapped_ex", PLAST_E_CAPACITY, cap)
 
 
 def plast_translate6(dna: torch.Tensor, contig_off: torch.Tensor, stream=None):

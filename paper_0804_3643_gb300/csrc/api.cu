@@ -117,19 +117,6 @@ struct Scratch {
   }
 };
 
-bool params_ok(const plast_params* p) {
-  if (!p) return true;
-  return p->w == 4 && p->nl == LEFT && p->nr == RIGHT - 4 && p->lg == LG && p->band == BAND && p->gap_open >= 0 &&
-         p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 400 && p->s1 >= -30000 &&
-         p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000 && p->s0 >= 0 && p->s0 <= 30000;
-}
-
-plast_params resolve(const plast_params* p) {
-  plast_params d;
-  plast_default_params(&d);
-  return p ? *p : d;
-}
-
 int bits_for(int64_t v) {
   int b = 1;
   while (b < 62 && ((int64_t)1 << b) <= v) b++;
@@ -470,8 +457,8 @@ struct Survivors {
 
 // Stage 2 into scratch; the survivors come back in canonical (key) order
 // when `sort`, else in the order the kernel wrote them.
-int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, cudaStream_t st, Scratch& sc,
-                 Survivors* sv, const std::vector<char>* key_mask = nullptr, bool sort = true) {
+int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params& prm, int32_t s0, cudaStream_t st,
+                 Scratch& sc, Survivors* sv, const std::vector<char>* key_mask = nullptr, bool sort = true) {
   NvtxRange nvtx_("stage 2: tiles, ungapped kernels, survivors");
   sv->n = 0;
   sv->sh = b2->pad_bits;
@@ -525,14 +512,14 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
       cap = (int64_t)n + 1024;
       continue;
     }
-    if (prm.s0 > 0 && n > 0) {
+    if (s0 > 0 && n > 0) {
       // Section 4.2's filter on the survivors
       uint64_t* kf;
       uint32_t* vf;
       CK(sc.get(&kf, (int64_t)n));
       CK(sc.get(&vf, (int64_t)n));
       CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
-      CK(launch_filter_gate(k0, v0, (int64_t)n, nullptr, sv->sh, b1->pad, b2->pad, prm.s0, kf, vf, d_count, st));
+      CK(launch_filter_gate(k0, v0, (int64_t)n, nullptr, sv->sh, b1->pad, b2->pad, s0, kf, vf, d_count, st));
       CK(cudaMemcpyAsync(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       sc.release(k0);
@@ -584,7 +571,6 @@ void plast_default_params(plast_params* p) {
   p->gap_open = 11;
   p->gap_extend = 1;
   p->s2 = 47;
-  p->s0 = 0;
 }
 
 const char* plast_strerror(int code) {
@@ -770,26 +756,35 @@ int plast_bank_export_index(const plast_bank* b, int64_t* key_off, int32_t* pos,
   return PLAST_OK;
 }
 
-static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
                          const std::vector<char>* mask, plast_hit* out, int64_t cap, int64_t* n_out, void* stream);
+
+// Key list -> mask (NULL: every key); false on a key outside 0..8799.
+static bool key_mask(const int32_t* keys, int32_t n_keys, std::vector<char>* mask) {
+  if (!keys) return true;
+  mask->assign(NKEYS, 0);
+  for (int32_t i = 0; i < n_keys; i++) {
+    if (keys[i] < 0 || keys[i] >= NKEYS) return false;
+    (*mask)[keys[i]] = 1;
+  }
+  return true;
+}
 
 int plast_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_hit* out,
                    int64_t cap, int64_t* n_out, void* stream) {
-  return ungapped_impl(b1, b2, params, nullptr, out, cap, n_out, stream);
+  return ungapped_impl(b1, b2, params, 0, nullptr, out, cap, n_out, stream);
 }
 
-int plast_ungapped_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
-                        int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out, void* stream) {
-  if ((!keys && n_keys != 0) || n_keys < 0) return PLAST_E_INVALID;
-  std::vector<char> mask(NKEYS, 0);
-  for (int32_t i = 0; i < n_keys; i++) {
-    if (keys[i] < 0 || keys[i] >= NKEYS) return PLAST_E_INVALID;
-    mask[keys[i]] = 1;
-  }
-  return ungapped_impl(b1, b2, params, &mask, out, cap, n_out, stream);
+int plast_ungapped_ex(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                      const int32_t* keys, int32_t n_keys, plast_hit* out, int64_t cap, int64_t* n_out,
+                      void* stream) {
+  if (n_keys < 0 || !s0_ok(s0)) return PLAST_E_INVALID;
+  std::vector<char> mask;
+  if (!key_mask(keys, n_keys, &mask)) return PLAST_E_INVALID;
+  return ungapped_impl(b1, b2, params, s0, keys ? &mask : nullptr, out, cap, n_out, stream);
 }
 
-static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params,
+static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
                          const std::vector<char>* mask, plast_hit* out, int64_t cap, int64_t* n_out, void* stream) {
   NvtxRange nvtx_("plast_ungapped (stages 1-2)");
   if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
@@ -802,7 +797,7 @@ static int ungapped_impl(const plast_bank* b1, const plast_bank* b2, const plast
   t_timer.reset();
   Scratch sc(st);
   Survivors sv;
-  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, mask);
+  int rc = run_ungapped(b1, b2, prm, s0, st, sc, &sv, mask);
   if (rc) return rc;
   *n_out = sv.n;
   if (sv.n > cap) return PLAST_E_CAPACITY;
@@ -948,20 +943,13 @@ int plast_small_gapped(const plast_bank* b1, const plast_bank* b2, const plast_p
   return run_gapped(b1, b2, prm, key, val, n_in, sh, out, cap, n_out, st, sc);
 }
 
-static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
-                       int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
-                       void* stream) {
+static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                       const int32_t* keys, int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out,
+                       int64_t* n_ungapped_out, void* stream) {
   NvtxRange nvtx_("plast_search");
-  if (!b1 || !b2 || !n_out || cap < 0 || !params_ok(params)) return PLAST_E_INVALID;
+  if (!b1 || !b2 || !n_out || cap < 0 || n_keys < 0 || !params_ok(params) || !s0_ok(s0)) return PLAST_E_INVALID;
   std::vector<char> mask;
-  if (keys) {
-    if (n_keys < 0) return PLAST_E_INVALID;
-    mask.assign(NKEYS, 0);
-    for (int32_t i = 0; i < n_keys; i++) {
-      if (keys[i] < 0 || keys[i] >= NKEYS) return PLAST_E_INVALID;
-      mask[keys[i]] = 1;
-    }
-  }
+  if (!key_mask(keys, n_keys, &mask)) return PLAST_E_INVALID;
   const plast_params prm = resolve(params);
   cudaStream_t st = (cudaStream_t)stream;
   CK(bank_wait(b1, st));
@@ -972,24 +960,21 @@ static int search_impl(const plast_bank* b1, const plast_bank* b2, const plast_p
   t_timer.reset();
   Scratch sc(st);
   Survivors sv;
-  int rc = run_ungapped(b1, b2, prm, st, sc, &sv, keys ? &mask : nullptr, false);
+  int rc = run_ungapped(b1, b2, prm, s0, st, sc, &sv, keys ? &mask : nullptr, false);
   if (rc) return rc;
   if (n_ungapped_out) *n_ungapped_out = sv.n;
   return run_gapped_search(b1, b2, prm, sv, out, cap, n_out, st, sc);
 }
 
 int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params* params, plast_gapped* out,
-                 int64_t cap, int64_t* n_out, int64_t* n_ungapped_out, void* stream) {
-  return search_impl(b1, b2, params, nullptr, 0, out, cap, n_out, n_ungapped_out, stream);
+                 int64_t cap, int64_t* n_out, void* stream) {
+  return search_impl(b1, b2, params, 0, nullptr, 0, out, cap, n_out, nullptr, stream);
 }
 
-int plast_search_keys(const plast_bank* b1, const plast_bank* b2, const plast_params* params, const int32_t* keys,
-                      int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out, int64_t* n_ungapped_out,
-                      void* stream) {
-  if (!keys && n_keys != 0) return PLAST_E_INVALID;
-  static const int32_t none = 0;
-  return search_impl(b1, b2, params, keys ? keys : &none, keys ? n_keys : 0, out, cap, n_out, n_ungapped_out,
-                     stream);
+int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                    const int32_t* keys, int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out,
+                    int64_t* n_ungapped_out, void* stream) {
+  return search_impl(b1, b2, params, s0, keys, n_keys, out, cap, n_out, n_ungapped_out, stream);
 }
 
 int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,
@@ -1053,6 +1038,7 @@ struct plast_plan {
   const plast_bank* b1 = nullptr;
   const plast_bank* b2 = nullptr;
   plast_params prm{};
+  int32_t s0 = 0;  // Section 4.2's filter threshold (0: off)
   int device = 0;
   int64_t max_hits = 0, max_records = 0, n_tiles = 0;
   TileList tl;  // host copy of the work list (launch split)
@@ -1094,9 +1080,10 @@ void plast_plan_free(plast_plan* p) {
   delete p;
 }
 
-int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int64_t max_hits,
-                      plast_gapped* records, int64_t max_records, void* stream, plast_plan** out) {
-  if (!b1 || !b2 || !out || !records || max_hits < 1 || max_records < 1 || !params_ok(params))
+int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
+                      int64_t max_hits, plast_gapped* records, int64_t max_records, void* stream,
+                      plast_plan** out) {
+  if (!b1 || !b2 || !out || !records || max_hits < 1 || max_records < 1 || !params_ok(params) || !s0_ok(s0))
     return PLAST_E_INVALID;
   if (max_hits > (int64_t)UINT32_MAX) return PLAST_E_INVALID;
   max_records = std::min(max_records, max_hits);  // a search never has more records than hits
@@ -1112,6 +1099,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
   p->b1 = b1;
   p->b2 = b2;
   p->prm = resolve(params);
+  p->s0 = s0;
   p->max_hits = max_hits;
   p->max_records = max_records;
   p->out = records;
@@ -1139,7 +1127,7 @@ int plast_plan_create(const plast_bank* b1, const plast_bank* b2, const plast_pa
       (e = alloc((void**)&p->pass, 4 * (size_t)max_hits)) ||
       (e = alloc((void**)&p->total, sizeof(unsigned long long))))
     return fail(e);
-  if (p->prm.s0 > 0 &&
+  if (p->s0 > 0 &&
       ((e = alloc((void**)&p->kf, 8 * (size_t)max_hits)) || (e = alloc((void**)&p->vf, 4 * (size_t)max_hits)) ||
        (e = alloc((void**)&p->count_f, sizeof(unsigned long long)))))
     return fail(e);
@@ -1186,10 +1174,10 @@ int plast_plan_run(plast_plan* p, void* stream) {
     CK(launch_tiles(p->tl, a, p->counter, true, st));
   }
   CK(launch_clamp_count(p->count, p->max_hits, p->n_dev, st));
-  const bool filter = p->prm.s0 > 0;
+  const bool filter = p->s0 > 0;
   if (filter) {
     CK(cudaMemsetAsync(p->count_f, 0, sizeof(unsigned long long), st));
-    CK(launch_filter_gate(p->k0, p->v0, p->max_hits, p->n_dev, p->sh, p->b1->pad, p->b2->pad, p->prm.s0, p->kf,
+    CK(launch_filter_gate(p->k0, p->v0, p->max_hits, p->n_dev, p->sh, p->b1->pad, p->b2->pad, p->s0, p->kf,
                           p->vf, p->count_f, st));
     CK(launch_clamp_count(p->count_f, p->max_hits, p->n_dev, st));
   }

@@ -101,6 +101,26 @@ __device__ __forceinline__ uint32_t lds_u8(uint32_t saddr) {
   return v;
 }
 
+// Host: the parameter checks every entry point applies (NULL = defaults).
+// The kernels fix w, the window, LG and the band; gap costs are bounded so
+// that the small gapped extension's offset rows stay inside int16.
+inline bool params_ok(const plast_params* p) {
+  if (!p) return true;
+  return p->w == 4 && p->nl == LEFT && p->nr == RIGHT - 4 && p->lg == LG && p->band == BAND && p->gap_open >= 0 &&
+         p->gap_extend >= 0 && p->gap_open <= 1000 && p->gap_extend <= 400 && p->s1 >= -30000 &&
+         p->s1 <= 30000 && p->s2 >= -30000 && p->s2 <= 30000;
+}
+
+// Host: the parameters a call runs with (the defaults for NULL).
+inline plast_params resolve(const plast_params* p) {
+  plast_params d;
+  plast_default_params(&d);
+  return p ? *p : d;
+}
+
+// Host: range of Section 4.2's filter threshold (0 = no filter).
+inline bool s0_ok(int32_t s0) { return s0 >= 0 && s0 <= 30000; }
+
 __device__ __forceinline__ int seed_key(int a0, int a1, int a2, int a3) {
   // Key = ((c1 * 2 + c2) * 11 + c3) * 20 + c4; -1 when a letter is a stop or
   // the sentinel.

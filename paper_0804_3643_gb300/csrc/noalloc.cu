@@ -45,7 +45,8 @@ static_assert(SCRATCH_BYTES <= (size_t)PLAST_NOALLOC_SCRATCH_BYTES, "scratch lay
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PLAST_NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch, looked up once per device with that
-// device current.
+// device current and kept for the life of the process (a device reset, which
+// gives the device a new context, invalidates it; the header says so).
 unsigned char* scratch_on_current_device(cudaError_t* err) {
   static std::mutex mu;
   static unsigned char* addr[64] = {nullptr};
@@ -82,13 +83,9 @@ extern "C" int plast_small_gapped_noalloc(const plast_bank* b1, const plast_bank
   if (!b1 || !b2 || !n_out || n_in < 0 || cap < 0) return PLAST_E_INVALID;
   if (n_in > NMAX) return PLAST_E_INVALID;
   if (n_in > 0 && !in) return PLAST_E_INVALID;
-  plast_params prm;
-  plast_default_params(&prm);
-  if (params) prm = *params;
-  if (prm.w != 4 || prm.nl != LEFT || prm.nr != RIGHT - 4 || prm.lg != LG || prm.band != BAND ||
-      prm.gap_open < 0 || prm.gap_extend < 0 || prm.gap_open > 1000 || prm.gap_extend > 400 ||
-      prm.s2 < -30000 || prm.s2 > 30000)
-    return PLAST_E_INVALID;
+  // the same parameter checks as plast_small_gapped
+  if (!params_ok(params)) return PLAST_E_INVALID;
+  const plast_params prm = resolve(params);
   *n_out = 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (bank_wait(b1, st) != cudaSuccess || bank_wait(b2, st) != cudaSuccess) return PLAST_E_CUDA;

@@ -392,6 +392,10 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
   constexpr int NQ = NW >= 2 ? NW / 2 : 1;  // 4-row words per (cell, residue)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint4 sent16 = make_uint4(0x15151515u, 0x15151515u, 0x15151515u, 0x15151515u);
+  // only the first 4 * NQ bytes of each cell's row slot are written here; the
+  // rest of the slot (up to NR_MAX) may hold a previous, larger tile's rows,
+  // which the profile build below reads with its 16-byte load but never uses
+  // (it takes the words sx[q], q < NQ, only)
   for (int i = tid; i < WIN * 4 * NQ; i += NT_THREADS) {
     const int r = i % (4 * NQ), k = i / (4 * NQ);
     nrows[k * NR_MAX + r] = r < rows ? (uint8_t)a.nb1[(u0 + r) * WIN + k] : (uint8_t)SENTINEL;

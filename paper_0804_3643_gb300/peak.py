@@ -5,7 +5,9 @@ current GPU; prints one JSON line per instruction kind.
 
 Under ncu, with --metrics sm__inst_executed_pipe_alu.sum,
 sm__inst_executed_pipe_fmaheavy.sum,smsp__inst_executed.sum, it shows on which
-pipe each kind issues; the stage-2 roofline in the design doc rests on that split.
+pipe each kind issues: integer maxima on the ALU pipe, int16x2 adds and IMAD
+on the FMA-heavy pipe, each about 64 lanes per clock per SM.  The integer
+rooflines bench.py reports (stage 2 and stage 3.1) rest on that split.
 """
 import os
 import subprocess

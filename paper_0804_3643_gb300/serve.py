@@ -243,7 +243,7 @@ class GpuExecutor:
             do = ho.to(self.device, non_blocking=True)
             q = B.plast_index_bank(dc, do, self.params, stream=st)
             pairs = B.plast_pair_count(q, self.bank)
-            recs, _ = B.plast_search(q, self.bank, self.params, stream=st)
+            recs = B.plast_search(q, self.bank, self.params, stream=st)
             host = B.gapped_numpy(recs)
             q.free()
         return split_records(host, first), pairs

@@ -7,8 +7,8 @@
   device;
 * serving: a 1,000,000-protein resident bank against a 250-protein query.
 
-Each comparison runs the GPU on a random sample of keys (plast_*_keys, the
-per-key decomposition of Section 5.1) and requires the records to equal the
+Each comparison runs the GPU on a random sample of keys (plast_ungapped_ex /
+plast_search_ex with a key list, the per-key decomposition of Section 5.1) and requires the records to equal the
 oracle's stages 1-3.1 over the same keys byte for byte.  The six-frame
 translation is compared in full.
 """
@@ -48,10 +48,11 @@ def sample_keys(o1, o2, rng, n, lo=10 ** 4, hi=4 * 10 ** 6, budget=6 * 10 ** 7):
 
 def check_keys(B, g1, g2, o1, o2, keys):
     want_h = oracle.ungapped(o1, o2, keys=keys, threads=16)
-    got_h = B.hits_numpy(B.plast_ungapped_keys(g1, g2, keys))
+    got_h = B.hits_numpy(B.plast_ungapped_ex(g1, g2, keys=keys))
     assert np.array_equal(got_h.view(np.uint8), want_h.view(np.uint8))
-    want_g = oracle.small_gapped(o1, o2, want_h)
-    recs, n_ung = B.plast_search_keys(g1, g2, keys)
+    del got_h
+    want_g = oracle.small_gapped(o1, o2, want_h, threads=16)
+    recs, n_ung = B.plast_search_ex(g1, g2, keys=keys)
     assert n_ung == len(want_h)
     assert np.array_equal(B.gapped_numpy(recs).view(np.uint8), want_g.view(np.uint8))
     return len(want_h), len(want_g)
@@ -67,19 +68,23 @@ def test_batching_stress_full_size(B):
     o2 = oracle.make_bank(b2.codes, b2.seq_off)
     assert B.plast_pair_count(g1, g2) > 5 * 10 ** 10
     keys, pairs = sample_keys(o1, o2, np.random.default_rng(31), 40)
-    # low-complexity keys: the largest lists with up to 2e7 pairs
+    # low-complexity keys: the three with the most pairs (about 2e8 each, up
+    # to 45 million stage-2 hits per key), the lists the persistent queue cuts
+    # across tiles and CTAs, plus three with 4e6 to 2e7 pairs
     pp = np.diff(o1.idx.key_off) * np.diff(o2.idx.key_off)
-    heavy = np.argsort(pp)[::-1]
-    heavy = heavy[(pp[heavy] > 4 * 10 ** 6) & (pp[heavy] < 2 * 10 ** 7)][:3]
-    keys = np.unique(np.concatenate([keys, heavy.astype(np.int32)]))
+    order = np.argsort(pp)[::-1]
+    top = order[:3]
+    assert pp[top].min() > 10 ** 8
+    mid = order[(pp[order] > 4 * 10 ** 6) & (pp[order] < 2 * 10 ** 7)][:3]
+    keys = np.unique(np.concatenate([keys, top.astype(np.int32), mid.astype(np.int32)]))
     nh, ng = check_keys(B, g1, g2, o1, o2, keys)
-    assert nh > 1000 and ng > 100
+    assert nh > 10 ** 7 and ng > 10 ** 6
     try:
         B.plast_set_schedule(1)
-        r1, _ = B.plast_search_keys(g1, g2, keys)
+        r1, _ = B.plast_search_ex(g1, g2, keys=keys)
     finally:
         B.plast_set_schedule(0)
-    r0, _ = B.plast_search_keys(g1, g2, keys)
+    r0, _ = B.plast_search_ex(g1, g2, keys=keys)
     assert np.array_equal(r0.cpu().numpy(), r1.cpu().numpy())
 
 

@@ -36,7 +36,7 @@ def full():
     g1 = B.plast_index_bank(d1.codes, d1.seq_off)
     g2 = B.plast_index_bank(d2.codes, d2.seq_off)
     hits = B.hits_numpy(B.plast_ungapped(g1, g2))
-    recs_t, n_ung = B.plast_search(g1, g2)
+    recs_t, n_ung = B.plast_search_ex(g1, g2)
     recs = B.gapped_numpy(recs_t)
     o1 = oracle.make_bank(b1.codes, b1.seq_off)
     o2 = oracle.make_bank(b2.codes, b2.seq_off)
@@ -89,7 +89,7 @@ def test_fullsize_sampled_keys_bit_exact(full):
     got_h = hits[np.isin(hkeys, sample)]
     assert len(want_h) > 1000
     assert np.array_equal(got_h.view(np.uint8), want_h.view(np.uint8))
-    want_g = oracle.small_gapped(o1, o2, want_h)
+    want_g = oracle.small_gapped(o1, o2, want_h, threads=16)
     rkeys = keys_of(o1, recs["seq1"], recs["pos1"])
     got_g = recs[np.isin(rkeys, sample)]
     assert np.array_equal(got_g.view(np.uint8), want_g.view(np.uint8))
@@ -111,7 +111,7 @@ def test_fullsize_schedules_agree(full):
     B, g1, g2, o1, o2, hits, recs, n_ung = full
     try:
         B.plast_set_schedule(1)
-        r1, n1 = B.plast_search(g1, g2)
+        r1, n1 = B.plast_search_ex(g1, g2)
     finally:
         B.plast_set_schedule(0)
     assert n1 == n_ung

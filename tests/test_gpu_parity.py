@@ -93,7 +93,7 @@ def test_ungapped_parity_plain(B, plain):
 
 def test_search_parity_plain(B, plain):
     g1, o1, g2, o2 = plain
-    recs, n_ung = B.plast_search(g1, g2)
+    recs, n_ung = B.plast_search_ex(g1, g2)
     want_h = oracle.ungapped(o1, o2)
     want = oracle.small_gapped(o1, o2, want_h)
     assert n_ung == len(want_h)
@@ -119,7 +119,7 @@ def test_thresholds_and_gap_costs(B, plain):
                            (38, 40, 1000, 1), (38, 40, 7, 400)]:
         prm = oracle.Params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
         gp = B.plast_default_params(s1=s1, s2=s2, gap_open=go, gap_extend=ge)
-        recs, n_ung = B.plast_search(g1, g2, gp)
+        recs, n_ung = B.plast_search_ex(g1, g2, gp)
         want_h = oracle.ungapped(o1, o2, prm)
         assert n_ung == len(want_h)
         assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h, prm))
@@ -158,7 +158,7 @@ def test_identical_banks_every_pair_passes(B):
     got = B.hits_numpy(B.plast_ungapped(g, g, B.plast_default_params(s1=0)))
     assert len(want) == oracle.ungapped(ob, ob, prm, return_pairs=True)[1]
     assert same(got, want)
-    recs, _ = B.plast_search(g, g, B.plast_default_params(s1=0, s2=-10 ** 4))
+    recs, _ = B.plast_search_ex(g, g, B.plast_default_params(s1=0, s2=-10 ** 4))
     assert same(B.gapped_numpy(recs), oracle.small_gapped(ob, ob, want, prm))
 
 
@@ -169,7 +169,7 @@ def test_low_complexity_workload(B):
     want = oracle.ungapped(o1, o2, threads=8)
     got = B.hits_numpy(B.plast_ungapped(g1, g2))
     assert same(got, want)
-    recs, _ = B.plast_search(g1, g2)
+    recs, _ = B.plast_search_ex(g1, g2)
     assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want))
 
 
@@ -213,7 +213,7 @@ def test_tplastn_parity_small(B):
     got = B.hits_numpy(B.plast_ungapped(g1, g2))
     assert len(want) > 0
     assert same(got, want)
-    recs, _ = B.plast_search(g1, g2)
+    recs, _ = B.plast_search_ex(g1, g2)
     assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want))
 
 
@@ -262,7 +262,7 @@ def test_allocation_failure_injection(B, plain):
     # memory; every call reports PLAST_E_OOM, frees what it took, and the
     # library works again once the limit is lifted
     g1, o1, g2, o2 = plain
-    want, n_want = B.plast_search(g1, g2)
+    want, n_want = B.plast_search_ex(g1, g2)
     b1, _ = synth.workload("plastp_plain", seed=1)
     d1 = B.DeviceBank.from_host(b1.codes, b1.seq_off)
     try:
@@ -275,7 +275,7 @@ def test_allocation_failure_injection(B, plain):
             assert e.value.code == B.PLAST_E_OOM
     finally:
         B.plast_set_alloc_limit(0)
-    got, n_got = B.plast_search(g1, g2)
+    got, n_got = B.plast_search_ex(g1, g2)
     assert n_got == n_want and torch.equal(got, want)
     g3 = B.plast_index_bank(d1.codes, d1.seq_off)
     check_index(B, g3, o1)
@@ -295,7 +295,7 @@ def test_bank_built_on_another_stream(B):
     for _ in range(3):
         g1 = B.plast_index_bank(d1.codes, d1.seq_off, stream=side)
         g2 = B.plast_index_bank(d2.codes, d2.seq_off, stream=side)
-        recs, _ = B.plast_search(g1, g2)  # current stream
+        recs, _ = B.plast_search_ex(g1, g2)  # current stream
         assert same(B.gapped_numpy(recs), want)
         g3 = B.plast_index_bank(d2.codes, d2.seq_off, stream=side)
         g3.free()
@@ -307,20 +307,22 @@ def test_s0_filter(B, plain):
     g1, o1, g2, o2 = plain
     full = oracle.ungapped(o1, o2, threads=8)
     for s0 in (B.PLAST_FILTER_S0, 70):
-        prm = B.plast_default_params(s0=s0)
         want_h = oracle.ungapped(o1, o2, oracle.Params(s0=s0), threads=8)
         assert 100 < len(want_h) < len(full)
-        assert same(B.hits_numpy(B.plast_ungapped(g1, g2, prm)), want_h)
-        recs, n_ung = B.plast_search(g1, g2, prm)
+        assert same(B.hits_numpy(B.plast_ungapped_ex(g1, g2, s0=s0)), want_h)
+        recs, n_ung = B.plast_search_ex(g1, g2, s0=s0)
         assert n_ung == len(want_h)
         assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h))
         keys = np.arange(0, B.NKEYS, 7, dtype=np.int32)
         want_k = oracle.ungapped(o1, o2, oracle.Params(s0=s0), keys=keys, threads=8)
-        assert same(B.hits_numpy(B.plast_ungapped_keys(g1, g2, keys, prm)), want_k)
+        assert same(B.hits_numpy(B.plast_ungapped_ex(g1, g2, s0=s0, keys=keys)), want_k)
     # a filter at or below S1 removes nothing (U <= F)
-    assert same(B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s0=38))), full)
-    with pytest.raises(B.PlastError):
-        B.plast_ungapped(g1, g2, B.plast_default_params(s0=-1))
+    assert same(B.hits_numpy(B.plast_ungapped_ex(g1, g2, s0=38)), full)
+    for bad in (-1, 30001):
+        with pytest.raises(B.PlastError):
+            B.plast_ungapped_ex(g1, g2, s0=bad)
+        with pytest.raises(B.PlastError):
+            B.plast_search_ex(g1, g2, s0=bad)
 
 
 def test_plastx_both_translated(B):
@@ -336,7 +338,7 @@ def test_plastx_both_translated(B):
     want_h = oracle.ungapped(want[0], want[1], threads=8)
     assert len(want_h) > 1000
     assert same(B.hits_numpy(B.plast_ungapped(got[0], got[1])), want_h)
-    recs, n_ung = B.plast_search(got[0], got[1])
+    recs, n_ung = B.plast_search_ex(got[0], got[1])
     assert n_ung == len(want_h)
     assert same(B.gapped_numpy(recs), oracle.small_gapped(want[0], want[1], want_h))
 
@@ -354,6 +356,6 @@ def test_plastx_translated_queries(B):
     want_h = oracle.ungapped(oq, op, threads=8)
     assert len(want_h) > 0
     assert same(B.hits_numpy(B.plast_ungapped(gq, gp)), want_h)
-    recs, n_ung = B.plast_search(gq, gp)
+    recs, n_ung = B.plast_search_ex(gq, gp)
     assert n_ung == len(want_h)
     assert same(B.gapped_numpy(recs), oracle.small_gapped(oq, op, want_h))

@@ -46,7 +46,7 @@ def test_plan_run_and_graph_replay(B, banks):
     assert nu == n_hits
     got = B.gapped_numpy(recs)
     assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
-    ref, nu2 = B.plast_search(g1, g2)
+    ref, nu2 = B.plast_search_ex(g1, g2)
     assert nu2 == n_hits and torch.equal(ref, recs)
 
     st = torch.cuda.Stream()
@@ -92,8 +92,7 @@ def test_plan_with_filter(B, banks):
     hits = oracle.ungapped(o1, o2, prm_o, threads=16)
     want = oracle.small_gapped(o1, o2, hits)
     assert 0 < len(hits) < n_hits
-    prm = B.plast_default_params(s0=B.PLAST_FILTER_S0)
-    plan = B.Plan(g1, g2, max_hits=n_hits + 100, max_records=len(want) + 100, params=prm)
+    plan = B.Plan(g1, g2, max_hits=n_hits + 100, max_records=len(want) + 100, s0=B.PLAST_FILTER_S0)
     plan.run()
     recs, nu = plan.result()
     assert nu == len(hits)

@@ -58,7 +58,7 @@ def test_shapes_plain(B):
     assert len(want_h) > 500
     for h in each_shape(B, lambda: B.hits_numpy(B.plast_ungapped(g1, g2))):
         assert same(h, want_h)
-    for r, n in each_shape(B, lambda: B.plast_search(g1, g2)):
+    for r, n in each_shape(B, lambda: B.plast_search_ex(g1, g2)):
         assert n == len(want_h) and same(B.gapped_numpy(r), want)
 
 
@@ -81,7 +81,7 @@ def test_small_query_large_bank(B):
     assert len(want) > 20
     for h in each_shape(B, lambda: B.hits_numpy(B.plast_ungapped(gq, gb))):
         assert same(h, want_h)
-    for r, n in each_shape(B, lambda: B.plast_search(gq, gb)):
+    for r, n in each_shape(B, lambda: B.plast_search_ex(gq, gb)):
         assert n == len(want_h) and same(B.gapped_numpy(r), want)
     # the query as bank 2: wide rows from the large bank, few windows per key
     want_sw = oracle.ungapped(ob, oq, threads=16)
@@ -112,7 +112,7 @@ def test_wide_tiles_cut(B):
     assert len(want_h) > 100
     for h in each_shape(B, lambda: B.hits_numpy(B.plast_ungapped(gq, gb))):
         assert same(h, want_h)
-    for r, n in each_shape(B, lambda: B.plast_search(gq, gb)):
+    for r, n in each_shape(B, lambda: B.plast_search_ex(gq, gb)):
         assert n == len(want_h) and same(B.gapped_numpy(r), want)
 
 

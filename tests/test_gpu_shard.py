@@ -24,7 +24,7 @@ def test_sharded_search_merges_to_the_full_search():
     def search(codes, seq_off):
         d = B.DeviceBank.from_host(codes, seq_off)
         g = B.plast_index_bank(d.codes, d.seq_off)
-        recs, _ = B.plast_search(g1, g)
+        recs, _ = B.plast_search_ex(g1, g)
         return B.gapped_numpy(recs).copy()
 
     full = search(b2.codes, b2.seq_off)

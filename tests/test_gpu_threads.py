@@ -82,7 +82,7 @@ def test_concurrent_index_and_search(B):
             res = []
             for _ in range(3):
                 h = B.hits_numpy(B.plast_ungapped(g[i], g[j], stream=s))
-                r, n = B.plast_search(g[i], g[j], stream=s)
+                r, n = B.plast_search_ex(g[i], g[j], stream=s)
                 res.append((h, B.gapped_numpy(r), n))
             return res
         return f

@@ -112,3 +112,15 @@ def test_threshold_filter(plain_hits):
     allg = oracle.small_gapped(B1, B2, hits, oracle.Params(s2=-10 ** 6))
     kept = oracle.small_gapped(B1, B2, hits, oracle.Params(s2=47))
     assert (kept == allg[allg["score"] >= 47]).all()
+
+
+def test_threads_equal_one_thread(plain_hits):
+    # the hits cut into ranges over several threads give the same records in
+    # the same (input) order as one thread
+    B1, B2, hits = plain_hits
+    many = np.concatenate([hits] * 8)
+    one = oracle.small_gapped(B1, B2, many, oracle.Params(s2=30))
+    assert len(one) > 0
+    for th in (2, 3, 8):
+        assert np.array_equal(oracle.small_gapped(B1, B2, many, oracle.Params(s2=30), threads=th).view(np.uint8),
+                              one.view(np.uint8))
