@@ -34,6 +34,15 @@ GAPPED_DTYPE = np.dtype(
      ("score", "<i2"), ("ungapped", "<i2"), ("r_i", "<i2"), ("r_j", "<i2"),
      ("l_i", "<i2"), ("l_j", "<i2")])
 assert HIT_DTYPE.itemsize == 20 and GAPPED_DTYPE.itemsize == 28
+ALIGN_FIELDS = ("seq1", "seq2", "pos1", "pos2", "score", "q_start", "q_end", "s_start", "s_end", "length",
+                "identities", "mismatches", "gap_opens")
+ALIGN_DTYPE = np.dtype([(n, "<i4") for n in ALIGN_FIELDS])
+
+# Stage 3.2 defaults (readings: the paper values neither): X = 38, BLAST's
+# preliminary gapped drop-off of 15 bits at BLOSUM62 11/1's gapped lambda
+# 0.267; S3 = S2 (E-values are out of scope).
+XDROP = 38
+S3 = 47
 
 
 class _Params(ctypes.Structure):
@@ -103,6 +112,12 @@ def lib() -> ctypes.CDLL:
         L.oracle_ungapped.argtypes = [P, P, i32, P, P, P, P, i32, P, P, P, i32, i32, P, i32, P, P, P]
         L.oracle_ungapped.restype = i64
         L.oracle_small_gapped.argtypes = [P, P, P, P, P, P, i64, i32, P]
+        L.oracle_xdrop_side.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P, P, P, P]
+        L.oracle_xdrop_side.restype = i32
+        L.oracle_full_gapped_one.argtypes = [P, i64, i64, P, i64, i64, i32, i32, i32, P, P, i32, P]
+        L.oracle_full_gapped_one.restype = i32
+        L.oracle_full_gapped.argtypes = [P, P, P, P, i32, i32, i32, i32, P, i64, i32, P, P]
+        L.oracle_full_gapped.restype = i64
         L.oracle_small_gapped.restype = i64
         L.oracle_free.argtypes = [P]
         L.oracle_smith_waterman.argtypes = [P, i32, P, i32, i32, i32]
@@ -268,6 +283,51 @@ def small_gapped(b1: Bank, b2: Bank, hits: np.ndarray, params: Params = Params()
     res = np.frombuffer(bytes(buf), dtype=GAPPED_DTYPE).copy()
     L.oracle_free(out)
     return res
+
+
+# --------------------------------------------------------------------------
+# Stage 3.2 and the tabular fields of stage 4 (Sections 3.3.4, 3.3.5)
+# --------------------------------------------------------------------------
+def xdrop_side(A, B, go: int = 11, ge: int = 1, x: int = XDROP):
+    """(score, end_i, end_j, path) of one anchored, unbanded side with the
+    row-wise drop-off x; path is a string of M / I / D from the anchor out."""
+    a, b = _i8(A), _i8(B)
+    ei, ej, nops = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ops = ctypes.create_string_buffer(a.size + b.size + 1)
+    sc = lib().oracle_xdrop_side(_p(a), 1, a.size, _p(b), 1, b.size, go, ge, x, ctypes.byref(ei), ctypes.byref(ej),
+                                 ops, ctypes.byref(nops))
+    return sc, ei.value, ej.value, ops.raw[: nops.value].decode()
+
+
+def full_gapped_one(s1, p1: int, s2, p2: int, go: int = 11, ge: int = 1, x: int = XDROP):
+    """(alignment record, [(diagonal, start, stop), ...]) of the full gapped
+    extension anchored at seed starts p1, p2 (seq1 / seq2 fields left 0)."""
+    a, b = _i8(s1), _i8(s2)
+    al = np.zeros(1, dtype=ALIGN_DTYPE)
+    cap = a.size + b.size + 4
+    segs = np.zeros(3 * cap, dtype=np.int32)
+    nseg = ctypes.c_int32()
+    lib().oracle_full_gapped_one(_p(a), a.size, p1, _p(b), b.size, p2, go, ge, x, _p(al), _p(segs), cap,
+                                 ctypes.byref(nseg))
+    return al[0], [tuple(int(v) for v in segs[3 * k: 3 * k + 3]) for k in range(nseg.value)]
+
+
+def full_gapped(b1: Bank, b2: Bank, records: np.ndarray, params: Params = Params(), x: int = XDROP, s3: int = S3,
+                threads: int = 1, return_extended: bool = False):
+    """Stage 3.2 of stage-3.1 records (any order) with the redundancy lists:
+    alignments scoring >= s3, sorted by (seq1, pos1, seq2, pos2) of their
+    anchors; ``return_extended`` adds how many records were extended."""
+    recs = np.ascontiguousarray(records, dtype=GAPPED_DTYPE)
+    out = ctypes.c_void_p()
+    ext = ctypes.c_int64()
+    L = lib()
+    n = L.oracle_full_gapped(_p(b1.codes), _p(b1.seq_off), _p(b2.codes), _p(b2.seq_off), params.gap_open,
+                             params.gap_extend, x, s3, _p(recs) if recs.size else None, recs.size, threads,
+                             ctypes.byref(out), ctypes.byref(ext))
+    buf = (ctypes.c_char * (n * ALIGN_DTYPE.itemsize)).from_address(out.value) if n else b""
+    res = np.frombuffer(bytes(buf), dtype=ALIGN_DTYPE).copy()
+    L.oracle_free(out)
+    return (res, ext.value) if return_extended else res
 
 
 def search(b1: Bank, b2: Bank, params: Params = Params(), threads: int = 1) -> np.ndarray:

@@ -21,6 +21,10 @@
  *                                 example, brute force
  *   gapped_side / small_gapped .. band-0 reduction, Smith-Waterman bound and
  *                                 equality, single-gap closed form, symmetry
+ *   xdrop_side / full_gapped .... Smith-Waterman bound and equality (no
+ *                                 drop-off), hand-worked drop-off stops, the
+ *                                 path rescored, redundancy worked by hand,
+ *                                 input-order independence
  *   translate6 .................. genetic-code degeneracy, back-translation
  *   smith_waterman .............. textbook cases worked by hand
  *
@@ -622,6 +626,403 @@ int64_t oracle_small_gapped(const int8_t* codes1, const int64_t* seq_off1, const
   free(jobs);
   free(th);
   *out = res;
+  return n;
+}
+
+/* ------------------------------------------------------------------------
+ * Stage 3.2: full gapped extension (Section 3.3.4: a hit whose small gapped
+ * extension reaches S2 gets "the standard dynamic programming procedure";
+ * Section 2.3.3: a gapped extension stops once its score falls more than a
+ * drop-off X below the best) and the trace-back of stage 4 (Section
+ * 3.3.5) down to BLAST's tabular fields.  Readings:
+ *  - anchor, sides, gap costs and the free end are those of stage 3.1: one
+ *    extension right of the seed start (from its first residue pair) and one
+ *    left of it, Gotoh with a gap of length k costing go + k * ge, no clamp
+ *    at zero; but no band and no LG limit: a side runs to the sequence ends;
+ *  - the drop-off is taken row by row: a cell whose H is more than X below
+ *    T, the best H of all earlier rows (H(0,0) = 0 included), is dropped
+ *    (H = E = F = minus infinity), and a side ends at its first row with no
+ *    live cell;
+ *  - the side's score is the best live H, its end the first cell holding it
+ *    in row-major order;
+ *  - the trace-back from the end cell prefers, in H, the diagonal, then E
+ *    (gap in A: a B residue against nothing), then F (gap in B); in E or F it
+ *    prefers the gap's opening over its extension when both give the value.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t lo, hi;    /* columns computed in this row (hi < lo: none) */
+  int32_t *H, *E, *F; /* values of columns lo .. hi; dropped cells hold NEG_INF */
+} xd_row;
+
+static int32_t xd_get(const xd_row* r, const int32_t* v, int32_t j) {
+  return (j < r->lo || j > r->hi) ? NEG_INF : v[j - r->lo];
+}
+
+/* One anchored side.  Rows i = 1..la take A_i = A[(i-1) * astride], columns
+ * j = 1..lb take B_j = B[(j-1) * bstride].  Returns the side's score, its end
+ * cell in (*ei, *ej), and the path from (0,0) to the end cell in ops[0 ..
+ * *n_ops) from the anchor outwards: 'M' a residue pair, 'I' an A residue
+ * against a gap, 'D' a B residue against a gap (ops holds la + lb). */
+int32_t oracle_xdrop_side(const int8_t* A, int64_t astride, int32_t la, const int8_t* B, int64_t bstride, int32_t lb,
+                          int32_t go, int32_t ge, int32_t X, int32_t* ei, int32_t* ej, char* ops, int32_t* n_ops) {
+  const int32_t goe = go + ge;
+  xd_row* rows = (xd_row*)calloc((size_t)la + 1, sizeof(xd_row));
+  int32_t T = 0;       /* best H of the rows done so far */
+  int32_t best = 0, bi = 0, bj = 0;
+  int32_t last = -1;   /* last row with a live cell */
+  for (int32_t i = 0; i <= la; i++) {
+    const xd_row* up = i > 0 ? &rows[i - 1] : NULL;
+    int32_t first = 0;
+    if (up) {
+      /* live cells of the row above bound where this row's can be */
+      int32_t lo = INT32_MAX, hi = -1;
+      for (int32_t j = up->lo; j <= up->hi; j++)
+        if (up->H[j - up->lo] > NEG_INF) {
+          if (j < lo) lo = j;
+          hi = j;
+        }
+      if (hi < 0) break;
+      first = lo;
+    }
+    /* columns first .. at most lb, stopping after the row above's live cells
+     * end once a cell is dropped (nothing further right can be live) */
+    int32_t cap = lb - first + 1;
+    xd_row* r = &rows[i];
+    r->lo = first;
+    r->hi = first - 1;
+    r->H = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    r->E = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    r->F = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    int32_t up_hi = -1;
+    if (up)
+      for (int32_t j = up->lo; j <= up->hi; j++)
+        if (up->H[j - up->lo] > NEG_INF) up_hi = j;
+    int32_t row_best = NEG_INF, row_bj = -1;
+    for (int32_t j = first; j <= lb; j++) {
+      int32_t h, e = NEG_INF, f = NEG_INF, d = NEG_INF;
+      if (i == 0 && j == 0) {
+        h = 0;
+      } else {
+        if (j > first) {
+          const int32_t e1 = r->E[j - 1 - first], h1 = r->H[j - 1 - first];
+          const int32_t a = e1 > NEG_INF ? e1 - ge : NEG_INF, b = h1 > NEG_INF ? h1 - goe : NEG_INF;
+          e = a > b ? a : b;
+        }
+        if (up) {
+          const int32_t f1 = xd_get(up, up->F, j), h1 = xd_get(up, up->H, j);
+          const int32_t a = f1 > NEG_INF ? f1 - ge : NEG_INF, b = h1 > NEG_INF ? h1 - goe : NEG_INF;
+          f = a > b ? a : b;
+          const int32_t hd = j >= 1 ? xd_get(up, up->H, j - 1) : NEG_INF;
+          if (hd > NEG_INF) d = hd + B62[A[(int64_t)(i - 1) * astride]][B[(int64_t)(j - 1) * bstride]];
+        }
+        h = d;
+        if (e > h) h = e;
+        if (f > h) h = f;
+      }
+      if (h < T - X) h = e = f = NEG_INF; /* dropped */
+      r->H[j - first] = h;
+      r->E[j - first] = e;
+      r->F[j - first] = f;
+      r->hi = j;
+      if (h > row_best) {
+        row_best = h;
+        row_bj = j;
+      }
+      if (h == NEG_INF && j > up_hi) break;
+    }
+    if (row_best == NEG_INF) break; /* no live cell: the side ends */
+    last = i;
+    if (row_best > best) {
+      best = row_best;
+      bi = i;
+      bj = row_bj;
+    }
+    if (row_best > T) T = row_best;
+  }
+  /* trace-back from (bi, bj) */
+  int32_t n = 0, i = bi, j = bj;
+  int state = 0; /* 0: H, 1: E, 2: F */
+  while (i > 0 || j > 0) {
+    const xd_row* r = &rows[i];
+    if (state == 0) {
+      const int32_t h = xd_get(r, r->H, j);
+      const int32_t hd = (i >= 1 && j >= 1) ? xd_get(&rows[i - 1], rows[i - 1].H, j - 1) : NEG_INF;
+      if (hd > NEG_INF && h == hd + B62[A[(int64_t)(i - 1) * astride]][B[(int64_t)(j - 1) * bstride]]) {
+        ops[n++] = 'M';
+        i--;
+        j--;
+      } else if (h == xd_get(r, r->E, j)) {
+        state = 1;
+      } else {
+        state = 2;
+      }
+    } else if (state == 1) {
+      const int32_t e = xd_get(r, r->E, j);
+      const int32_t hl = xd_get(r, r->H, j - 1);
+      ops[n++] = 'D';
+      state = (hl > NEG_INF && e == hl - goe) ? 0 : 1;
+      j--;
+    } else {
+      const int32_t f = xd_get(r, r->F, j);
+      const int32_t hu = xd_get(&rows[i - 1], rows[i - 1].H, j);
+      ops[n++] = 'I';
+      state = (hu > NEG_INF && f == hu - goe) ? 0 : 2;
+      i--;
+    }
+  }
+  for (int32_t a = 0, b = n - 1; a < b; a++, b--) { /* anchor outwards */
+    const char t = ops[a];
+    ops[a] = ops[b];
+    ops[b] = t;
+  }
+  *n_ops = n;
+  *ei = bi;
+  *ej = bj;
+  (void)last;
+  for (int32_t k = 0; k <= la; k++) {
+    free(rows[k].H);
+    free(rows[k].E);
+    free(rows[k].F);
+  }
+  free(rows);
+  return best;
+}
+
+typedef struct {
+  int32_t seq1, seq2, pos1, pos2; /* the anchor: seed start of the hit it came from */
+  int32_t score;                  /* right side + left side */
+  int32_t q_start, q_end, s_start, s_end; /* aligned residues, 0-based, end exclusive */
+  int32_t length, identities, mismatches, gap_opens;
+} oracle_alignment;
+
+typedef struct {
+  int32_t diag, start, stop; /* an ungapped segment: pos1 - pos2, first and last pos1 */
+} xd_segment;
+
+/* Both sides of the anchor (p1, p2) of sequences s1 (len1) and s2 (len2):
+ * score and tabular fields in *al, the alignment's ungapped segments
+ * appended to *segs (growing *nseg / *capseg).  Gap runs are counted per
+ * side (a run on each side of the anchor is two openings, as scored). */
+int32_t oracle_full_gapped_pair(const int8_t* s1, int64_t len1, int64_t p1, const int8_t* s2, int64_t len2, int64_t p2,
+                                int32_t go, int32_t ge, int32_t X, oracle_alignment* al, xd_segment** segs,
+                                int32_t* nseg, int32_t* capseg) {
+  const int32_t lar = (int32_t)(len1 - p1), lbr = (int32_t)(len2 - p2);
+  const int32_t lal = (int32_t)p1, lbl = (int32_t)p2;
+  char* opr = (char*)malloc((size_t)lar + lbr + 1);
+  char* opl = (char*)malloc((size_t)lal + lbl + 1);
+  int32_t ri, rj, li, lj, nr, nl;
+  const int32_t right = oracle_xdrop_side(s1 + p1, 1, lar, s2 + p2, 1, lbr, go, ge, X, &ri, &rj, opr, &nr);
+  const int32_t left = oracle_xdrop_side(s1 + p1 - 1, -1, lal, s2 + p2 - 1, -1, lbl, go, ge, X, &li, &lj, opl, &nl);
+  al->pos1 = (int32_t)p1;
+  al->pos2 = (int32_t)p2;
+  al->score = right + left;
+  al->q_start = (int32_t)p1 - li;
+  al->q_end = (int32_t)p1 + ri;
+  al->s_start = (int32_t)p2 - lj;
+  al->s_end = (int32_t)p2 + rj;
+  al->length = nl + nr;
+  al->identities = al->mismatches = al->gap_opens = 0;
+  /* columns in sequence order: the left path reversed, then the right path */
+  int64_t x = p1 - li, y = p2 - lj;
+  int32_t in_seg = 0;
+  xd_segment cur = {0, 0, 0};
+  for (int32_t c = 0; c < nl + nr; c++) {
+    const int left_part = c < nl;
+    const char op = left_part ? opl[nl - 1 - c] : opr[c - nl];
+    const char prev = c == 0 || c == nl ? 0 : (left_part ? opl[nl - c] : opr[c - nl - 1]);
+    if (op == 'M') {
+      if (s1[x] == s2[y]) al->identities++;
+      else al->mismatches++;
+      if (in_seg && cur.diag == (int32_t)(x - y) && cur.stop == (int32_t)x - 1) {
+        cur.stop = (int32_t)x;
+      } else {
+        if (in_seg) {
+          if (*nseg == *capseg) {
+            *capseg = *capseg ? 2 * *capseg : 16;
+            *segs = (xd_segment*)realloc(*segs, sizeof(xd_segment) * (size_t)*capseg);
+          }
+          (*segs)[(*nseg)++] = cur;
+        }
+        cur.diag = (int32_t)(x - y);
+        cur.start = cur.stop = (int32_t)x;
+        in_seg = 1;
+      }
+      x++;
+      y++;
+    } else {
+      if (op != prev) al->gap_opens++; /* a new run (runs do not cross the anchor) */
+      if (op == 'I') x++;
+      else y++;
+    }
+  }
+  if (in_seg) {
+    if (*nseg == *capseg) {
+      *capseg = *capseg ? 2 * *capseg : 16;
+      *segs = (xd_segment*)realloc(*segs, sizeof(xd_segment) * (size_t)*capseg);
+    }
+    (*segs)[(*nseg)++] = cur;
+  }
+  free(opr);
+  free(opl);
+  return al->score;
+}
+
+/* One anchor, for tests: the alignment and its ungapped segments as
+ * (diagonal, start, stop) triples in seg_out[0 .. 3 * *n_seg) (at most cap
+ * segments are copied; *n_seg is the full count). */
+int32_t oracle_full_gapped_one(const int8_t* s1, int64_t len1, int64_t p1, const int8_t* s2, int64_t len2, int64_t p2,
+                               int32_t go, int32_t ge, int32_t X, oracle_alignment* al, int32_t* seg_out, int32_t cap,
+                               int32_t* n_seg) {
+  xd_segment* segs = NULL;
+  int32_t nseg = 0, capseg = 0;
+  const int32_t sc = oracle_full_gapped_pair(s1, len1, p1, s2, len2, p2, go, ge, X, al, &segs, &nseg, &capseg);
+  for (int32_t k = 0; k < nseg && k < cap; k++) {
+    seg_out[3 * k] = segs[k].diag;
+    seg_out[3 * k + 1] = segs[k].start;
+    seg_out[3 * k + 2] = segs[k].stop;
+  }
+  *n_seg = nseg;
+  free(segs);
+  return sc;
+}
+
+/* ------------------------------------------------------------------------
+ * Stage 3.2 over the stage-3.1 records, with the redundant-alignment lists
+ * of Section 3.3.4: the ungapped segments (diagonal, start, stop) of every
+ * gapped alignment computed are kept, and a hit lying on one of them (same
+ * pair of sequences, same diagonal, pos1 between start and stop) is not
+ * extended again.  The paper keeps the segments in k linked lists by
+ * diagonal group; the result depends only on which segments exist, so this
+ * statement keeps one plain list per pair of sequences.  Which hits are
+ * skipped depends on the order they are taken in, which the paper leaves to
+ * its streaming; here (a reading) the records of each pair are taken by
+ * decreasing small gapped score, then increasing pos1, then pos2, so the
+ * result does not depend on the input order.  Alignments scoring at least
+ * s3 are returned, sorted by (seq1, pos1, seq2, pos2) of their anchor.
+ * Pairs of sequences are independent: with n_threads > 1 they are shared
+ * out in contiguous ranges.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  const int8_t *codes1, *codes2;
+  const int64_t *seq_off1, *seq_off2;
+  int32_t go, ge, X;
+  const oracle_gapped* in;
+  const int64_t* order;     /* records grouped by pair, in processing order */
+  const int64_t* group_at;  /* group g: order[group_at[g] .. group_at[g + 1]) */
+  int64_t g_lo, g_hi;
+  oracle_alignment* slot;   /* per record, in order[] positions */
+  char* done;               /* 1: extended (not redundant) */
+} full_job;
+
+static const oracle_gapped* g_sort_in; /* qsort context (set before each sort, single-threaded) */
+
+static int cmp_full_order(const void* a, const void* b) {
+  const oracle_gapped* x = &g_sort_in[*(const int64_t*)a];
+  const oracle_gapped* y = &g_sort_in[*(const int64_t*)b];
+  if (x->seq1 != y->seq1) return x->seq1 < y->seq1 ? -1 : 1;
+  if (x->seq2 != y->seq2) return x->seq2 < y->seq2 ? -1 : 1;
+  if (x->score != y->score) return x->score > y->score ? -1 : 1;
+  if (x->pos1 != y->pos1) return x->pos1 < y->pos1 ? -1 : 1;
+  if (x->pos2 != y->pos2) return x->pos2 < y->pos2 ? -1 : 1;
+  return 0;
+}
+
+static void* full_worker(void* arg) {
+  full_job* j = (full_job*)arg;
+  xd_segment* segs = NULL;
+  int32_t nseg = 0, capseg = 0;
+  for (int64_t g = j->g_lo; g < j->g_hi; g++) {
+    nseg = 0;
+    for (int64_t k = j->group_at[g]; k < j->group_at[g + 1]; k++) {
+      const oracle_gapped* h = &j->in[j->order[k]];
+      const int32_t d = h->pos1 - h->pos2;
+      int redundant = 0;
+      for (int32_t s = 0; s < nseg && !redundant; s++)
+        redundant = segs[s].diag == d && segs[s].start <= h->pos1 && h->pos1 <= segs[s].stop;
+      j->done[k] = 0;
+      if (redundant) continue;
+      const int64_t o1 = j->seq_off1[h->seq1], o2 = j->seq_off2[h->seq2];
+      const int64_t len1 = j->seq_off1[h->seq1 + 1] - o1, len2 = j->seq_off2[h->seq2 + 1] - o2;
+      oracle_alignment* al = &j->slot[k];
+      oracle_full_gapped_pair(j->codes1 + o1, len1, h->pos1, j->codes2 + o2, len2, h->pos2, j->go, j->ge, j->X, al,
+                              &segs, &nseg, &capseg);
+      al->seq1 = h->seq1;
+      al->seq2 = h->seq2;
+      j->done[k] = 1;
+    }
+  }
+  free(segs);
+  return NULL;
+}
+
+static int cmp_alignment(const void* a, const void* b) {
+  const oracle_alignment* x = (const oracle_alignment*)a;
+  const oracle_alignment* y = (const oracle_alignment*)b;
+  if (x->seq1 != y->seq1) return x->seq1 < y->seq1 ? -1 : 1;
+  if (x->pos1 != y->pos1) return x->pos1 < y->pos1 ? -1 : 1;
+  if (x->seq2 != y->seq2) return x->seq2 < y->seq2 ? -1 : 1;
+  if (x->pos2 != y->pos2) return x->pos2 < y->pos2 ? -1 : 1;
+  return 0;
+}
+
+/* Returns the number of alignments (malloc'ed in *out); *n_extended receives
+ * how many records were extended (the rest were redundant). */
+int64_t oracle_full_gapped(const int8_t* codes1, const int64_t* seq_off1, const int8_t* codes2,
+                           const int64_t* seq_off2, int32_t go, int32_t ge, int32_t X, int32_t s3,
+                           const oracle_gapped* in, int64_t n_in, int32_t n_threads, oracle_alignment** out,
+                           int64_t* n_extended) {
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_in > 0 ? n_in : 1));
+  for (int64_t k = 0; k < n_in; k++) order[k] = k;
+  g_sort_in = in;
+  qsort(order, (size_t)n_in, sizeof(int64_t), cmp_full_order);
+  int64_t* group_at = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_in + 1));
+  int64_t ng = 0;
+  for (int64_t k = 0; k < n_in; k++)
+    if (k == 0 || in[order[k]].seq1 != in[order[k - 1]].seq1 || in[order[k]].seq2 != in[order[k - 1]].seq2)
+      group_at[ng++] = k;
+  group_at[ng] = n_in;
+  oracle_alignment* slot = (oracle_alignment*)calloc((size_t)(n_in > 0 ? n_in : 1), sizeof(oracle_alignment));
+  char* done = (char*)calloc((size_t)(n_in > 0 ? n_in : 1), 1);
+  if (n_threads < 1) n_threads = 1;
+  if (ng < (int64_t)n_threads * 4) n_threads = 1;
+  full_job* jobs = (full_job*)calloc((size_t)n_threads, sizeof(full_job));
+  pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+  for (int32_t t = 0; t < n_threads; t++) {
+    full_job* j = &jobs[t];
+    j->codes1 = codes1;
+    j->codes2 = codes2;
+    j->seq_off1 = seq_off1;
+    j->seq_off2 = seq_off2;
+    j->go = go;
+    j->ge = ge;
+    j->X = X;
+    j->in = in;
+    j->order = order;
+    j->group_at = group_at;
+    j->g_lo = ng * t / n_threads;
+    j->g_hi = ng * (t + 1) / n_threads;
+    j->slot = slot;
+    j->done = done;
+  }
+  if (n_threads == 1) {
+    full_worker(&jobs[0]);
+  } else {
+    for (int32_t t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, full_worker, &jobs[t]);
+    for (int32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+  }
+  int64_t n = 0, ext = 0;
+  for (int64_t k = 0; k < n_in; k++) {
+    ext += done[k];
+    if (done[k] && slot[k].score >= s3) slot[n++] = slot[k];
+  }
+  qsort(slot, (size_t)n, sizeof(oracle_alignment), cmp_alignment);
+  free(order);
+  free(group_at);
+  free(done);
+  free(jobs);
+  free(th);
+  *out = slot;
+  if (n_extended) *n_extended = ext;
   return n;
 }
 
