@@ -113,6 +113,27 @@ typedef struct {
   int16_t r_i, r_j, l_i, l_j;
 } plast_gapped;
 
+/*
+ * Full gapped alignment (stage 3.2, Section 3.3.4) with the tabular fields of
+ * the trace-back (stage 4, Section 3.3.5; BLAST's -m 8 columns without the
+ * E-value and bit score, which need statistics the paper does not give).
+ * pos1 / pos2 are the seed start of the stage-3.1 record it was extended
+ * from; [q_start, q_end) and [s_start, s_end) the aligned residues of the two
+ * sequences (0-based, local); length = alignment columns; gap_opens counts
+ * the gap runs of each side of the anchor (a run on each side of it is two).
+ * 52 bytes.
+ */
+typedef struct {
+  int32_t seq1, seq2, pos1, pos2;
+  int32_t score;
+  int32_t q_start, q_end, s_start, s_end;
+  int32_t length, identities, mismatches, gap_opens;
+} plast_alignment;
+
+/* Stage-3.2 drop-off used when a caller has no other: 38, BLAST's
+ * preliminary gapped drop-off of 15 bits at BLOSUM62 11/1's lambda 0.267. */
+#define PLAST_XDROP 38
+
 /* Fill *p with the default parameters listed above. */
 void plast_default_params(plast_params* p);
 
@@ -240,6 +261,30 @@ int plast_search(const plast_bank* b1, const plast_bank* b2, const plast_params*
 int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t s0,
                     const int32_t* keys, int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out,
                     int64_t* n_ungapped_out, void* stream);
+
+/*
+ * Stage 3.2 and the trace-back (Sections 3.3.4 and 3.3.5) of n_in stage-3.1
+ * records `in` (device, any order; as plast_search returns them): each is
+ * extended with gaps in both directions from its seed start, without band or
+ * length limit, the extension of a side stopping at the first row whose
+ * cells all lie more than `xdrop` below the best of the rows before
+ * (PLAST_XDROP if unsure).  Section 3.3.4's redundancy lists: for each pair of
+ * sequences the records are taken by decreasing small gapped score, then by
+ * position, and a record whose seed start lies on a gap-free segment
+ * (diagonal, first and last residue) of an alignment already computed for
+ * that pair is not extended.  Alignments scoring >= s3 are written to out
+ * sorted by (seq1, pos1, seq2, pos2); *n_extended_out (host, may be NULL)
+ * receives how many records were extended.  Gap costs come from params.
+ * Errors as plast_small_gapped, plus PLAST_E_INVALID for xdrop outside
+ * 0..30000 or banks of more than 2^24 sequences each, and PLAST_E_CAPACITY
+ * (with *n_out = 0) when an extension outgrows the kernel's working space: a
+ * row of more than 1024 computed columns, more than about one million cells
+ * for one side, or more than 8192 gap-free segments for one pair of
+ * sequences.
+ */
+int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t xdrop,
+                      int32_t s3, const plast_gapped* in, int64_t n_in, plast_alignment* out, int64_t cap,
+                      int64_t* n_out, int64_t* n_extended_out, void* stream);
 
 /*
  * plast_small_gapped without device allocation.  The paper has no

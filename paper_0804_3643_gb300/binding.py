@@ -31,6 +31,11 @@ GAPPED_DTYPE = np.dtype(
     [("seq1", "<i4"), ("pos1", "<i4"), ("seq2", "<i4"), ("pos2", "<i4"),
      ("score", "<i2"), ("ungapped", "<i2"), ("r_i", "<i2"), ("r_j", "<i2"),
      ("l_i", "<i2"), ("l_j", "<i2")])
+ALIGN_DTYPE = np.dtype([(n, "<i4") for n in (
+    "seq1", "seq2", "pos1", "pos2", "score", "q_start", "q_end", "s_start", "s_end", "length", "identities",
+    "mismatches", "gap_opens")])
+PLAST_XDROP = 38
+ALIGN_BYTES = ALIGN_DTYPE.itemsize    # 52
 HIT_BYTES = HIT_DTYPE.itemsize        # 20
 GAPPED_BYTES = GAPPED_DTYPE.itemsize  # 28
 
@@ -113,6 +118,8 @@ def lib() -> ctypes.CDLL:
         L.plast_search_ex.restype = ctypes.c_int
         L.plast_ungapped_ex.argtypes = [P, P, pPrm, i32, P, i32, P, i64, pI64, P]
         L.plast_ungapped_ex.restype = ctypes.c_int
+        L.plast_full_gapped.argtypes = [P, P, pPrm, i32, i32, P, i64, P, i64, pI64, pI64, P]
+        L.plast_full_gapped.restype = ctypes.c_int
         L.plast_small_gapped_noalloc.argtypes = [P, P, pPrm, P, i64, P, i64, pI64, P]
         L.plast_small_gapped_noalloc.restype = ctypes.c_int
         L.plast_plan_create.argtypes = [P, P, pPrm, i32, i64, P, i64, P, ctypes.POINTER(ctypes.c_void_p)]
@@ -390,6 +397,28 @@ def plast_small_gapped(b1: Bank, b2: Bank, hits: torch.Tensor, params: plast_par
     if rc:
         raise PlastError("plast_small_gapped", rc, n.value)
     return buf[: n.value * GAPPED_BYTES].view(-1, GAPPED_BYTES)
+
+
+def plast_full_gapped(b1: Bank, b2: Bank, records: torch.Tensor, params: plast_params | None = None,
+                      xdrop: int = PLAST_XDROP, s3: int = 47, cap: int | None = None, stream=None):
+    """Stage 3.2 and the trace-back fields of stage-3.1 ``records`` ([m, 28]
+    plast_gapped, device): (alignments [n, 52] uint8 device tensor of
+    plast_alignment in canonical order, number of records extended)."""
+    records = records.contiguous()
+    m = records.numel() // GAPPED_BYTES
+    cap = m if cap is None else cap
+    buf = _records(None, cap, ALIGN_BYTES)
+    n, ext = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().plast_full_gapped(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
+                                 int(xdrop), int(s3), _ptr(records), m, _ptr(buf), cap, ctypes.byref(n),
+                                 ctypes.byref(ext), _stream(stream))
+    if rc:
+        raise PlastError("plast_full_gapped", rc, n.value)
+    return buf[: n.value * ALIGN_BYTES].view(-1, ALIGN_BYTES), ext.value
+
+
+def alignments_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.contiguous().cpu().numpy().reshape(-1).view(ALIGN_DTYPE)
 
 
 NOALLOC_MAX_HITS = 65536

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
 LIB = os.path.join(HERE, "libplast.so")
-SOURCES = ["prims.cu", "index.cu", "ungapped.cu", "filter.cu", "gapped.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["prims.cu", "index.cu", "ungapped.cu", "filter.cu", "gapped.cu", "full.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "gapped.cuh"
 #include "filter.cuh"
+#include "full.cuh"
 #include "index.cuh"
 #include "ungapped.cuh"
 
@@ -975,6 +976,125 @@ int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_para
                     const int32_t* keys, int32_t n_keys, plast_gapped* out, int64_t cap, int64_t* n_out,
                     int64_t* n_ungapped_out, void* stream) {
   return search_impl(b1, b2, params, s0, keys, n_keys, out, cap, n_out, n_ungapped_out, stream);
+}
+
+int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t xdrop,
+                      int32_t s3, const plast_gapped* in, int64_t n_in, plast_alignment* out, int64_t cap,
+                      int64_t* n_out, int64_t* n_extended_out, void* stream) {
+  NvtxRange nvtx_("plast_full_gapped (stage 3.2)");
+  if (!b1 || !b2 || !n_out || n_in < 0 || cap < 0 || !params_ok(params) || xdrop < 0 || xdrop > 30000)
+    return PLAST_E_INVALID;
+  if ((n_in > 0 && !in) || n_in > (int64_t)UINT32_MAX) return PLAST_E_INVALID;
+  const plast_params prm = resolve(params);
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(bank_wait(b1, st));
+  CK(bank_wait(b2, st));
+  *n_out = 0;
+  if (n_extended_out) *n_extended_out = 0;
+  CK(upload_tables_once());
+  if (n_in == 0) return PLAST_OK;
+  if (b1->n_seqs == 0 || b2->n_seqs == 0) return PLAST_E_INVALID;
+  const int q1 = bits_for(b1->n_seqs), q2 = bits_for(b2->n_seqs);
+  if (q1 > 24 || q2 > 24) return PLAST_E_INVALID;
+  const int64_t n = n_in;
+  Scratch sc(st);
+  // canonical order of the records (padded positions), then the processing
+  // order (pair of sequences, decreasing small gapped score; ties keep the
+  // canonical order: the sort is stable)
+  uint64_t *k0, *k1;
+  uint32_t *v0, *v1, *canon, *proc;
+  int* d_bad;
+  CK(sc.get(&k0, n));
+  CK(sc.get(&k1, n));
+  CK(sc.get(&v0, n));
+  CK(sc.get(&v1, n));
+  CK(sc.get(&canon, n));
+  CK(sc.get(&d_bad, 1));
+  void* rtmp;
+  const size_t rtb = radix_tmp_bytes(n);
+  CK(sc.get((char**)&rtmp, rtb));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  const int sh = b2->pad_bits;
+  CK(launch_full_canon(in, n, b1->pad_off, b1->n_seqs, b2->pad_off, b2->n_seqs, sh, k0, v0, d_bad, st));
+  int h_bad = 0;
+  int rc = check_bad(d_bad, st, &h_bad);
+  if (rc) return rc;
+  if (h_bad) return PLAST_E_INVALID;
+  bool alt = false;
+  CK(radix_sort_pairs(k0, v0, k1, v1, n, b1->pad_bits + sh, rtmp, rtb, st, &alt));
+  CK(cudaMemcpyAsync(canon, alt ? v1 : v0, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  CK(launch_full_proc(in, canon, n, q2, k0, v0, st));
+  CK(radix_sort_pairs(k0, v0, k1, v1, n, q1 + q2 + 16, rtmp, rtb, st, &alt));
+  proc = alt ? v1 : v0;
+  // pairs of sequences: their first positions in processing order
+  int32_t *flag, *done, *keep;
+  int64_t *at, *gstart, *ng, *m_dev, *ext_dev;
+  CK(sc.get(&flag, n));
+  CK(sc.get(&at, n));
+  CK(sc.get(&gstart, n + 1));
+  CK(sc.get(&ng, 1));
+  void* stmp;
+  const size_t stb = scan_tmp_bytes(n);
+  CK(sc.get((char**)&stmp, stb));
+  CK(launch_full_groups(in, proc, n, flag, nullptr, nullptr, nullptr, 0, st));
+  CK(scan_exclusive(flag, at, n, ng, stmp, stb, st));
+  CK(launch_full_groups(in, proc, n, flag, at, ng, gstart, 1, st));
+  // the extensions
+  const int64_t warps = std::min<int64_t>(full_gapped_warps(num_sms()), (n + 3) / 4 * 4);
+  plast_alignment* res;
+  uint8_t* arena;
+  int32_t* segs;
+  int* d_err;
+  CK(sc.get(&res, n));
+  CK(sc.get(&done, n));
+  CK(sc.get(&arena, (size_t)warps * FG_ARENA));
+  CK(sc.get(&segs, (size_t)warps * 3 * FG_SEGS));
+  CK(sc.get(&d_err, 1));
+  CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  FullArgs fa;
+  fa.pad1 = b1->pad;
+  fa.pad2 = b2->pad;
+  fa.pad_off1 = b1->pad_off;
+  fa.pad_off2 = b2->pad_off;
+  fa.in = in;
+  fa.proc = proc;
+  fa.gstart = gstart;
+  fa.ng_dev = ng;
+  fa.go = prm.gap_open;
+  fa.ge = prm.gap_extend;
+  fa.xdrop = xdrop;
+  fa.res = res;
+  fa.done = done;
+  fa.arena = arena;
+  fa.segs = segs;
+  fa.err = d_err;
+  t_timer.reset();
+  t_timer.mark(0, st);
+  CK(launch_full_gapped(fa, warps, st));
+  t_timer.mark(1, st);
+  // the alignments kept, in canonical order
+  CK(sc.get(&keep, n));
+  CK(sc.get(&m_dev, 1));
+  CK(sc.get(&ext_dev, 1));
+  CK(launch_full_keep(canon, n, done, res, s3, keep, st));
+  CK(scan_exclusive(keep, at, n, m_dev, stmp, stb, st));
+  CK(scan_exclusive(done, gstart, n, ext_dev, stmp, stb, st));
+  int64_t m = 0, ext = 0;
+  int h_err = 0;
+  CK(cudaMemcpyAsync(&m, m_dev, sizeof(m), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&ext, ext_dev, sizeof(ext), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_err) return PLAST_E_CAPACITY;
+  *n_out = m;
+  if (n_extended_out) *n_extended_out = ext;
+  if (m > cap) return PLAST_E_CAPACITY;
+  if (m == 0) return PLAST_OK;
+  if (!out) return PLAST_E_INVALID;
+  CK(launch_full_write(canon, n, keep, at, res, out, st));
+  t_timer.mark(2, st);
+  CK(cudaStreamSynchronize(st));
+  return PLAST_OK;
 }
 
 int plast_translate6(const uint8_t* dna, const int64_t* contig_off, int32_t n_contigs, int8_t* aa_out,

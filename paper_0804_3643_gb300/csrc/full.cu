@@ -1,0 +1,480 @@
+// full.cu -- stage 3.2 (Section 3.3.4: the full gapped extension of the hits
+// whose small gapped extension reaches S2, with the list of ungapped segments
+// that keeps a hit lying on an alignment already found from being extended
+// again) and the trace-back of stage 4 (Section 3.3.5) down to BLAST's
+// tabular fields, on sm_103a.
+//
+// Work split.  The records of one pair of sequences depend on one another
+// through the segment list, so one warp takes all the records of a pair, in
+// the processing order (decreasing small gapped score, then pos1, then
+// pos2); pairs are independent and spread over the warps.
+//
+// One side of one record is an anchored dynamic programme without a band,
+// cut by the drop-off X row by row: a cell whose H is more than X below T,
+// the best H of the rows before it, is dropped (H = F = minus infinity).  The
+// warp computes a row 32 columns at a time, one column per lane, from the
+// first live column of the row above:
+//   F  = max(F_up - ge, H_up - go - ge)        (shared memory: the row above)
+//   D  = H_diag + s(A_i, B_j)
+//   DF = max(D, F)
+//   E  = max over k < j in the row of DF(k) - go - (j - k) ge
+//      = (exclusive prefix maximum of DF(k) + k ge) - go - j ge   (warp scan)
+//   H  = max(DF, E)
+// E here is not reset at dropped cells; a value that reaches a cell through a
+// dropped one is already below T - X there, so it neither keeps a cell alive
+// nor equals the H of a live cell, and the scores, end cells and paths are
+// those of the row-by-row statement.  A row stops at the first chunk past
+// the row above's live cells whose last cell is dropped (beyond them only E
+// feeds a cell, and it only falls).
+//
+// Each cell leaves one direction byte in the warp's arena (global memory):
+// the source of H (0 diagonal, 1 E, 2 F, in that order of preference), and
+// whether E and F open their gap at this cell (preferred over an extension
+// of equal value).  After the side's last row, lane 0 walks back from the end
+// cell (first maximum in row-major order) to the anchor, counting the
+// alignment's columns, identities and gap runs and emitting its gap-free
+// segments (diagonal pos1 - pos2, first and last pos1).
+//
+// Limits (reported as PLAST_E_CAPACITY by the call): a row of more than
+// FG_W computed columns, more than FG_ARENA bytes of directions and row
+// table for one side, more than FG_SEGS segments for one pair of sequences.
+#include <stdint.h>
+
+#include "common.cuh"
+#include "full.cuh"
+
+namespace plast {
+
+constexpr int FG_WARPS = 4;  // warps per CTA
+constexpr int32_t FG_NEG = -(1 << 28);
+constexpr int FG_SMEM = FG_WARPS * 4 * FG_W * 4;  // per warp: H and F of two rows
+
+__device__ __forceinline__ int32_t warp_max(int32_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
+// B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
+// end cell; the directions and the row table (c0, offset per row) are in
+// `arena`.  *err gets FG_ERR_* bits on a capacity overflow.
+struct SideOut {
+  int32_t score, ei, ej;
+};
+
+__device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int bs, int lb, int go, int ge, int X,
+                           const int8_t* tab, int32_t* Hbuf, int32_t* Fbuf, uint8_t* arena, int* err, int lane) {
+  const int goe = go + ge;
+  int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (c0, offset) per row
+  const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
+  int64_t off = tab_bytes;
+  SideOut out = {0, 0, 0};
+  if (tab_bytes > FG_ARENA) {
+    if (lane == 0) atomicOr(err, FG_ERR_ARENA);
+    return out;
+  }
+  int32_t T = 0, best = 0, bi = 0, bj = 0;
+  int plo = 0, phi = 0, pc0 = 0, pwid = 0;  // the row above: live columns, stored columns
+  int pb = 0;                               // buffer holding the row above
+  for (int i = 0; i <= la; i++) {
+    const int c0 = i == 0 ? 0 : plo;
+    const int lim = i == 0 ? 0 : phi + 1;  // the last column a cell of the row above can feed
+    const int cb = pb ^ 1;
+    const int32_t* Hp = Hbuf + pb * FG_W;
+    const int32_t* Fp = Fbuf + pb * FG_W;
+    int32_t* Hc = Hbuf + cb * FG_W;
+    int32_t* Fc = Fbuf + cb * FG_W;
+    const int ai = i > 0 ? A[(int64_t)(i - 1) * as] : 0;
+    const int8_t* trow = tab + ai * NCODE;
+    int32_t carryP = FG_NEG, carryH = FG_NEG;
+    int32_t rmax = FG_NEG, rarg = 0;
+    int lo = -1, hi = -1, cend = c0;
+    bool overflow = false;
+    for (int cs = c0; cs <= lb; cs += 32) {
+      const int j = cs + lane;
+      const bool in = j <= lb;
+      int32_t hd = FG_NEG, hu = FG_NEG, fu = FG_NEG;
+      if (i > 0 && in) {
+        const int kd = j - 1 - pc0, ku = j - pc0;
+        if (j >= 1 && kd >= 0 && kd < pwid) hd = Hp[kd];
+        if (ku >= 0 && ku < pwid) {
+          hu = Hp[ku];
+          fu = Fp[ku];
+        }
+      }
+      int32_t D = FG_NEG;
+      if (in && i > 0 && j >= 1 && hd > FG_NEG) D = hd + trow[B[(int64_t)(j - 1) * bs]];
+      const int32_t F = max(fu - ge, hu - goe);
+      int32_t DF = max(D, F);
+      if (i == 0 && j == 0) DF = 0;
+      // E from the exclusive prefix maximum of DF(k) + k ge over the row
+      const int32_t P = in ? DF + j * ge : FG_NEG;
+      int32_t incl = P;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, y);
+      }
+      int32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      excl = lane == 0 ? carryP : max(excl, carryP);
+      const int32_t E = excl - go - j * ge;
+      int32_t H = max(DF, E);
+      const bool live = in && H >= T - X;
+      const int32_t Hs = live ? H : FG_NEG;
+      int32_t hleft = __shfl_up_sync(0xffffffffu, Hs, 1);
+      if (lane == 0) hleft = carryH;
+      // direction byte of the cell
+      const uint32_t src = (D > FG_NEG && H == D) ? 0u : (H == E ? 1u : 2u);
+      const uint32_t eop = (hleft > FG_NEG && E == hleft - goe) ? 4u : 0u;
+      const uint32_t fop = (hu > FG_NEG && F == hu - goe) ? 8u : 0u;
+      const int w = j - c0;
+      if (in) {
+        if (w < FG_W && off + w < FG_ARENA) {
+          Hc[w] = Hs;
+          Fc[w] = live ? F : FG_NEG;
+          arena[off + w] = (uint8_t)(src | eop | fop);
+        } else {
+          overflow = true;
+        }
+      }
+      // live window, row maximum (first column on ties)
+      const unsigned lm = __ballot_sync(0xffffffffu, live);
+      if (lm) {
+        if (lo < 0) lo = cs + __ffs(lm) - 1;
+        hi = cs + 31 - __clz(lm);
+        const int32_t m = warp_max(Hs);
+        if (m > rmax) {
+          rmax = m;
+          rarg = cs + __ffs(__ballot_sync(0xffffffffu, live && Hs == m)) - 1;
+        }
+      }
+      carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
+      carryH = __shfl_sync(0xffffffffu, Hs, 31);
+      cend = min(cs + 32, lb + 1);
+      if (cs + 31 >= lim && !(lm >> 31)) break;  // past the row above's reach, last cell dropped
+    }
+    if (__any_sync(0xffffffffu, overflow)) {
+      if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
+      return out;
+    }
+    if (rmax == FG_NEG) break;  // no live cell: the side ends
+    if (lane == 0) {
+      rowtab[2 * i] = c0;
+      rowtab[2 * i + 1] = (int32_t)off;
+    }
+    off += cend - c0;
+    if (rmax > best) {
+      best = rmax;
+      bi = i;
+      bj = rarg;
+    }
+    T = max(T, rmax);
+    plo = lo;
+    phi = hi;
+    pc0 = c0;
+    pwid = cend - c0;
+    pb = cb;
+    __syncwarp();
+  }
+  out.score = best;
+  out.ei = bi;
+  out.ej = bj;
+  return out;
+}
+
+// Lane 0: the path of a side from its end cell back to the anchor.  Columns
+// (cell (i, j) holds residues x = x0 + dx * (i - 1), y = y0 + dy * (j - 1) of
+// the padded banks) are counted into *st; gap-free runs are appended to segs
+// (pos1 coordinates are local: x - xoff), except the run that reaches the
+// anchor, returned in *anchor_run (valid when its length is > 0).
+struct PathStats {
+  int32_t length, identities, mismatches, gap_opens;
+};
+struct Run {
+  int32_t diag, start, stop, len;
+};
+
+__device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pad1, const int8_t* pad2, int64_t x1,
+                          int64_t y1, int dir, int64_t xoff, int64_t yoff, PathStats* st, int32_t* segs, int* nseg,
+                          int* err, Run* anchor_run) {
+  const int32_t* rowtab = reinterpret_cast<const int32_t*>(arena);
+  int i = ei, j = ej, state = 0, prev_gap = 0;
+  Run cur = {0, 0, 0, 0};
+  auto flush = [&](bool at_anchor) {
+    if (cur.len == 0) return;
+    if (at_anchor) {
+      *anchor_run = cur;
+    } else if (*nseg < FG_SEGS) {
+      segs[3 * *nseg] = cur.diag;
+      segs[3 * *nseg + 1] = cur.start;
+      segs[3 * *nseg + 2] = cur.stop;
+      (*nseg)++;
+    } else {
+      atomicOr(err, FG_ERR_SEGS);
+    }
+    cur.len = 0;
+  };
+  while (i > 0 || j > 0) {
+    const uint8_t d = arena[rowtab[2 * i + 1] + (j - rowtab[2 * i])];
+    if (state == 0) {
+      const uint32_t src = d & 3u;
+      if (src == 0) {
+        // residue pair (A_i, B_j)
+        const int64_t x = x1 + (int64_t)dir * (i - 1), y = y1 + (int64_t)dir * (j - 1);
+        if (pad1[x] == pad2[y]) st->identities++;
+        else st->mismatches++;
+        st->length++;
+        const int32_t px = (int32_t)(x - xoff), py = (int32_t)(y - yoff);
+        if (cur.len > 0 && cur.diag == px - py) {
+          cur.start = min(cur.start, px);
+          cur.stop = max(cur.stop, px);
+          cur.len++;
+        } else {
+          flush(false);
+          cur.diag = px - py;
+          cur.start = cur.stop = px;
+          cur.len = 1;
+        }
+        prev_gap = 0;
+        i--;
+        j--;
+      } else {
+        state = (int)src;
+      }
+    } else {
+      flush(false);  // a gap ends the current run
+      if (prev_gap != state) st->gap_opens++;
+      prev_gap = state;
+      st->length++;
+      // a run is a stretch of equal gap columns, whatever the path's
+      // opening decisions (with a free opening a run may open twice)
+      if (state == 1) {  // gap in A: B_j against nothing
+        state = (d & 4u) ? 0 : 1;
+        j--;
+      } else {           // gap in B: A_i against nothing
+        state = (d & 8u) ? 0 : 2;
+        i--;
+      }
+    }
+  }
+  flush(true);
+}
+
+__global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
+  __shared__ int8_t tab[NCODE * NCODE];
+  extern __shared__ __align__(16) int32_t fsm[];
+  for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t* Hbuf = fsm + warp * 4 * FG_W;
+  int32_t* Fbuf = Hbuf + 2 * FG_W;
+  const int64_t gw = (int64_t)blockIdx.x * FG_WARPS + warp;
+  uint8_t* arena = a.arena + gw * FG_ARENA;
+  int32_t* segs = a.segs + gw * 3 * FG_SEGS;
+  const int64_t ng = *a.ng_dev;
+  for (int64_t g = gw; g < ng; g += (int64_t)gridDim.x * FG_WARPS) {
+    int nseg = 0;
+    for (int64_t k = a.gstart[g]; k < a.gstart[g + 1]; k++) {
+      const uint32_t rec = a.proc[k];
+      const plast_gapped r = a.in[rec];
+      // the redundancy check: the anchor on a segment of this pair's list
+      const int32_t dg = r.pos1 - r.pos2;
+      bool on = false;
+      for (int s = lane; s < nseg; s += 32)
+        on |= segs[3 * s] == dg && segs[3 * s + 1] <= r.pos1 && r.pos1 <= segs[3 * s + 2];
+      if (__any_sync(0xffffffffu, on)) {
+        if (lane == 0) a.done[rec] = 0;
+        continue;
+      }
+      const int64_t s1 = a.pad_off1[r.seq1], s2 = a.pad_off2[r.seq2];
+      const int len1 = (int)(a.pad_off1[r.seq1 + 1] - s1 - GAP), len2 = (int)(a.pad_off2[r.seq2 + 1] - s2 - GAP);
+      const int64_t x0 = s1 + r.pos1, y0 = s2 + r.pos2;  // padded anchor
+      // right side: rows A_1.. = pad1[x0 ..], columns pad2[y0 ..]
+      const SideOut R = side_dp(a.pad1 + x0, 1, len1 - r.pos1, a.pad2 + y0, 1, len2 - r.pos2, a.go, a.ge, a.xdrop,
+                                tab, Hbuf, Fbuf, arena, a.err, lane);
+      __syncwarp();
+      PathStats st = {0, 0, 0, 0};
+      Run rr = {0, 0, 0, 0}, lr = {0, 0, 0, 0};
+      if (lane == 0) walk_side(arena, R.ei, R.ej, a.pad1, a.pad2, x0, y0, 1, s1, s2, &st, segs, &nseg, a.err, &rr);
+      __syncwarp();
+      // left side: rows A_1.. = pad1[x0 - 1 ..] backwards
+      const SideOut L = side_dp(a.pad1 + x0 - 1, -1, r.pos1, a.pad2 + y0 - 1, -1, r.pos2, a.go, a.ge, a.xdrop, tab,
+                                Hbuf, Fbuf, arena, a.err, lane);
+      __syncwarp();
+      if (lane == 0) {
+        walk_side(arena, L.ei, L.ej, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, &st, segs, &nseg, a.err, &lr);
+        // the runs that reach the anchor from both sides are one segment
+        if (rr.len > 0 || lr.len > 0) {
+          Run m = rr.len > 0 ? rr : lr;
+          if (rr.len > 0 && lr.len > 0) m.start = lr.start;
+          if (nseg < FG_SEGS) {
+            segs[3 * nseg] = m.diag;
+            segs[3 * nseg + 1] = m.start;
+            segs[3 * nseg + 2] = m.stop;
+            nseg++;
+          } else {
+            atomicOr(a.err, FG_ERR_SEGS);
+          }
+        }
+        plast_alignment al;
+        al.seq1 = r.seq1;
+        al.seq2 = r.seq2;
+        al.pos1 = r.pos1;
+        al.pos2 = r.pos2;
+        al.score = R.score + L.score;
+        al.q_start = r.pos1 - L.ei;
+        al.q_end = r.pos1 + R.ei;
+        al.s_start = r.pos2 - L.ej;
+        al.s_end = r.pos2 + R.ej;
+        al.length = st.length;
+        al.identities = st.identities;
+        al.mismatches = st.mismatches;
+        al.gap_opens = st.gap_opens;
+        a.res[rec] = al;
+        a.done[rec] = 1;
+      }
+      nseg = __shfl_sync(0xffffffffu, nseg, 0);
+      __syncwarp();
+    }
+  }
+}
+
+cudaError_t launch_full_gapped(const FullArgs& a, int64_t warps, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_full_gapped, cudaFuncAttributeMaxDynamicSharedMemorySize, FG_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (warps <= 0) return cudaSuccess;
+  note_launch();
+  k_full_gapped<<<(unsigned)(warps / FG_WARPS), FG_WARPS * 32, FG_SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+int64_t full_gapped_warps(int n_sms) { return (int64_t)n_sms * 3 * FG_WARPS; }
+
+// ---------------------------------------------------------------------------
+// Ordering and output
+// ---------------------------------------------------------------------------
+// Canonical key (padded pos1 << sh | padded pos2) of each record, with the
+// record's fields checked against the banks (bad |= 1 otherwise).
+__global__ void k_full_canon(const plast_gapped* in, int64_t n, const int64_t* po1, int32_t n1, const int64_t* po2,
+                             int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n; h += (int64_t)gridDim.x * blockDim.x) {
+    const plast_gapped r = in[h];
+    bool ok = r.seq1 >= 0 && r.seq1 < n1 && r.seq2 >= 0 && r.seq2 < n2;
+    int64_t p1 = 0, p2 = 0;
+    if (ok) {
+      const int64_t l1 = po1[r.seq1 + 1] - po1[r.seq1] - GAP, l2 = po2[r.seq2 + 1] - po2[r.seq2] - GAP;
+      ok = r.pos1 >= 0 && r.pos1 < l1 && r.pos2 >= 0 && r.pos2 < l2;
+      p1 = po1[r.seq1] + r.pos1;
+      p2 = po2[r.seq2] + r.pos2;
+    }
+    if (!ok) {
+      atomicOr(bad, 1);
+      p1 = p2 = 0;
+    }
+    key[h] = ((uint64_t)p1 << sh) | (uint64_t)p2;
+    val[h] = (uint32_t)h;
+  }
+}
+
+// Processing key of the records in canonical order: (seq1, seq2, 32767 -
+// small gapped score); sorted stably after the canonical sort, ties keep
+// (pos1, pos2) order.
+__global__ void k_full_proc(const plast_gapped* in, const uint32_t* canon, int64_t n, int b2, uint64_t* key,
+                            uint32_t* val) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = canon[c];
+    const plast_gapped r = in[h];
+    key[c] = ((((uint64_t)(uint32_t)r.seq1 << b2) | (uint64_t)(uint32_t)r.seq2) << 16) |
+             (uint64_t)(uint16_t)(32767 - (int32_t)r.score);
+    val[c] = h;
+  }
+}
+
+// flag[k] = 1 where a new pair of sequences starts in processing order
+__global__ void k_full_group_flags(const plast_gapped* in, const uint32_t* proc, int64_t n, int32_t* flag) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const plast_gapped r = in[proc[k]];
+    bool head = k == 0;
+    if (!head) {
+      const plast_gapped q = in[proc[k - 1]];
+      head = q.seq1 != r.seq1 || q.seq2 != r.seq2;
+    }
+    flag[k] = head;
+  }
+}
+
+__global__ void k_full_group_starts(const int32_t* flag, const int64_t* at, int64_t n, const int64_t* ng,
+                                    int64_t* gstart) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    if (flag[k]) gstart[at[k]] = k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) gstart[*ng] = n;
+}
+
+// keep[c] = the record at canonical position c was extended and scores >= s3
+__global__ void k_full_keep(const uint32_t* canon, int64_t n, const int32_t* done, const plast_alignment* res,
+                            int32_t s3, int32_t* keep) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = canon[c];
+    keep[c] = done[h] && res[h].score >= s3;
+  }
+}
+
+__global__ void k_full_write(const uint32_t* canon, int64_t n, const int32_t* keep, const int64_t* at,
+                             const plast_alignment* res, plast_alignment* out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+    if (keep[c]) out[at[c]] = res[canon[c]];
+}
+
+static unsigned grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)(b > 0 ? b : 1);
+}
+
+cudaError_t launch_full_canon(const plast_gapped* in, int64_t n, const int64_t* po1, int32_t n1, const int64_t* po2,
+                              int32_t n2, int sh, uint64_t* key, uint32_t* val, int* bad, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  k_full_canon<<<grid_for(n), 256, 0, st>>>(in, n, po1, n1, po2, n2, sh, key, val, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_proc(const plast_gapped* in, const uint32_t* canon, int64_t n, int b2, uint64_t* key,
+                             uint32_t* val, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  k_full_proc<<<grid_for(n), 256, 0, st>>>(in, canon, n, b2, key, val);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_groups(const plast_gapped* in, const uint32_t* proc, int64_t n, int32_t* flag,
+                               const int64_t* at, const int64_t* ng, int64_t* gstart, int phase, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  if (phase == 0) k_full_group_flags<<<grid_for(n), 256, 0, st>>>(in, proc, n, flag);
+  else k_full_group_starts<<<grid_for(n), 256, 0, st>>>(flag, at, n, ng, gstart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_keep(const uint32_t* canon, int64_t n, const int32_t* done, const plast_alignment* res,
+                             int32_t s3, int32_t* keep, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  k_full_keep<<<grid_for(n), 256, 0, st>>>(canon, n, done, res, s3, keep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_write(const uint32_t* canon, int64_t n, const int32_t* keep, const int64_t* at,
+                              const plast_alignment* res, plast_alignment* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  note_launch();
+  k_full_write<<<grid_for(n), 256, 0, st>>>(canon, n, keep, at, res, out);
+  return cudaGetLastError();
+}
+
+}  // namespace plast
