@@ -278,7 +278,7 @@ int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_para
  * Errors as plast_small_gapped, plus PLAST_E_INVALID for xdrop outside
  * 0..30000 or banks of more than 2^24 sequences each, and PLAST_E_CAPACITY
  * (with *n_out = 0) when an extension outgrows the kernel's working space: a
- * row of more than 1024 computed columns, more than about one million cells
+ * row of more than 1024 computed columns, more than about half a million cells
  * for one side, or more than 8192 gap-free segments for one pair of
  * sequences.
  */

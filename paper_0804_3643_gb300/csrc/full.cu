@@ -47,13 +47,14 @@ namespace plast {
 
 constexpr int FG_WARPS = 4;  // warps per CTA
 constexpr int32_t FG_NEG = -(1 << 28);
-constexpr int FG_SMEM = FG_WARPS * 4 * FG_W * 4;  // per warp: H and F of two rows
+constexpr int FG_SMEM = FG_WARPS * 4 * FG_W * 2;  // per warp: H and F of two rows (int16)
 
-__device__ __forceinline__ int32_t warp_max(int32_t v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
+// The row above is kept in shared memory as int16 values relative to its
+// drop-off line thr = T - X: a live cell's H lies in [thr, thr + X + 11] (no
+// cell rises more than one diagonal step, at most 11, above the best of the
+// earlier rows), and an F below the line can neither keep a cell alive nor
+// give the H of a live one, so it is kept as -1 (dropped) like a dead cell.
+__device__ __forceinline__ int32_t dec16(int16_t v, int32_t thr) { return v >= 0 ? (int32_t)v + thr : FG_NEG; }
 
 // One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
 // B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
@@ -63,8 +64,9 @@ struct SideOut {
   int32_t score, ei, ej;
 };
 
-__device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int bs, int lb, int go, int ge, int X,
-                           const int8_t* tab, int32_t* Hbuf, int32_t* Fbuf, uint8_t* arena, int* err, int lane) {
+template <int DIR>
+__device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int go, int ge, int X, const int8_t* tab,
+                           int16_t* Hbuf, int16_t* Fbuf, uint8_t* arena, int* err, int lane) {
   const int goe = go + ge;
   int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (c0, offset) per row
   const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
@@ -76,16 +78,18 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
   }
   int32_t T = 0, best = 0, bi = 0, bj = 0;
   int plo = 0, phi = 0, pc0 = 0, pwid = 0;  // the row above: live columns, stored columns
+  int32_t pthr = 0;                         // the row above's drop-off line
   int pb = 0;                               // buffer holding the row above
   for (int i = 0; i <= la; i++) {
     const int c0 = i == 0 ? 0 : plo;
     const int lim = i == 0 ? 0 : phi + 1;  // the last column a cell of the row above can feed
     const int cb = pb ^ 1;
-    const int32_t* Hp = Hbuf + pb * FG_W;
-    const int32_t* Fp = Fbuf + pb * FG_W;
-    int32_t* Hc = Hbuf + cb * FG_W;
-    int32_t* Fc = Fbuf + cb * FG_W;
-    const int ai = i > 0 ? A[(int64_t)(i - 1) * as] : 0;
+    const int16_t* Hp = Hbuf + pb * FG_W;
+    const int16_t* Fp = Fbuf + pb * FG_W;
+    int16_t* Hc = Hbuf + cb * FG_W;
+    int16_t* Fc = Fbuf + cb * FG_W;
+    const int32_t thr = T - X;
+    const int ai = i > 0 ? A[DIR * (i - 1)] : 0;
     const int8_t* trow = tab + ai * NCODE;
     int32_t carryP = FG_NEG, carryH = FG_NEG;
     int32_t rmax = FG_NEG, rarg = 0;
@@ -97,14 +101,14 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
       int32_t hd = FG_NEG, hu = FG_NEG, fu = FG_NEG;
       if (i > 0 && in) {
         const int kd = j - 1 - pc0, ku = j - pc0;
-        if (j >= 1 && kd >= 0 && kd < pwid) hd = Hp[kd];
+        if (j >= 1 && kd >= 0 && kd < pwid) hd = dec16(Hp[kd], pthr);
         if (ku >= 0 && ku < pwid) {
-          hu = Hp[ku];
-          fu = Fp[ku];
+          hu = dec16(Hp[ku], pthr);
+          fu = dec16(Fp[ku], pthr);
         }
       }
       int32_t D = FG_NEG;
-      if (in && i > 0 && j >= 1 && hd > FG_NEG) D = hd + trow[B[(int64_t)(j - 1) * bs]];
+      if (in && i > 0 && j >= 1 && hd > FG_NEG) D = hd + trow[B[DIR * (j - 1)]];
       const int32_t F = max(fu - ge, hu - goe);
       int32_t DF = max(D, F);
       if (i == 0 && j == 0) DF = 0;
@@ -120,7 +124,7 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
       excl = lane == 0 ? carryP : max(excl, carryP);
       const int32_t E = excl - go - j * ge;
       int32_t H = max(DF, E);
-      const bool live = in && H >= T - X;
+      const bool live = in && H >= thr;
       const int32_t Hs = live ? H : FG_NEG;
       int32_t hleft = __shfl_up_sync(0xffffffffu, Hs, 1);
       if (lane == 0) hleft = carryH;
@@ -131,8 +135,8 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
       const int w = j - c0;
       if (in) {
         if (w < FG_W && off + w < FG_ARENA) {
-          Hc[w] = Hs;
-          Fc[w] = live ? F : FG_NEG;
+          Hc[w] = live ? (int16_t)(H - thr) : (int16_t)-1;
+          Fc[w] = live ? (int16_t)max(F - thr, -1) : (int16_t)-1;
           arena[off + w] = (uint8_t)(src | eop | fop);
         } else {
           overflow = true;
@@ -143,7 +147,7 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
       if (lm) {
         if (lo < 0) lo = cs + __ffs(lm) - 1;
         hi = cs + 31 - __clz(lm);
-        const int32_t m = warp_max(Hs);
+        const int32_t m = __reduce_max_sync(0xffffffffu, Hs);
         if (m > rmax) {
           rmax = m;
           rarg = cs + __ffs(__ballot_sync(0xffffffffu, live && Hs == m)) - 1;
@@ -174,6 +178,7 @@ __device__ SideOut side_dp(const int8_t* A, int as, int la, const int8_t* B, int
     phi = hi;
     pc0 = c0;
     pwid = cend - c0;
+    pthr = thr;
     pb = cb;
     __syncwarp();
   }
@@ -263,12 +268,12 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pa
 
 __global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
   __shared__ int8_t tab[NCODE * NCODE];
-  extern __shared__ __align__(16) int32_t fsm[];
+  extern __shared__ __align__(16) int16_t fsm[];
   for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t* Hbuf = fsm + warp * 4 * FG_W;
-  int32_t* Fbuf = Hbuf + 2 * FG_W;
+  int16_t* Hbuf = fsm + warp * 4 * FG_W;
+  int16_t* Fbuf = Hbuf + 2 * FG_W;
   const int64_t gw = (int64_t)blockIdx.x * FG_WARPS + warp;
   uint8_t* arena = a.arena + gw * FG_ARENA;
   int32_t* segs = a.segs + gw * 3 * FG_SEGS;
@@ -291,16 +296,16 @@ __global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
       const int len1 = (int)(a.pad_off1[r.seq1 + 1] - s1 - GAP), len2 = (int)(a.pad_off2[r.seq2 + 1] - s2 - GAP);
       const int64_t x0 = s1 + r.pos1, y0 = s2 + r.pos2;  // padded anchor
       // right side: rows A_1.. = pad1[x0 ..], columns pad2[y0 ..]
-      const SideOut R = side_dp(a.pad1 + x0, 1, len1 - r.pos1, a.pad2 + y0, 1, len2 - r.pos2, a.go, a.ge, a.xdrop,
-                                tab, Hbuf, Fbuf, arena, a.err, lane);
+      const SideOut R = side_dp<1>(a.pad1 + x0, len1 - r.pos1, a.pad2 + y0, len2 - r.pos2, a.go, a.ge, a.xdrop, tab,
+                                   Hbuf, Fbuf, arena, a.err, lane);
       __syncwarp();
       PathStats st = {0, 0, 0, 0};
       Run rr = {0, 0, 0, 0}, lr = {0, 0, 0, 0};
       if (lane == 0) walk_side(arena, R.ei, R.ej, a.pad1, a.pad2, x0, y0, 1, s1, s2, &st, segs, &nseg, a.err, &rr);
       __syncwarp();
       // left side: rows A_1.. = pad1[x0 - 1 ..] backwards
-      const SideOut L = side_dp(a.pad1 + x0 - 1, -1, r.pos1, a.pad2 + y0 - 1, -1, r.pos2, a.go, a.ge, a.xdrop, tab,
-                                Hbuf, Fbuf, arena, a.err, lane);
+      const SideOut L = side_dp<-1>(a.pad1 + x0 - 1, r.pos1, a.pad2 + y0 - 1, r.pos2, a.go, a.ge, a.xdrop, tab, Hbuf,
+                                    Fbuf, arena, a.err, lane);
       __syncwarp();
       if (lane == 0) {
         walk_side(arena, L.ei, L.ej, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, &st, segs, &nseg, a.err, &lr);
@@ -353,7 +358,7 @@ cudaError_t launch_full_gapped(const FullArgs& a, int64_t warps, cudaStream_t st
   return cudaGetLastError();
 }
 
-int64_t full_gapped_warps(int n_sms) { return (int64_t)n_sms * 3 * FG_WARPS; }
+int64_t full_gapped_warps(int n_sms) { return (int64_t)n_sms * 5 * FG_WARPS; }
 
 // ---------------------------------------------------------------------------
 // Ordering and output
