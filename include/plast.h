@@ -377,12 +377,13 @@ int plast_set_schedule(int mode);
  * current device (random banks, the stage-2 kernel timed with every tile of
  * one shape, against a long and a short bank 2; about a second), installs
  * them and copies them to *out (may be NULL).  It also picks the wide kernel
- * variant, how many cells of the wide profile are held as int16 (no sign
- * extension, twice the shared-memory traffic), by timing each.
+ * variant by timing each: how many cells of the wide profile are held as
+ * int16 (no sign extension, twice the shared-memory traffic), then how many
+ * passes ahead a warp fetches its next bank-2 windows (the staging depth).
  * plast_get_tile_costs / plast_set_tile_costs read and install costs and
  * variant (for a cached calibration; PLAST_E_INVALID unless the slot costs
- * are positive, the tile costs non-negative and wide_int16_cells one of the
- * variants).  plast_set_tile_shape forces the shape of every tile (1 wide;
+ * are positive, the tile costs non-negative, wide_int16_cells one of the
+ * variants and wide_stage_depth 0, 1 or 2).  plast_set_tile_shape forces the shape of every tile (1 wide;
  * 2, 3, 4, 5 narrow of 8, 4, 2, 16 rows; 0, the default, by cost).  Shapes change
  * the schedule, never the results.  Settings are process-wide and apply to
  * later calls.
@@ -393,7 +394,7 @@ typedef struct plast_tile_costs {
   double narrow4_slot, narrow4_tile; /* 4 rows */
   double narrow2_slot, narrow2_tile; /* 2 rows */
   int32_t wide_int16_cells; /* kernel variant: cells of the wide profile held as int16 (0, 12, 14 or 16) */
-  int32_t reserved;         /* 0 */
+  int32_t wide_stage_depth; /* kernel variant: bank-2 windows fetched 1 or 2 passes ahead (0 = 1) */
   double narrow16_slot, narrow16_tile; /* 16 rows */
 } plast_tile_costs;
 int plast_autotune(void* stream, plast_tile_costs* out);

@@ -57,11 +57,11 @@ COST_FIELDS = ("wide_slot", "wide_tile", "narrow_slot", "narrow_tile", "narrow4_
 
 class plast_tile_costs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in COST_FIELDS[:8]] + \
-        [("wide_int16_cells", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+        [("wide_int16_cells", ctypes.c_int32), ("wide_stage_depth", ctypes.c_int32)] + \
         [(n, ctypes.c_double) for n in COST_FIELDS[8:]]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class PlastError(RuntimeError):
@@ -229,7 +229,8 @@ def plast_get_tile_costs() -> dict:
 
 def plast_set_tile_costs(costs: dict) -> None:
     c = plast_tile_costs(**{k: float(costs[k]) for k in COST_FIELDS},
-                         wide_int16_cells=int(costs.get("wide_int16_cells", 12)))
+                         wide_int16_cells=int(costs.get("wide_int16_cells", 12)),
+                         wide_stage_depth=int(costs.get("wide_stage_depth", 1)))
     rc = lib().plast_set_tile_costs(ctypes.byref(c))
     if rc:
         raise PlastError("plast_set_tile_costs", rc)

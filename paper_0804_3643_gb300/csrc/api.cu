@@ -151,8 +151,7 @@ plast_tile_costs g_costs = {0.317, 2960.0, 0.479, 566.0, 0.616, 1101.0, 1.094, 1
 std::atomic<int> g_shape{0};
 constexpr int64_t WIDE_PASS = (UNG_THREADS / 32) * 4;     // bank-2 windows per CTA pass, wide tile
 constexpr int64_t NARROW_PASS = UNG_NARROW_PASS;           // narrow tiles
-int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) & ~(g - 1); }  // g a power of two
-static_assert((WIDE_PASS & (WIDE_PASS - 1)) == 0 && (NARROW_PASS & (NARROW_PASS - 1)) == 0, "passes");
+int64_t round_up(int64_t n, int64_t g) { return (n + g - 1) / g * g; }
 
 int shape_rows(int shape) {
   switch (shape) {
@@ -1500,7 +1499,7 @@ int plast_get_tile_costs(plast_tile_costs* out) {
   std::lock_guard<std::mutex> lk(g_cost_mu);
   *out = g_costs;
   out->wide_int16_cells = ungapped_variant_n16(ungapped_variant());
-  out->reserved = 0;
+  out->wide_stage_depth = ungapped_variant_depth(ungapped_variant());
   return PLAST_OK;
 }
 
@@ -1511,12 +1510,13 @@ int plast_set_tile_costs(const plast_tile_costs* c) {
   for (int i = 0; i < UNG_SHAPES; i++)
     if (!(slot[i] > 0) || !(tile[i] >= 0) || slot[i] > 1e6 || tile[i] > 1e12) return PLAST_E_INVALID;
   int variant = -1;
+  const int depth = c->wide_stage_depth ? c->wide_stage_depth : 1;
   for (int v = 0; v < UNG_VARIANTS; v++)
-    if (ungapped_variant_n16(v) == c->wide_int16_cells) variant = v;
+    if (ungapped_variant_n16(v) == c->wide_int16_cells && ungapped_variant_depth(v) == depth) variant = v;
   if (variant < 0) return PLAST_E_INVALID;
   std::lock_guard<std::mutex> lk(g_cost_mu);
   g_costs = *c;
-  g_costs.reserved = 0;
+  g_costs.wide_stage_depth = depth;
   set_ungapped_variant(variant);
   return PLAST_OK;
 }
@@ -1585,18 +1585,24 @@ int plast_autotune(void* stream, plast_tile_costs* out) {
   const int saved_variant = ungapped_variant();
   double best_t = 0;
   int best_v = saved_variant;
-  for (int v = 0; v < UNG_VARIANTS && rc == PLAST_OK; v++) {
+  // the int16 cells at staging depth 1, then the staging depths of the best
+  auto try_variant = [&](int v, bool first) {
     set_ungapped_variant(v);
     double slot, tile, t_long;
     rc = fit(1, &slot, &tile, &t_long);
-    if (rc == PLAST_OK && (v == 0 || t_long < best_t)) {
+    if (rc == PLAST_OK && (first || t_long < best_t)) {
       best_t = t_long;
       best_v = v;
       c.wide_slot = slot;
       c.wide_tile = tile;
       c.wide_int16_cells = ungapped_variant_n16(v);
+      c.wide_stage_depth = ungapped_variant_depth(v);
     }
-  }
+  };
+  for (int v = 0; v < UNG_N16_VARIANTS && rc == PLAST_OK; v++) try_variant(v, v == 0);
+  for (int v = best_v % UNG_N16_VARIANTS + UNG_N16_VARIANTS; v < UNG_VARIANTS && rc == PLAST_OK;
+       v += UNG_N16_VARIANTS)
+    try_variant(v, false);
   set_ungapped_variant(rc == PLAST_OK ? best_v : saved_variant);
   double t_long;
   if (rc == PLAST_OK) rc = fit(2, &c.narrow_slot, &c.narrow_tile, &t_long);

@@ -41,7 +41,7 @@ constexpr int GAP = 80;
 // Launch geometry of the stage-2 kernel.
 constexpr int UNG_T1 = 128;        // bank-1 rows per wide profile tile
 constexpr int UNG_NT1 = 8;         // bank-1 rows per narrow profile tile
-constexpr int UNG_THREADS = 1024;  // 32 warps, one CTA per SM
+constexpr int UNG_THREADS = 768;   // 24 warps (85 registers a thread), one CTA per SM
 
 // BLOSUM62, upper triangle by rows, order A R N D C Q E G H I L K M F P S T W Y V
 // (Henikoff & Henikoff 1992).  Expanded to a 22 x 22 table with the stop row

@@ -67,7 +67,8 @@ constexpr int TAB_BYTES = 512;                             // int8 [22][22], pad
 constexpr int T24_STRIDE = 24;                             // bytes per residue a of the word table
 constexpr int T24_BYTES = 544;                             // int8 [22][24] (b = 22, 23 zero), padded
 constexpr int ROWS_BYTES = WIN * UNG_T1;                   // 6144, cell-major; shares the staging area
-constexpr int STAGE_BYTES = NWARPS * 4 * WIN;              // 6144: 4 bank-2 windows per warp
+constexpr int WSTAGE_BYTES = NWARPS * 4 * WIN;             // 4 bank-2 windows per warp
+constexpr int STAGE_BYTES = WSTAGE_BYTES > WIN * UNG_T1 ? WSTAGE_BYTES : WIN * UNG_T1;  // also the tile's rows
 constexpr int WKEY_BYTES = NWARPS * WBUF * 8;              // 8192
 constexpr int WVAL_BYTES = NWARPS * WBUF * 4;              // 4096
 static_assert(ROWS_BYTES <= STAGE_BYTES, "the tile's bank-1 rows fit the staging area");
@@ -531,7 +532,7 @@ __device__ __forceinline__ void narrow_tile(const UngArgs& a, int rows, int64_t 
   }
 }
 
-template <int N16>
+template <int N16, int DEPTH>
 __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
   using L = Wide<N16>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -640,21 +641,28 @@ __global__ void __launch_bounds__(UNG_THREADS, 1) k_ungapped(UngArgs a) {
       __syncthreads();
 
       const unsigned char* plane = prof + g * 16;
-      // lanes 0..11 fetch the warp's next 4 windows (12 x 16 bytes) one
-      // iteration ahead; sentinel windows past the end of the key.  Window
+      // lanes 0..11 fetch the warp's next 4 windows (12 x 16 bytes) DEPTH
+      // iterations ahead; sentinel windows past the end of the key.  Window
       // indexes are relative to the key's first (32-bit arithmetic).
       const int n2 = (int)(v1 - v0), lw = lane / 3;
       const uint4* src = reinterpret_cast<const uint4*>(a.nb2 + v0 * WIN) + lane % 3;
-      uint4 pre = sent16;
-      if (lane < 12 && warp * 4 + lw < n2) pre = __ldg(src + (int64_t)(warp * 4 + lw) * 3);
+      // (DEPTH passes ahead: the staging depth the autotuner picks)
+      uint4 pre[DEPTH];
+#pragma unroll
+      for (int d = 0; d < DEPTH; d++) {
+        const int vn = warp * 4 + d * NWARPS * 4 + lw;
+        pre[d] = lane < 12 && vn < n2 ? __ldg(src + (int64_t)vn * 3) : sent16;
+      }
       for (int vb = warp * 4; vb < n2; vb += NWARPS * 4) {
         const bool vok = vb + js < n2;
         __syncwarp();
-        if (lane < 12) my_stage[lane] = pre;
+        if (lane < 12) my_stage[lane] = pre[0];
         __syncwarp();
         if (lane < 12) {
-          const int vn = vb + NWARPS * 4 + lw;
-          pre = vn < n2 ? __ldg(src + (int64_t)vn * 3) : sent16;
+#pragma unroll
+          for (int d = 0; d + 1 < DEPTH; d++) pre[d] = pre[d + 1];
+          const int vn = vb + DEPTH * NWARPS * 4 + lw;
+          pre[DEPTH - 1] = vn < n2 ? __ldg(src + (int64_t)vn * 3) : sent16;
         }
         uint32_t s[8], m[8];
         {  // cells 0-3 from the folded seed planes
@@ -735,25 +743,39 @@ __global__ void __launch_bounds__(NT_THREADS, 2) k_ungapped_narrow(UngArgs a) {
 }
 
 namespace {
-std::atomic<int> g_variant{-1};  // index into UNG_N16 (-1: the default)
-constexpr int UNG_N16[UNG_VARIANTS] = {0, 12, 14, UNG_MAX_N16};
-constexpr int UNG_DEFAULT_VARIANT = 1;
+std::atomic<int> g_variant{-1};  // index into the variants (-1: the default)
+constexpr int UNG_N16[UNG_N16_VARIANTS] = {0, 12, 14, UNG_MAX_N16};
+constexpr int UNG_DEFAULT_VARIANT = 1;  // 12 int16 cells, one pass ahead
 
-template <int N16>
+template <int N16, int DEPTH>
 cudaError_t launch_variant(const UngArgs& a, int grid, cudaStream_t st) {
   static std::atomic<bool> attr_set[64];  // per device; calls may come from several threads
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_set[dev]) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_ungapped<N16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide<N16>::SMEM);
+        cudaFuncSetAttribute(k_ungapped<N16, DEPTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, Wide<N16>::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   if (grid <= 0) return cudaSuccess;
   note_launch();
-  k_ungapped<N16><<<grid, UNG_THREADS, Wide<N16>::SMEM, st>>>(a);
+  k_ungapped<N16, DEPTH><<<grid, UNG_THREADS, Wide<N16>::SMEM, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int DEPTH>
+cudaError_t launch_depth(int n16v, const UngArgs& a, int grid, cudaStream_t st) {
+  switch (n16v) {
+    case 0:
+      return launch_variant<UNG_N16[0], DEPTH>(a, grid, st);
+    case 1:
+      return launch_variant<UNG_N16[1], DEPTH>(a, grid, st);
+    case 3:
+      return launch_variant<UNG_N16[3], DEPTH>(a, grid, st);
+    default:
+      return launch_variant<UNG_N16[2], DEPTH>(a, grid, st);
+  }
 }
 }  // namespace
 
@@ -762,7 +784,9 @@ int ungapped_variant() {
   return v < 0 ? UNG_DEFAULT_VARIANT : v;
 }
 
-int ungapped_variant_n16(int v) { return v >= 0 && v < UNG_VARIANTS ? UNG_N16[v] : -1; }
+// variant v: int16 cells UNG_N16[v % 4], staging depth 1 + v / 4
+int ungapped_variant_n16(int v) { return v >= 0 && v < UNG_VARIANTS ? UNG_N16[v % UNG_N16_VARIANTS] : -1; }
+int ungapped_variant_depth(int v) { return v >= 0 && v < UNG_VARIANTS ? 1 + v / UNG_N16_VARIANTS : -1; }
 
 void set_ungapped_variant(int v) { g_variant.store(v); }
 
@@ -782,16 +806,9 @@ cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st) 
 }
 
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st) {
-  switch (ungapped_variant()) {
-    case 0:
-      return launch_variant<UNG_N16[0]>(a, grid, st);
-    case 1:
-      return launch_variant<UNG_N16[1]>(a, grid, st);
-    case 3:
-      return launch_variant<UNG_N16[3]>(a, grid, st);
-    default:
-      return launch_variant<UNG_N16[2]>(a, grid, st);
-  }
+  const int v = ungapped_variant();
+  return ungapped_variant_depth(v) == 2 ? launch_depth<2>(v % UNG_N16_VARIANTS, a, grid, st)
+                                        : launch_depth<1>(v % UNG_N16_VARIANTS, a, grid, st);
 }
 
 }  // namespace plast

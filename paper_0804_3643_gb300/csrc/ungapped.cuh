@@ -42,12 +42,15 @@ struct UngArgs {
 };
 
 // Wide-tile variants of the stage-2 kernel: how many cells the profile holds
-// as int16 (UNG_N16 in ungapped.cu: 0, 12, 14, UNG_MAX_N16).
-constexpr int UNG_VARIANTS = 4;
+// as int16 (UNG_N16 in ungapped.cu: 0, 12, 14, UNG_MAX_N16) and how many
+// passes ahead the bank-2 windows are fetched (the staging depth, 1 or 2).
+constexpr int UNG_N16_VARIANTS = 4;
+constexpr int UNG_VARIANTS = 2 * UNG_N16_VARIANTS;
 constexpr int UNG_MAX_N16 = 16;
-int ungapped_variant();            // the variant launch_ungapped runs
-int ungapped_variant_n16(int v);   // its int16 cells (-1 for no such variant)
-void set_ungapped_variant(int v);  // -1: the default
+int ungapped_variant();              // the variant launch_ungapped runs
+int ungapped_variant_n16(int v);     // its int16 cells (-1 for no such variant)
+int ungapped_variant_depth(int v);   // its staging depth (-1 for no such variant)
+void set_ungapped_variant(int v);    // -1: the default
 // wide tiles (the current variant) / narrow tiles, each a persistent launch
 cudaError_t launch_ungapped(const UngArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_ungapped_narrow(const UngArgs& a, int grid, cudaStream_t st);

@@ -126,8 +126,12 @@ def test_host_only_entry_points(lib):
     with pytest.raises(B.PlastError):
         B.plast_set_tile_costs(dict(c, wide_int16_cells=18))
     for n16 in (0, 12, 14, 16):
-        B.plast_set_tile_costs(dict(c, wide_int16_cells=n16))
-        assert B.plast_get_tile_costs()["wide_int16_cells"] == n16
+        for depth in (1, 2):
+            B.plast_set_tile_costs(dict(c, wide_int16_cells=n16, wide_stage_depth=depth))
+            got = B.plast_get_tile_costs()
+            assert got["wide_int16_cells"] == n16 and got["wide_stage_depth"] == depth
+    with pytest.raises(B.PlastError):
+        B.plast_set_tile_costs(dict(c, wide_stage_depth=3))
     B.plast_set_tile_costs(dict(c, wide_tile=c["wide_tile"] + 1))
     assert B.plast_get_tile_costs()["wide_tile"] == c["wide_tile"] + 1
     B.plast_set_tile_costs(c)

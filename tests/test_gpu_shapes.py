@@ -151,9 +151,11 @@ def test_autotune(B):
 
 
 def test_wide_variants_parity(B):
-    # every wide-kernel variant (int16 cells 0, 12, 14, 16) gives the oracle's hits,
-    # with full tiles, a ragged last tile and rows of sentinels
-    b1, b2 = synth.workload("plastp_plain", seed=8, scale=0.5)
+    # every wide-kernel variant (int16 cells 0, 12, 14, 16; bank-2 windows
+    # fetched one or two passes ahead) gives the oracle's hits, with full
+    # tiles, a ragged last tile and rows of sentinels; bank 2 large enough
+    # that keys span several passes of 96 windows
+    b1, b2 = synth.workload("plastp_plain", seed=8, scale=0.5, n2=8000)
     g1, o1 = both(B, b1.codes, b1.seq_off)
     g2, o2 = both(B, b2.codes, b2.seq_off)
     want = oracle.ungapped(o1, o2, threads=16)
@@ -163,9 +165,10 @@ def test_wide_variants_parity(B):
     try:
         B.plast_set_tile_shape(1)
         for n16 in (0, 12, 14, 16):
-            B.plast_set_tile_costs(dict(saved, wide_int16_cells=n16))
-            assert same(B.hits_numpy(B.plast_ungapped(g1, g2)), want)
-            assert same(B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s1=20))), want20)
+            for depth in (1, 2):
+                B.plast_set_tile_costs(dict(saved, wide_int16_cells=n16, wide_stage_depth=depth))
+                assert same(B.hits_numpy(B.plast_ungapped(g1, g2)), want)
+                assert same(B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s1=20))), want20)
     finally:
         B.plast_set_tile_shape(0)
         B.plast_set_tile_costs(saved)
