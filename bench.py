@@ -257,8 +257,7 @@ def stage31_roofline(hits: int, ms: float, n_sm: int, sm_max: float, sm_mhz) -> 
     floor4 = n_sm * ALU_LANES_PER_CLK_SM * 2 / 4 * sm_max * 1e6
     return {
         "bound": "alu",
-        "kernel": "stage 3.1: k_small_gapped (every survivor, scores) then k_gapped_ends (passing survivors, "
-                  "end cells), timed together",
+        "kernel": "stage 3.1: k_small_gapped (every stage-2 survivor: both sides' scores and end cells)",
         "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tcell/s", "frac": achieved / peak,
         "traffic": None, "cells_per_hit": BAND_CELLS_PER_HIT, "kernel_ms": ms,
         "peak_basis": f"{n_sm} SMs x {per_clk:.2f} cells/clock (ALU pipe 64 lanes x 2 int16 halves / 3 fused "
