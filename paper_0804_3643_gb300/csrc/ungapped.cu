@@ -259,9 +259,48 @@ __device__ __forceinline__ void narrow_pairs_reg(const uint32_t (&win)[12], cons
   }
 }
 
+// The lane's rows whose score reaches s1, as a mask with row 4q + j (half
+// j & 1 of word 2q + (j >> 1)) at bit 8j + q.  m - s1 is exact in int16
+// (-32 <= m <= 48 * 11: m starts at or above the folded seed cell M1 >= -32;
+// |s1| <= 30000), so the sign bit of a half is clear where the row reaches
+// s1; one prmt gathers the four sign bits of two words.
+template <int NW>
+__device__ __forceinline__ uint32_t hit_mask(const uint32_t (&m)[NW], uint32_t s1x2) {
+  if constexpr (NW == 1) {
+    const uint32_t x = ~__vsub2(m[0], s1x2);
+    return ((x >> 15) & 0x1u) | ((x >> 23) & 0x100u);
+  } else {
+    uint32_t mask = 0;
+#pragma unroll
+    for (int q = 0; q < NW / 2; q++) {
+      const uint32_t p = ~__byte_perm(__vsub2(m[2 * q], s1x2), __vsub2(m[2 * q + 1], s1x2), 0x7531u);
+      mask |= (p >> (7 - q)) & (0x01010101u << q);  // bits 7, 15, 23, 31: rows 4q .. 4q + 3
+    }
+    return mask;
+  }
+}
+
+// m[w] for a run-time w, by a select tree (no indexed register array).
+template <int NW>
+__device__ __forceinline__ uint32_t pick_word(const uint32_t (&m)[NW], int w) {
+  uint32_t v[NW];
+#pragma unroll
+  for (int i = 0; i < NW; i++) v[i] = m[i];
+#pragma unroll
+  for (int st = 1; st < NW; st <<= 1) {
+    const bool hi = (w & st) != 0;
+#pragma unroll
+    for (int i = 0; i < NW; i += 2 * st) v[i] = hi ? v[i + st] : v[i];
+  }
+  return v[0];
+}
+
 // Records the rows of this lane whose score reaches s1 against bank-2
 // occurrence v: rows r0 + i for i < 2 * NW (row 2w in the low half of m[w],
-// row 2w + 1 in the high half), of which the first valid_rows exist.
+// row 2w + 1 in the high half), of which the first valid_rows exist.  A warp
+// with no hit leaves after one vote; otherwise each lane walks its own set
+// bits, and the lanes' slots in the warp buffer come from one ballot when no
+// lane has more than one hit (the usual case), else from a shuffle scan.
 template <int NW>
 __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int valid_rows, int64_t r0, int64_t v,
                                           const UngArgs& a, uint32_t s1x2, int lane, uint64_t* my_wk,
@@ -280,23 +319,34 @@ __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int
   }
   const bool maybe = vok && __vcmpges2(mx, s1x2) != 0u;
   if (!__any_sync(0xffffffffu, maybe)) return;
-  unsigned mask = 0;
+  uint32_t mask = 0;
   if (maybe) {
+    mask = hit_mask<NW>(m, s1x2);
+    if (valid_rows < 2 * NW) {
+      uint32_t keep = 0;
 #pragma unroll
-    for (int w = 0; w < NW; w++) {
-      const uint32_t c = __vcmpges2(m[w], s1x2);
-      mask |= ((c & 1u) | ((c >> 15) & 2u)) << (2 * w);
+      for (int r = 0; r < 2 * NW; r++)
+        if (r < valid_rows) keep |= 1u << (8 * (r & 3) + (r >> 2));
+      mask &= keep;
     }
-    if (valid_rows < 2 * NW) mask &= valid_rows <= 0 ? 0u : ((1u << valid_rows) - 1u);
   }
   const int cnt = __popc(mask);
-  int incl = cnt;
+  const unsigned with = __ballot_sync(0xffffffffu, cnt != 0);
+  int excl, total;
+  if (__ballot_sync(0xffffffffu, cnt > 1) == 0u) {
+    excl = __popc(with & ((1u << lane) - 1u));
+    total = __popc(with);
+  } else {
+    int incl = cnt;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    excl = incl - cnt;
+    total = __shfl_sync(0xffffffffu, incl, 31);
   }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
   if (wcnt + total > WBUF) {
     __syncwarp();
     flush_warp(my_wk, my_wv, wcnt, lane, a.out_count, a.out_key, a.out_val, a.cap);
@@ -304,32 +354,33 @@ __device__ __forceinline__ void emit_hits(const uint32_t (&m)[NW], bool vok, int
     wcnt = 0;
   }
   const uint64_t p2 = vok ? (uint64_t)a.pos2[v] : 0;
+  int64_t at;  // this lane's first slot: in the warp buffer, or global when too many for it
   if (total > WBUF) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.out_count, (unsigned long long)total);
-    base = __shfl_sync(0xffffffffu, base, 0) + (incl - cnt);
-#pragma unroll
-    for (int i = 0; i < 2 * NW; i++)
-      if (mask & (1u << i)) {
-        const uint64_t p1 = a.pos1[r0 + i];
-        if ((int64_t)base < a.cap) {
-          a.out_key[base] = (p1 << a.sh) | p2;
-          a.out_val[base] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-        }
-        base++;
-      }
+    at = (int64_t)__shfl_sync(0xffffffffu, base, 0) + excl;
   } else {
-    int at = wcnt + incl - cnt;
-#pragma unroll
-    for (int i = 0; i < 2 * NW; i++)
-      if (mask & (1u << i)) {
-        const uint64_t p1 = a.pos1[r0 + i];
-        my_wk[at] = (p1 << a.sh) | p2;
-        my_wv[at] = (m[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-        at++;
-      }
-    wcnt += total;
+    at = wcnt + excl;
   }
+  while (mask) {
+    const int b = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    const int r = 4 * (b & 7) + (b >> 3);
+    const uint32_t wv = pick_word<NW>(m, r >> 1);
+    const uint64_t key = ((uint64_t)a.pos1[r0 + r] << a.sh) | p2;
+    const uint32_t val = (r & 1) ? (wv >> 16) : (wv & 0xffffu);
+    if (total > WBUF) {
+      if (at < a.cap) {
+        a.out_key[at] = key;
+        a.out_val[at] = val;
+      }
+    } else {
+      my_wk[at] = key;
+      my_wv[at] = val;
+    }
+    at++;
+  }
+  if (total <= WBUF) wcnt += total;
   __syncwarp();
 }
 
