@@ -43,8 +43,10 @@
 // through a sentinel cell comes back above the best cell of the clipped
 // grid, so the fixed band over i <= LG equals the one clipped at the sequence
 // ends.  Columns j < 0 start at -16000 and stay far below zero.  Columns
-// j > LG (rows i > LG - BAND) lie outside the grid; they feed no cell of the
-// grid and are kept out of the maximum (compile-time column limits).
+// j > LG (rows i > LG - BAND) lie outside the grid and feed no cell of it
+// (a cell reads only cells of its own or a smaller column), so they are not
+// computed (compile-time column limits); the stale values left in their
+// slots are read only by other such cells.
 #include <atomic>
 
 #include "gapped.cuh"
@@ -93,12 +95,13 @@ __device__ __forceinline__ uint32_t band_cell(Band& B, const unsigned char* row0
   return h;
 }
 
-template <int JB>
+// Cells 0 .. JLIM of row i (the cells JB > JLIM have j > LG, see below).
+template <int JB, int JLIM>
 __device__ __forceinline__ void band_cells(Band& B, const unsigned char* row0, const unsigned char* row1,
                                            uint32_t sb0, uint32_t sb1, uint32_t& E, const GapConst& k) {
-  if constexpr (JB < BW) {
+  if constexpr (JB <= JLIM) {
     band_cell<JB>(B, row0, row1, sb0, sb1, E, k);
-    band_cells<JB + 1>(B, row0, row1, sb0, sb1, E, k);
+    band_cells<JB + 1, JLIM>(B, row0, row1, sb0, sb1, E, k);
   }
 }
 
@@ -110,12 +113,13 @@ __device__ __forceinline__ uint32_t row_max(const Band& B, uint32_t m) {
   else return m;
 }
 
-// Row i; columns jb > JLIM have j > LG and stay out of the maximum.
+// Row i; columns jb > JLIM have j > LG: they are neither computed nor in the
+// maximum.
 template <int JLIM>
 __device__ __forceinline__ void gapped_row(Band& B, int i, const unsigned char* row0, const unsigned char* row1,
                                            uint32_t sb0, uint32_t sb1, const GapConst& k) {
   uint32_t E = x2(NEG16);
-  band_cells<0>(B, row0, row1, sb0 + i, sb1 + i, E, k);
+  band_cells<0, JLIM>(B, row0, row1, sb0 + i, sb1 + i, E, k);
   const uint32_t rmax = __vsub2(row_max<1, JLIM>(B, B.H[0]), x2(i * k.ge));  // without the row offset
   const uint32_t up = __vcmpgts2(rmax, B.best);  // 0xffff in the halves that improve
   B.best = __vmaxs2(B.best, rmax);
