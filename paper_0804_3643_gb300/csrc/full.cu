@@ -47,14 +47,23 @@ namespace plast {
 
 constexpr int FG_WARPS = 4;  // warps per CTA
 constexpr int32_t FG_NEG = -(1 << 28);
-constexpr int FG_SMEM = FG_WARPS * 4 * FG_W * 2;  // per warp: H and F of two rows (int16)
+constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 2) * 4;  // per warp: two rows of (H, F) int16 slots
 
 // The row above is kept in shared memory as int16 values relative to its
-// drop-off line thr = T - X: a live cell's H lies in [thr, thr + X + 11] (no
-// cell rises more than one diagonal step, at most 11, above the best of the
-// earlier rows), and an F below the line can neither keep a cell alive nor
-// give the H of a live one, so it is kept as -1 (dropped) like a dead cell.
-__device__ __forceinline__ int32_t dec16(int16_t v, int32_t thr) { return v >= 0 ? (int32_t)v + thr : FG_NEG; }
+// drop-off line thr = T - X, one 32-bit slot per column (H in the low half,
+// F in the high half): a live cell's H lies in [thr, thr + X + 11] (no cell
+// rises more than one diagonal step, at most 11, above the best of the
+// earlier rows), and a dead cell, or an F below the line, is stored as
+// -32768.  Decoded, such a value lies more than 32,000 below the line and
+// everything computed from it (by adding a score or subtracting gap costs)
+// stays below the line of this row and of every later one, so it can neither
+// keep a cell alive nor equal the H of a live cell: the scores, end cells
+// and paths are those of minus infinity, with no test per use.  Slot 0 of a
+// row (the column left of its first) and the slot after its last column
+// hold -32768 too, so the row below reads out-of-range columns as dead with
+// one clamp of the index.
+constexpr uint32_t FG_DEAD = 0x80008000u;
+constexpr int FG_SLOTS = FG_W + 2;  // per row buffer
 
 // One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
 // B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
@@ -66,7 +75,7 @@ struct SideOut {
 
 template <int DIR>
 __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int go, int ge, int X, const int8_t* tab,
-                           int16_t* Hbuf, int16_t* Fbuf, uint8_t* arena, int* err, int lane) {
+                           uint32_t* Sbuf, uint8_t* arena, int* err, int lane) {
   const int goe = go + ge;
   int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (c0, offset) per row
   const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
@@ -77,17 +86,17 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     return out;
   }
   int32_t T = 0, best = 0, bi = 0, bj = 0;
-  int plo = 0, phi = 0, pc0 = 0, pwid = 0;  // the row above: live columns, stored columns
+  int plo = 0, phi = 0, pc0 = 0, pwid = 0;  // the row above: live columns, first column, stored columns
   int32_t pthr = 0;                         // the row above's drop-off line
   int pb = 0;                               // buffer holding the row above
+  if (lane == 0) Sbuf[1] = FG_DEAD;         // row 0 has no row above: an empty one
+  __syncwarp();
   for (int i = 0; i <= la; i++) {
     const int c0 = i == 0 ? 0 : plo;
     const int lim = i == 0 ? 0 : phi + 1;  // the last column a cell of the row above can feed
     const int cb = pb ^ 1;
-    const int16_t* Hp = Hbuf + pb * FG_W;
-    const int16_t* Fp = Fbuf + pb * FG_W;
-    int16_t* Hc = Hbuf + cb * FG_W;
-    int16_t* Fc = Fbuf + cb * FG_W;
+    const uint32_t* Sp = Sbuf + pb * FG_SLOTS;
+    uint32_t* Sc = Sbuf + cb * FG_SLOTS;
     const int32_t thr = T - X;
     const int ai = i > 0 ? A[DIR * (i - 1)] : 0;
     const int8_t* trow = tab + ai * NCODE;
@@ -96,51 +105,50 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     int lo = -1, hi = -1, cend = c0;
     bool overflow = false;
     for (int cs = c0; cs <= lb; cs += 32) {
+      // capacity of the chunk's last column (the same test for every lane)
+      const int wl = min(cs + 31, lb) - c0;
+      if (wl + 1 > FG_W || off + wl >= FG_ARENA) {
+        overflow = true;
+        break;
+      }
       const int j = cs + lane;
       const bool in = j <= lb;
-      int32_t hd = FG_NEG, hu = FG_NEG, fu = FG_NEG;
-      if (i > 0 && in) {
-        const int kd = j - 1 - pc0, ku = j - pc0;
-        if (j >= 1 && kd >= 0 && kd < pwid) hd = dec16(Hp[kd], pthr);
-        if (ku >= 0 && ku < pwid) {
-          hu = dec16(Hp[ku], pthr);
-          fu = dec16(Fp[ku], pthr);
-        }
-      }
-      int32_t D = FG_NEG;
-      if (in && i > 0 && j >= 1 && hd > FG_NEG) D = hd + trow[B[DIR * (j - 1)]];
+      // row above: slot of column j is j - pc0 + 1 (j >= c0 >= pc0), clamped
+      // to the dead slot after its last column; column j - 1 one slot left
+      const int dj = j - pc0;
+      const uint32_t su = Sp[min(dj + 1, pwid + 1)];
+      const uint32_t sd = Sp[min(dj, pwid + 1)];
+      const int32_t hu = (int32_t)(int16_t)(su & 0xffffu) + pthr;
+      const int32_t fu = ((int32_t)su >> 16) + pthr;
+      const int32_t hd = (int32_t)(int16_t)(sd & 0xffffu) + pthr;
+      // (past the sequence end and at j = 0 B reads the sentinel padding)
+      const int32_t D = hd + trow[B[DIR * (j - 1)]];
       const int32_t F = max(fu - ge, hu - goe);
       int32_t DF = max(D, F);
       if (i == 0 && j == 0) DF = 0;
-      // E from the exclusive prefix maximum of DF(k) + k ge over the row
+      // E from the exclusive prefix maximum of DF(k) + k ge over the row (a
+      // lane below the shuffle distance gets its own value back)
       const int32_t P = in ? DF + j * ge : FG_NEG;
       int32_t incl = P;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl = max(incl, y);
-      }
+      for (int o = 1; o < 32; o <<= 1) incl = max(incl, __shfl_up_sync(0xffffffffu, incl, o));
       int32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
       excl = lane == 0 ? carryP : max(excl, carryP);
       const int32_t E = excl - go - j * ge;
-      int32_t H = max(DF, E);
+      const int32_t H = max(DF, E);
       const bool live = in && H >= thr;
       const int32_t Hs = live ? H : FG_NEG;
       int32_t hleft = __shfl_up_sync(0xffffffffu, Hs, 1);
       if (lane == 0) hleft = carryH;
-      // direction byte of the cell
-      const uint32_t src = (D > FG_NEG && H == D) ? 0u : (H == E ? 1u : 2u);
+      // direction byte of the cell (of use at live cells only: a value
+      // derived from a dead one never equals a live H)
+      const uint32_t src = H == D ? 0u : (H == E ? 1u : 2u);
       const uint32_t eop = (hleft > FG_NEG && E == hleft - goe) ? 4u : 0u;
-      const uint32_t fop = (hu > FG_NEG && F == hu - goe) ? 8u : 0u;
-      const int w = j - c0;
+      const uint32_t fop = F == hu - goe ? 8u : 0u;
       if (in) {
-        if (w < FG_W && off + w < FG_ARENA) {
-          Hc[w] = live ? (int16_t)(H - thr) : (int16_t)-1;
-          Fc[w] = live ? (int16_t)max(F - thr, -1) : (int16_t)-1;
-          arena[off + w] = (uint8_t)(src | eop | fop);
-        } else {
-          overflow = true;
-        }
+        const int w = j - c0;
+        Sc[w + 1] = live ? __byte_perm((uint32_t)(H - thr), (uint32_t)max(F - thr, -32768), 0x5410u) : FG_DEAD;
+        arena[off + w] = (uint8_t)(src | eop | fop);
       }
       // live window, row maximum (first column on ties)
       const unsigned lm = __ballot_sync(0xffffffffu, live);
@@ -150,7 +158,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
         const int32_t m = __reduce_max_sync(0xffffffffu, Hs);
         if (m > rmax) {
           rmax = m;
-          rarg = cs + __ffs(__ballot_sync(0xffffffffu, live && Hs == m)) - 1;
+          rarg = cs + __ffs(__ballot_sync(0xffffffffu, Hs == m)) - 1;
         }
       }
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
@@ -158,7 +166,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       cend = min(cs + 32, lb + 1);
       if (cs + 31 >= lim && !(lm >> 31)) break;  // past the row above's reach, last cell dropped
     }
-    if (__any_sync(0xffffffffu, overflow)) {
+    if (overflow) {
       if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
       return out;
     }
@@ -166,6 +174,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     if (lane == 0) {
       rowtab[2 * i] = c0;
       rowtab[2 * i + 1] = (int32_t)off;
+      Sc[cend - c0 + 1] = FG_DEAD;  // the dead slot after the row's last column
     }
     off += cend - c0;
     if (rmax > best) {
@@ -272,8 +281,8 @@ __global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
   for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int16_t* Hbuf = fsm + warp * 4 * FG_W;
-  int16_t* Fbuf = Hbuf + 2 * FG_W;
+  uint32_t* Sbuf = reinterpret_cast<uint32_t*>(fsm) + warp * 2 * FG_SLOTS;
+  if (lane == 0) Sbuf[0] = Sbuf[FG_SLOTS] = FG_DEAD;  // slot 0 of both rows: never written
   const int64_t gw = (int64_t)blockIdx.x * FG_WARPS + warp;
   uint8_t* arena = a.arena + gw * FG_ARENA;
   int32_t* segs = a.segs + gw * 3 * FG_SEGS;
@@ -297,15 +306,15 @@ __global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
       const int64_t x0 = s1 + r.pos1, y0 = s2 + r.pos2;  // padded anchor
       // right side: rows A_1.. = pad1[x0 ..], columns pad2[y0 ..]
       const SideOut R = side_dp<1>(a.pad1 + x0, len1 - r.pos1, a.pad2 + y0, len2 - r.pos2, a.go, a.ge, a.xdrop, tab,
-                                   Hbuf, Fbuf, arena, a.err, lane);
+                                   Sbuf, arena, a.err, lane);
       __syncwarp();
       PathStats st = {0, 0, 0, 0};
       Run rr = {0, 0, 0, 0}, lr = {0, 0, 0, 0};
       if (lane == 0) walk_side(arena, R.ei, R.ej, a.pad1, a.pad2, x0, y0, 1, s1, s2, &st, segs, &nseg, a.err, &rr);
       __syncwarp();
       // left side: rows A_1.. = pad1[x0 - 1 ..] backwards
-      const SideOut L = side_dp<-1>(a.pad1 + x0 - 1, r.pos1, a.pad2 + y0 - 1, r.pos2, a.go, a.ge, a.xdrop, tab, Hbuf,
-                                    Fbuf, arena, a.err, lane);
+      const SideOut L = side_dp<-1>(a.pad1 + x0 - 1, r.pos1, a.pad2 + y0 - 1, r.pos2, a.go, a.ge, a.xdrop, tab, Sbuf,
+                                    arena, a.err, lane);
       __syncwarp();
       if (lane == 0) {
         walk_side(arena, L.ei, L.ej, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, &st, segs, &nseg, a.err, &lr);
