@@ -742,7 +742,11 @@ def run_stage32(args, steps: int = 3) -> dict:
         call.append((time.perf_counter() - t1) * 1e3)
         kern.append(B.plast_stage_times()["upload_work_list"])  # interval 0: the extension kernel
     B.plast_set_timing(False)
+    cells = B.plast_full_gapped_cells()
     k_ms = statistics.median(kern)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(peaks().get("sm_max_mhz", 2070.0))
+    peak = n_sm * ALU_LANES_PER_CLK_SM * 2 / 3 * sm_max * 1e6
     return {
         "metric": "stage 3.2 (full gapped extension, trace-back fields) of a search's stage-3.1 records",
         "unit": "ms",
@@ -751,6 +755,16 @@ def run_stage32(args, steps: int = 3) -> dict:
         "records": int(recs.shape[0]), "extended": int(ext), "alignments": int(al.shape[0]),
         "xdrop": B.PLAST_XDROP, "kernel_ms": round(k_ms, 3), "call_ms": round(statistics.median(call), 3),
         "records_per_s": recs.shape[0] / (k_ms / 1e3),
+        "cells": cells, "gcups": cells / (k_ms / 1e3) / 1e9,
+        "roofline": {
+            "bound": "alu", "kernel": "k_full_gapped", "unit": "Tcell/s",
+            "achieved": cells / (k_ms / 1e3) / 1e12, "peak": peak / 1e12,
+            "frac": cells / (k_ms / 1e3) / peak,
+            "peak_basis": f"{n_sm} SMs x {ALU_LANES_PER_CLK_SM * 2 / 3:.2f} cells/clock (three fused add-max "
+                          f"instructions per cell, two cells per int16x2 instruction, as for stage 3.1) x "
+                          f"{sm_max:.0f} MHz; unit: every computed cell of every extended side, dropped ones "
+                          f"included (plast_full_gapped_cells)",
+        },
         "timing": f"kernel: CUDA events on the call's stream, median of {steps}; call: host wall time",
     }
 

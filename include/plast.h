@@ -287,6 +287,14 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
                       int64_t* n_out, int64_t* n_extended_out, void* stream);
 
 /*
+ * The dynamic-programming cells that the last plast_full_gapped call made on
+ * this host thread computed: every cell of every row of every extended side,
+ * the dropped ones included (the unit of stage 3.2's throughput).  0 before
+ * the first call and after a call that failed.
+ */
+int64_t plast_full_gapped_cells(void);
+
+/*
  * plast_small_gapped without device allocation.  The paper has no
  * counterpart to this call; it exists for callers that cannot let a library
  * allocate device memory: a framework that reserved the GPU's memory for its

@@ -148,6 +148,8 @@ def lib() -> ctypes.CDLL:
         L.plast_stage_times.restype = ctypes.c_int
         L.plast_kernel_launches.argtypes = []
         L.plast_kernel_launches.restype = ctypes.c_longlong
+        L.plast_full_gapped_cells.argtypes = []
+        L.plast_full_gapped_cells.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -211,6 +213,12 @@ def plast_stage_times() -> dict:
 
 def plast_kernel_launches() -> int:
     return int(lib().plast_kernel_launches())
+
+
+def plast_full_gapped_cells() -> int:
+    """Dynamic-programming cells the last plast_full_gapped call of this
+    thread computed (0 before any call and after a failed one)."""
+    return int(lib().plast_full_gapped_cells())
 
 
 def plast_autotune(stream=None) -> dict:

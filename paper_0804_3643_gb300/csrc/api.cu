@@ -977,10 +977,15 @@ int plast_search_ex(const plast_bank* b1, const plast_bank* b2, const plast_para
   return search_impl(b1, b2, params, s0, keys, n_keys, out, cap, n_out, n_ungapped_out, stream);
 }
 
+static thread_local int64_t t_full_cells = 0;  // cells of this thread's last plast_full_gapped
+
+int64_t plast_full_gapped_cells(void) { return t_full_cells; }
+
 int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_params* params, int32_t xdrop,
                       int32_t s3, const plast_gapped* in, int64_t n_in, plast_alignment* out, int64_t cap,
                       int64_t* n_out, int64_t* n_extended_out, void* stream) {
   NvtxRange nvtx_("plast_full_gapped (stage 3.2)");
+  t_full_cells = 0;
   if (!b1 || !b2 || !n_out || n_in < 0 || cap < 0 || !params_ok(params) || xdrop < 0 || xdrop > 30000)
     return PLAST_E_INVALID;
   if ((n_in > 0 && !in) || n_in > (int64_t)UINT32_MAX) return PLAST_E_INVALID;
@@ -1044,12 +1049,15 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
   uint8_t* arena;
   int32_t* segs;
   int* d_err;
+  unsigned long long* d_cells;
   CK(sc.get(&res, n));
   CK(sc.get(&done, n));
   CK(sc.get(&arena, (size_t)warps * FG_ARENA));
   CK(sc.get(&segs, (size_t)warps * 3 * FG_SEGS));
   CK(sc.get(&d_err, 1));
+  CK(sc.get(&d_cells, 1));
   CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(d_cells, 0, sizeof(unsigned long long), st));
   FullArgs fa;
   fa.pad1 = b1->pad;
   fa.pad2 = b2->pad;
@@ -1067,6 +1075,7 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
   fa.arena = arena;
   fa.segs = segs;
   fa.err = d_err;
+  fa.cells = d_cells;
   t_timer.reset();
   t_timer.mark(0, st);
   CK(launch_full_gapped(fa, warps, st));
@@ -1080,11 +1089,14 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
   CK(scan_exclusive(done, gstart, n, ext_dev, stmp, stb, st));
   int64_t m = 0, ext = 0;
   int h_err = 0;
+  unsigned long long cells = 0;
+  CK(cudaMemcpyAsync(&cells, d_cells, sizeof(cells), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&m, m_dev, sizeof(m), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&ext, ext_dev, sizeof(ext), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&h_err, d_err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h_err) return PLAST_E_CAPACITY;
+  t_full_cells = (int64_t)cells;
   *n_out = m;
   if (n_extended_out) *n_extended_out = ext;
   if (m > cap) return PLAST_E_CAPACITY;

@@ -71,6 +71,7 @@ constexpr int FG_SLOTS = FG_W + 2;  // per row buffer
 // `arena`.  *err gets FG_ERR_* bits on a capacity overflow.
 struct SideOut {
   int32_t score, ei, ej;
+  int64_t cells;  // computed cells, every row
 };
 
 template <int DIR>
@@ -80,7 +81,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (c0, offset) per row
   const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
   int64_t off = tab_bytes;
-  SideOut out = {0, 0, 0};
+  SideOut out = {0, 0, 0, 0};
   if (tab_bytes > FG_ARENA) {
     if (lane == 0) atomicOr(err, FG_ERR_ARENA);
     return out;
@@ -170,6 +171,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
       return out;
     }
+    out.cells += cend - c0;
     if (rmax == FG_NEG) break;  // no live cell: the side ends
     if (lane == 0) {
       rowtab[2 * i] = c0;
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
         al.gap_opens = st.gap_opens;
         a.res[rec] = al;
         a.done[rec] = 1;
+        atomicAdd(a.cells, (unsigned long long)(R.cells + L.cells));
       }
       nseg = __shfl_sync(0xffffffffu, nseg, 0);
       __syncwarp();

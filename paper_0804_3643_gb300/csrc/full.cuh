@@ -24,6 +24,7 @@ struct FullArgs {
   uint8_t* arena;           // FG_ARENA bytes per warp
   int32_t* segs;            // 3 * FG_SEGS ints per warp
   int* err;                 // FG_ERR_* bits
+  unsigned long long* cells;  // computed dynamic-programming cells, summed
 };
 
 // Warps the stage-3.2 kernel runs with on a GPU of n_sms SMs (the arena and

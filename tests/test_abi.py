@@ -111,6 +111,7 @@ def test_host_only_entry_points(lib):
     assert p.as_dict() == dict(w=4, nl=22, nr=22, s1=38, lg=64, band=8, gap_open=11, gap_extend=1, s2=47)
     assert B.plast_strerror(B.PLAST_E_CAPACITY) == "output capacity too small"
     assert B.plast_strerror(0) == "ok"
+    assert B.plast_full_gapped_cells() >= 0
     B.plast_set_schedule(1)
     B.plast_set_schedule(0)
     with pytest.raises(B.PlastError):

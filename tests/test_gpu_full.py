@@ -6,7 +6,9 @@ the trace-back fields and the redundant-alignment lists, byte for byte.
   with other gap costs, and with the records given in a shuffled order;
 * sampled keys of the 10,000 x 100,000 workload (the records of those keys,
   from plast_search_ex, extended on both sides);
-* error paths: bad records, bad drop-off, a capacity too small.
+* error paths: bad records, bad drop-off, a capacity too small, and a row
+  wider than the kernel's row buffer (reported, and the library still
+  answers the next call).
 """
 import numpy as np
 import pytest
@@ -112,3 +114,31 @@ def test_full_gapped_errors(B, plain):
     assert e.value.code == B.PLAST_E_CAPACITY and e.value.needed > 1
     empty, ext = B.plast_full_gapped(g1, g2, recs[:0])
     assert empty.shape[0] == 0 and ext == 0
+
+
+def test_full_gapped_row_wider_than_the_kernel_holds(B, plain):
+    # free gaps and the largest drop-off keep every cell of a 3,000-residue
+    # row alive, wider than the 1,024 columns a row buffer holds: the call
+    # reports PLAST_E_CAPACITY and returns nothing partial
+    rng = np.random.default_rng(3)
+    codes = rng.integers(0, 20, size=3000).astype(np.int8)
+    off = np.array([0, 3000], dtype=np.int64)
+    d = B.DeviceBank.from_host(codes, off)
+    g = B.plast_index_bank(d.codes, d.seq_off)
+    r = np.zeros(1, dtype=B.GAPPED_DTYPE)
+    r["pos1"] = r["pos2"] = 100
+    t = torch.from_numpy(r.view(np.uint8).reshape(-1, B.GAPPED_BYTES).copy()).cuda()
+    with pytest.raises(B.PlastError) as e:
+        B.plast_full_gapped(g, g, t, B.plast_default_params(gap_open=0, gap_extend=0), xdrop=30000)
+    assert e.value.code == B.PLAST_E_CAPACITY
+    assert B.plast_full_gapped_cells() == 0
+    # the same record at the default costs fits, and the library recovers;
+    # the anchor sits on the main diagonal of a sequence against itself, so
+    # both sides run to the sequence ends: at least one cell per row
+    got, ext = B.plast_full_gapped(g, g, t)
+    want = oracle.full_gapped(oracle.make_bank(codes, off), oracle.make_bank(codes, off), r)
+    assert ext == 1 and same(B.alignments_numpy(got), want)
+    assert B.plast_full_gapped_cells() >= 3000
+    g1, g2, o1, o2, recs = plain
+    again, _ = B.plast_full_gapped(g1, g2, recs)
+    assert same(B.alignments_numpy(again), oracle.full_gapped(o1, o2, B.gapped_numpy(recs), threads=8))
