@@ -47,7 +47,7 @@ namespace plast {
 
 constexpr int FG_WARPS = 4;  // warps per CTA
 constexpr int32_t FG_NEG = -(1 << 28);
-constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 2) * 4;  // per warp: two rows of (H, F) int16 slots
+constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 4) * 4;  // per warp: two rows of (H, F) int16 slots
 
 // The row above is kept in shared memory as int16 values relative to its
 // drop-off line thr = T - X, one 32-bit slot per column (H in the low half,
@@ -63,12 +63,21 @@ constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 2) * 4;  // per warp: two rows of
 // hold -32768 too, so the row below reads out-of-range columns as dead with
 // one clamp of the index.
 constexpr uint32_t FG_DEAD = 0x80008000u;
-constexpr int FG_SLOTS = FG_W + 2;  // per row buffer
+constexpr int FG_SLOTS = FG_W + 4;  // per row buffer: two dead slots before the row, two after
 
 // One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
 // B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
-// end cell; the directions and the row table (c0, offset per row) are in
+// end cell; the directions and the row table (origin, offset per row) are in
 // `arena`.  *err gets FG_ERR_* bits on a capacity overflow.
+//
+// A row is computed 64 columns at a time, two adjacent columns j0 = cs + 2l
+// and j0 + 1 per lane, from an even origin o at or left of the row's first
+// column c0 (a column left of c0 is not computed: it is dead and feeds
+// nothing), so that a row of the random extensions (about 40 columns) takes
+// one pass and one scan.  Column j is kept in slot j - o + 2 (slots 0 and 1
+// and the two after the row hold the dead value), so the two slots a lane
+// reads and writes are one aligned 8-byte word; the E scan runs over the
+// lanes' pairwise maxima.
 struct SideOut {
   int32_t score, ei, ej;
   int64_t cells;  // computed cells, every row
@@ -78,22 +87,23 @@ template <int DIR>
 __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int go, int ge, int X, const int8_t* tab,
                            uint32_t* Sbuf, uint8_t* arena, int* err, int lane) {
   const int goe = go + ge;
-  int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (c0, offset) per row
+  int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (origin, offset) per row
   const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
-  int64_t off = tab_bytes;
   SideOut out = {0, 0, 0, 0};
   if (tab_bytes > FG_ARENA) {
     if (lane == 0) atomicOr(err, FG_ERR_ARENA);
     return out;
   }
+  int off = (int)tab_bytes;  // even
   int32_t T = 0, best = 0, bi = 0, bj = 0;
-  int plo = 0, phi = 0, pc0 = 0, pwid = 0;  // the row above: live columns, first column, stored columns
-  int32_t pthr = 0;                         // the row above's drop-off line
-  int pb = 0;                               // buffer holding the row above
-  if (lane == 0) Sbuf[1] = FG_DEAD;         // row 0 has no row above: an empty one
+  int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first dead slot after it
+  int32_t pthr = 0;                       // the row above's drop-off line
+  int pb = 0;                             // buffer holding the row above
+  if (lane == 0) Sbuf[2] = Sbuf[3] = FG_DEAD;  // row 0 has no row above: an empty one
   __syncwarp();
   for (int i = 0; i <= la; i++) {
     const int c0 = i == 0 ? 0 : plo;
+    const int o = c0 & ~1;                 // the row's origin (even)
     const int lim = i == 0 ? 0 : phi + 1;  // the last column a cell of the row above can feed
     const int cb = pb ^ 1;
     const uint32_t* Sp = Sbuf + pb * FG_SLOTS;
@@ -105,80 +115,93 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     int32_t rmax = FG_NEG, rarg = 0;
     int lo = -1, hi = -1, cend = c0;
     bool overflow = false;
-    for (int cs = c0; cs <= lb; cs += 32) {
+    for (int cs = o; cs <= lb; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
-      const int wl = min(cs + 31, lb) - c0;
-      if (wl + 1 > FG_W || off + wl >= FG_ARENA) {
+      const int wl = min(cs + 63, lb) - o;
+      if (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA) {
         overflow = true;
         break;
       }
-      const int j = cs + lane;
-      const bool in = j <= lb;
-      // row above: slot of column j is j - pc0 + 1 (j >= c0 >= pc0), clamped
-      // to the dead slot after its last column; column j - 1 one slot left
-      const int dj = j - pc0;
-      const uint32_t su = Sp[min(dj + 1, pwid + 1)];
-      const uint32_t sd = Sp[min(dj, pwid + 1)];
-      const int32_t hu = (int32_t)(int16_t)(su & 0xffffu) + pthr;
-      const int32_t fu = ((int32_t)su >> 16) + pthr;
-      const int32_t hd = (int32_t)(int16_t)(sd & 0xffffu) + pthr;
-      // (past the sequence end and at j = 0 B reads the sentinel padding)
-      const int32_t D = hd + trow[B[DIR * (j - 1)]];
-      const int32_t F = max(fu - ge, hu - goe);
-      int32_t DF = max(D, F);
-      if (i == 0 && j == 0) DF = 0;
+      const int j0 = cs + 2 * lane, j1 = j0 + 1;
+      const bool in0 = j0 >= c0 && j0 <= lb, in1 = j1 <= lb;
+      // row above: columns j0 - 1, j0, j0 + 1 at slots kp - 1, kp, kp + 1
+      // (kp = j0 - po + 2, even), clamped to the dead slots after it
+      const int kp = j0 - po + 2;
+      const uint32_t sm = Sp[min(kp - 1, pw2)];
+      const uint2 sv = *reinterpret_cast<const uint2*>(Sp + min(kp, pw2));
+      const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu) + pthr;
+      const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu) + pthr, fu0 = ((int32_t)sv.x >> 16) + pthr;
+      const int32_t hu1 = (int32_t)(int16_t)(sv.y & 0xffffu) + pthr, fu1 = ((int32_t)sv.y >> 16) + pthr;
+      // (j = 0 and columns past the sequence end read the sentinel padding)
+      const int32_t D0 = hd0 + trow[B[DIR * (j0 - 1)]], D1 = hu0 + trow[B[DIR * j0]];
+      const int32_t hg0 = hu0 - goe, hg1 = hu1 - goe;
+      const int32_t F0 = max(fu0 - ge, hg0), F1 = max(fu1 - ge, hg1);
+      int32_t DF0 = max(D0, F0);
+      const int32_t DF1 = max(D1, F1);
+      if (i == 0 && j0 == 0) DF0 = 0;
       // E from the exclusive prefix maximum of DF(k) + k ge over the row (a
       // lane below the shuffle distance gets its own value back)
-      const int32_t P = in ? DF + j * ge : FG_NEG;
-      int32_t incl = P;
+      const int32_t P0 = in0 ? DF0 + j0 * ge : FG_NEG, P1 = in1 ? DF1 + j1 * ge : FG_NEG;
+      int32_t incl = max(P0, P1);
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) incl = max(incl, __shfl_up_sync(0xffffffffu, incl, o));
-      int32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
-      excl = lane == 0 ? carryP : max(excl, carryP);
-      const int32_t E = excl - go - j * ge;
-      const int32_t H = max(DF, E);
-      const bool live = in && H >= thr;
-      const int32_t Hs = live ? H : FG_NEG;
-      int32_t hleft = __shfl_up_sync(0xffffffffu, Hs, 1);
-      if (lane == 0) hleft = carryH;
-      // direction byte of the cell (of use at live cells only: a value
-      // derived from a dead one never equals a live H)
-      const uint32_t src = H == D ? 0u : (H == E ? 1u : 2u);
-      const uint32_t eop = (hleft > FG_NEG && E == hleft - goe) ? 4u : 0u;
-      const uint32_t fop = F == hu - goe ? 8u : 0u;
-      if (in) {
-        const int w = j - c0;
-        Sc[w + 1] = live ? __byte_perm((uint32_t)(H - thr), (uint32_t)max(F - thr, -32768), 0x5410u) : FG_DEAD;
-        arena[off + w] = (uint8_t)(src | eop | fop);
+      for (int d = 1; d < 32; d <<= 1) incl = max(incl, __shfl_up_sync(0xffffffffu, incl, d));
+      int32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+      ex = lane == 0 ? carryP : max(ex, carryP);
+      const int32_t E0 = ex - go - j0 * ge, E1 = max(ex, P0) - go - j1 * ge;
+      const int32_t H0 = max(DF0, E0), H1 = max(DF1, E1);
+      const bool live0 = in0 && H0 >= thr, live1 = in1 && H1 >= thr;
+      const int32_t H0s = live0 ? H0 : FG_NEG, H1s = live1 ? H1 : FG_NEG;
+      int32_t hl0 = __shfl_up_sync(0xffffffffu, H1s, 1);
+      if (lane == 0) hl0 = carryH;
+      // direction bytes (of use at live cells only: a value derived from a
+      // dead one never equals a live H)
+      const uint32_t d0 = (H0 == D0 ? 0u : (H0 == E0 ? 1u : 2u)) | ((hl0 > FG_NEG && E0 == hl0 - goe) ? 4u : 0u) |
+                          (F0 == hg0 ? 8u : 0u);
+      const uint32_t d1 = (H1 == D1 ? 0u : (H1 == E1 ? 1u : 2u)) | ((H0s > FG_NEG && E1 == H0s - goe) ? 4u : 0u) |
+                          (F1 == hg1 ? 8u : 0u);
+      if (in0 || in1) {
+        const int w = j0 - o;  // even
+        *reinterpret_cast<uint2*>(Sc + w + 2) =
+            make_uint2(live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)max(F0 - thr, -32768), 0x5410u) : FG_DEAD,
+                       live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)max(F1 - thr, -32768), 0x5410u) : FG_DEAD);
+        *reinterpret_cast<uint16_t*>(arena + off + w) = (uint16_t)(d0 | (d1 << 8));
       }
       // live window, row maximum (first column on ties)
-      const unsigned lm = __ballot_sync(0xffffffffu, live);
+      const unsigned lm0 = __ballot_sync(0xffffffffu, live0), lm1 = __ballot_sync(0xffffffffu, live1);
+      const unsigned lm = lm0 | lm1;
       if (lm) {
-        if (lo < 0) lo = cs + __ffs(lm) - 1;
-        hi = cs + 31 - __clz(lm);
-        const int32_t m = __reduce_max_sync(0xffffffffu, Hs);
+        if (lo < 0) {
+          const int l = __ffs(lm) - 1;
+          lo = cs + 2 * l + (((lm0 >> l) & 1u) ? 0 : 1);
+        }
+        const int l = 31 - __clz(lm);
+        hi = cs + 2 * l + (int)((lm1 >> l) & 1u);
+        const int32_t m = __reduce_max_sync(0xffffffffu, max(H0s, H1s));
         if (m > rmax) {
           rmax = m;
-          rarg = cs + __ffs(__ballot_sync(0xffffffffu, Hs == m)) - 1;
+          const unsigned c = __ballot_sync(0xffffffffu, H0s == m), d = __ballot_sync(0xffffffffu, H1s == m);
+          const int f = __ffs(c | d) - 1;
+          rarg = cs + 2 * f + (((c >> f) & 1u) ? 0 : 1);
         }
       }
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
-      carryH = __shfl_sync(0xffffffffu, Hs, 31);
-      cend = min(cs + 32, lb + 1);
-      if (cs + 31 >= lim && !(lm >> 31)) break;  // past the row above's reach, last cell dropped
+      carryH = __shfl_sync(0xffffffffu, H1s, 31);
+      cend = min(cs + 64, lb + 1);
+      if (cs + 63 >= lim && !(lm1 >> 31)) break;  // past the row above's reach, last cell dropped
     }
     if (overflow) {
       if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
       return out;
     }
+    const int cw = (cend - o + 1) & ~1;  // stored columns, even
     out.cells += cend - c0;
     if (rmax == FG_NEG) break;  // no live cell: the side ends
     if (lane == 0) {
-      rowtab[2 * i] = c0;
-      rowtab[2 * i + 1] = (int32_t)off;
-      Sc[cend - c0 + 1] = FG_DEAD;  // the dead slot after the row's last column
+      rowtab[2 * i] = o;
+      rowtab[2 * i + 1] = off;
+      Sc[cw + 2] = Sc[cw + 3] = FG_DEAD;  // the dead slots after the row
     }
-    off += cend - c0;
+    off += cw;
     if (rmax > best) {
       best = rmax;
       bi = i;
@@ -187,8 +210,8 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     T = max(T, rmax);
     plo = lo;
     phi = hi;
-    pc0 = c0;
-    pwid = cend - c0;
+    po = o;
+    pw2 = cw + 2;
     pthr = thr;
     pb = cb;
     __syncwarp();
@@ -277,14 +300,14 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pa
   flush(true);
 }
 
-__global__ void __launch_bounds__(FG_WARPS * 32) k_full_gapped(FullArgs a) {
+__global__ void __launch_bounds__(FG_WARPS * 32, 5) k_full_gapped(FullArgs a) {
   __shared__ int8_t tab[NCODE * NCODE];
   extern __shared__ __align__(16) int16_t fsm[];
   for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* Sbuf = reinterpret_cast<uint32_t*>(fsm) + warp * 2 * FG_SLOTS;
-  if (lane == 0) Sbuf[0] = Sbuf[FG_SLOTS] = FG_DEAD;  // slot 0 of both rows: never written
+  if (lane == 0) Sbuf[0] = Sbuf[1] = Sbuf[FG_SLOTS] = Sbuf[FG_SLOTS + 1] = FG_DEAD;  // never written
   const int64_t gw = (int64_t)blockIdx.x * FG_WARPS + warp;
   uint8_t* arena = a.arena + gw * FG_ARENA;
   int32_t* segs = a.segs + gw * 3 * FG_SEGS;
