@@ -142,3 +142,37 @@ def test_full_gapped_row_wider_than_the_kernel_holds(B, plain):
     g1, g2, o1, o2, recs = plain
     again, _ = B.plast_full_gapped(g1, g2, recs)
     assert same(B.alignments_numpy(again), oracle.full_gapped(o1, o2, B.gapped_numpy(recs), threads=8))
+
+
+def test_full_gapped_largest_drop_off_and_free_gaps(B):
+    # X = 30000 keeps every cell alive: the rows' int16 values, relative to
+    # the drop-off line, reach X + 11, the edge of their range; free gaps
+    # (go = ge = 0) make E and F tie with the diagonal everywhere and keep
+    # whole rows alive too.  Sequences of at most 400 residues keep a side
+    # within the kernel's working space (longer ones get PLAST_E_CAPACITY);
+    # the records are anchors drawn at random (stage 3.2 takes any record),
+    # some on planted homologs, several per pair of sequences
+    rng = np.random.default_rng(9)
+    src = synth.random_protein_bank(rng, 12)
+    seqs = [src.seq(i)[:400] for i in range(12)]
+    codes = np.concatenate(seqs).astype(np.int8)
+    off = np.zeros(13, dtype=np.int64)
+    np.cumsum([len(q) for q in seqs], out=off[1:])
+    hom = [synth.mutate(rng, q, 0.7)[:400] for q in seqs[:6]] + [src.seq(i)[:400] for i in range(6, 12)]
+    codes2 = np.concatenate(hom).astype(np.int8)
+    off2 = np.zeros(13, dtype=np.int64)
+    np.cumsum([len(q) for q in hom], out=off2[1:])
+    g1, g2, o1, o2 = banks(B, synth.SynthBank(codes, off), synth.SynthBank(codes2, off2))
+    r = np.zeros(60, dtype=B.GAPPED_DTYPE)
+    r["seq1"] = rng.integers(0, 12, size=60)
+    r["seq2"] = np.where(rng.random(60) < 0.6, r["seq1"], rng.integers(0, 12, size=60))
+    r["pos1"] = [rng.integers(0, off[s + 1] - off[s]) for s in r["seq1"]]
+    r["pos2"] = [rng.integers(0, off2[s + 1] - off2[s]) for s in r["seq2"]]
+    r["score"] = rng.integers(40, 200, size=60)
+    t = torch.from_numpy(r.view(np.uint8).reshape(-1, B.GAPPED_BYTES).copy()).cuda()
+    for x, go, ge in ((30000, 11, 1), (5000, 11, 1), (20, 0, 0), (30000, 0, 0)):
+        want, ext_w = oracle.full_gapped(o1, o2, r, oracle.Params(gap_open=go, gap_extend=ge), x=x, s3=-10 ** 6,
+                                         return_extended=True)
+        got, ext = B.plast_full_gapped(g1, g2, t, B.plast_default_params(gap_open=go, gap_extend=ge), xdrop=x,
+                                       s3=-10 ** 6)
+        assert ext == ext_w and same(B.alignments_numpy(got), want), (x, go, ge)
