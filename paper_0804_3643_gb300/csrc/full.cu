@@ -27,17 +27,20 @@
 // the row above's live cells whose last cell is dropped (beyond them only E
 // feeds a cell, and it only falls).
 //
-// Each cell leaves one direction byte in the warp's arena (global memory):
-// the source of H (0 diagonal, 1 E, 2 F, in that order of preference), and
-// whether E and F open their gap at this cell (preferred over an extension
-// of equal value).  After the side's last row, lane 0 walks back from the end
-// cell (first maximum in row-major order) to the anchor, counting the
-// alignment's columns, identities and gap runs and emitting its gap-free
+// Each live cell leaves its H (int16, relative to its row's drop-off line)
+// in the warp's arena (global memory), a dead one a dead marker.  After the
+// side's last row, lane 0 walks back from the end cell (first maximum in
+// row-major order) to the anchor, taking at each cell the source the
+// recurrences give in the order of preference diagonal, E, F, and opening a
+// gap in preference to extending one of equal value, all from the stored H
+// values of the cell's row and the row above (an E is recomputed along its
+// row when the diagonal does not give the cell's H); it counts the
+// alignment's columns, identities and gap runs and emits its gap-free
 // segments (diagonal pos1 - pos2, first and last pos1).
 //
 // Limits (reported as PLAST_E_CAPACITY by the call): a row of more than
-// FG_W computed columns, more than FG_ARENA bytes of directions and row
-// table for one side, more than FG_SEGS segments for one pair of sequences.
+// FG_W computed columns, more than FG_ARENA bytes of H values and row table
+// for one side, more than FG_SEGS segments for one pair of sequences.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -87,14 +90,15 @@ template <int DIR>
 __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int go, int ge, int X, const int8_t* tab,
                            uint32_t* Sbuf, uint8_t* arena, int* err, int lane) {
   const int goe = go + ge;
-  int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (origin, offset) per row
-  const int64_t tab_bytes = ((int64_t)8 * (la + 1) + 15) & ~(int64_t)15;
+  int32_t* rowtab = reinterpret_cast<int32_t*>(arena);  // (origin, offset, line, stored columns) per row
+  int16_t* hval = reinterpret_cast<int16_t*>(arena);     // H of the stored columns, from the offset
+  const int64_t tab_bytes = (int64_t)16 * (la + 1);
   SideOut out = {0, 0, 0, 0};
   if (tab_bytes > FG_ARENA) {
     if (lane == 0) atomicOr(err, FG_ERR_ARENA);
     return out;
   }
-  int off = (int)tab_bytes;  // even
+  int off = (int)(tab_bytes / 2);  // in int16 units, even
   int32_t T = 0, best = 0, bi = 0, bj = 0;
   int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first dead slot after it
   int32_t pthr = 0;                       // the row above's drop-off line
@@ -111,14 +115,14 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     const int32_t thr = T - X;
     const int ai = i > 0 ? A[DIR * (i - 1)] : 0;
     const int8_t* trow = tab + ai * NCODE;
-    int32_t carryP = FG_NEG, carryH = FG_NEG;
+    int32_t carryP = FG_NEG;
     int32_t rmax = FG_NEG, rarg = 0;
     int lo = -1, hi = -1, cend = c0;
     bool overflow = false;
     for (int cs = o; cs <= lb; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
       const int wl = min(cs + 63, lb) - o;
-      if (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA) {
+      if (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA / 2) {
         overflow = true;
         break;
       }
@@ -151,20 +155,14 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       const int32_t H0 = max(DF0, E0), H1 = max(DF1, E1);
       const bool live0 = in0 && H0 >= thr, live1 = in1 && H1 >= thr;
       const int32_t H0s = live0 ? H0 : FG_NEG, H1s = live1 ? H1 : FG_NEG;
-      int32_t hl0 = __shfl_up_sync(0xffffffffu, H1s, 1);
-      if (lane == 0) hl0 = carryH;
-      // direction bytes (of use at live cells only: a value derived from a
-      // dead one never equals a live H)
-      const uint32_t d0 = (H0 == D0 ? 0u : (H0 == E0 ? 1u : 2u)) | ((hl0 > FG_NEG && E0 == hl0 - goe) ? 4u : 0u) |
-                          (F0 == hg0 ? 8u : 0u);
-      const uint32_t d1 = (H1 == D1 ? 0u : (H1 == E1 ? 1u : 2u)) | ((H0s > FG_NEG && E1 == H0s - goe) ? 4u : 0u) |
-                          (F1 == hg1 ? 8u : 0u);
       if (in0 || in1) {
         const int w = j0 - o;  // even
-        *reinterpret_cast<uint2*>(Sc + w + 2) =
-            make_uint2(live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)max(F0 - thr, -32768), 0x5410u) : FG_DEAD,
-                       live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)max(F1 - thr, -32768), 0x5410u) : FG_DEAD);
-        *reinterpret_cast<uint16_t*>(arena + off + w) = (uint16_t)(d0 | (d1 << 8));
+        const uint32_t v0 = live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)max(F0 - thr, -32768), 0x5410u)
+                                  : FG_DEAD;
+        const uint32_t v1 = live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)max(F1 - thr, -32768), 0x5410u)
+                                  : FG_DEAD;
+        *reinterpret_cast<uint2*>(Sc + w + 2) = make_uint2(v0, v1);
+        *reinterpret_cast<uint32_t*>(hval + off + w) = __byte_perm(v0, v1, 0x5410u);  // the two H halves
       }
       // live window, row maximum (first column on ties)
       const unsigned lm0 = __ballot_sync(0xffffffffu, live0), lm1 = __ballot_sync(0xffffffffu, live1);
@@ -185,7 +183,6 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
         }
       }
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
-      carryH = __shfl_sync(0xffffffffu, H1s, 31);
       cend = min(cs + 64, lb + 1);
       if (cs + 63 >= lim && !(lm1 >> 31)) break;  // past the row above's reach, last cell dropped
     }
@@ -197,8 +194,10 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     out.cells += cend - c0;
     if (rmax == FG_NEG) break;  // no live cell: the side ends
     if (lane == 0) {
-      rowtab[2 * i] = o;
-      rowtab[2 * i + 1] = off;
+      rowtab[4 * i] = o;
+      rowtab[4 * i + 1] = off;
+      rowtab[4 * i + 2] = thr;
+      rowtab[4 * i + 3] = cw;
       Sc[cw + 2] = Sc[cw + 3] = FG_DEAD;  // the dead slots after the row
     }
     off += cw;
@@ -234,11 +233,34 @@ struct Run {
   int32_t diag, start, stop, len;
 };
 
-__device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pad1, const int8_t* pad2, int64_t x1,
-                          int64_t y1, int dir, int64_t xoff, int64_t yoff, PathStats* st, int32_t* segs, int* nseg,
-                          int* err, Run* anchor_run) {
-  const int32_t* rowtab = reinterpret_cast<const int32_t*>(arena);
+// H(i, j) of a side from its arena (FG_NEG where the cell is dead or was not
+// computed).
+__device__ __forceinline__ int32_t stored_h(const uint8_t* arena, int i, int j) {
+  const int32_t* t = reinterpret_cast<const int32_t*>(arena) + 4 * i;
+  const int k = j - t[0];
+  if (k < 0 || k >= t[3]) return FG_NEG;
+  const int v = reinterpret_cast<const int16_t*>(arena)[t[1] + k];
+  return v == -32768 ? FG_NEG : v + t[2];
+}
+
+// Lane 0: the path of a side from its end cell (ei, ej), whose H is `score`,
+// back to the anchor.  Row i takes A_i = pad1[x1 + dir (i - 1)], column j
+// B_j = pad2[y1 + dir (j - 1)].  At a cell in state H the diagonal is taken
+// when H = H(i - 1, j - 1) + s(A_i, B_j) with the diagonal cell live, else E
+// when H equals the row's E there (max over the live cells k < j of the row
+// of H(i, k) - go - (j - k) ge, the value the extension's prefix maximum
+// gives: a term through a dropped cell lies below the line), else F; a gap
+// opens at the first cell back where its value equals the live neighbour's
+// H - go - ge.  Columns are counted into *st; gap-free runs are appended to
+// segs (pos1 coordinates are local: x - xoff), except the run that reaches
+// the anchor, returned in *anchor_run (valid when its length is > 0).
+__device__ void walk_side(const uint8_t* arena, int ei, int ej, int32_t score, const int8_t* pad1,
+                          const int8_t* pad2, int64_t x1, int64_t y1, int dir, int64_t xoff, int64_t yoff, int go,
+                          int ge, const int8_t* tab, PathStats* st, int32_t* segs, int* nseg, int* err,
+                          Run* anchor_run) {
+  const int goe = go + ge;
   int i = ei, j = ej, state = 0, prev_gap = 0;
+  int32_t v = score;  // the value of the current state at (i, j)
   Run cur = {0, 0, 0, 0};
   auto flush = [&](bool at_anchor) {
     if (cur.len == 0) return;
@@ -255,12 +277,11 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pa
     cur.len = 0;
   };
   while (i > 0 || j > 0) {
-    const uint8_t d = arena[rowtab[2 * i + 1] + (j - rowtab[2 * i])];
     if (state == 0) {
-      const uint32_t src = d & 3u;
-      if (src == 0) {
+      const int64_t x = x1 + (int64_t)dir * (i - 1), y = y1 + (int64_t)dir * (j - 1);
+      const int32_t hd = i > 0 && j > 0 ? stored_h(arena, i - 1, j - 1) : FG_NEG;
+      if (hd > FG_NEG && v == hd + tab[pad1[x] * NCODE + pad2[y]]) {
         // residue pair (A_i, B_j)
-        const int64_t x = x1 + (int64_t)dir * (i - 1), y = y1 + (int64_t)dir * (j - 1);
         if (pad1[x] == pad2[y]) st->identities++;
         else st->mismatches++;
         st->length++;
@@ -278,8 +299,17 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pa
         prev_gap = 0;
         i--;
         j--;
+        v = hd;
       } else {
-        state = (int)src;
+        // E of the cell from its row, left to right
+        const int32_t* t = reinterpret_cast<const int32_t*>(arena) + 4 * i;
+        int32_t e = FG_NEG;
+        for (int k = t[0]; k < j; k++) e = max(e - ge, stored_h(arena, i, k) - goe);
+        state = v == e ? 1 : 2;
+        // (row 0 has no F and column 0 no E: the recurrences never lead
+        // there; the walk stays on the grid regardless)
+        if (i == 0) state = 1;
+        else if (j == 0) state = 2;
       }
     } else {
       flush(false);  // a gap ends the current run
@@ -289,10 +319,22 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, const int8_t* pa
       // a run is a stretch of equal gap columns, whatever the path's
       // opening decisions (with a free opening a run may open twice)
       if (state == 1) {  // gap in A: B_j against nothing
-        state = (d & 4u) ? 0 : 1;
+        const int32_t hl = stored_h(arena, i, j - 1);
+        if (hl > FG_NEG && v == hl - goe) {
+          state = 0;
+          v = hl;
+        } else {
+          v += ge;
+        }
         j--;
       } else {           // gap in B: A_i against nothing
-        state = (d & 8u) ? 0 : 2;
+        const int32_t hu = stored_h(arena, i - 1, j);
+        if (hu > FG_NEG && v == hu - goe) {
+          state = 0;
+          v = hu;
+        } else {
+          v += ge;
+        }
         i--;
       }
     }
@@ -335,14 +377,17 @@ __global__ void __launch_bounds__(FG_WARPS * 32, 5) k_full_gapped(FullArgs a) {
       __syncwarp();
       PathStats st = {0, 0, 0, 0};
       Run rr = {0, 0, 0, 0}, lr = {0, 0, 0, 0};
-      if (lane == 0) walk_side(arena, R.ei, R.ej, a.pad1, a.pad2, x0, y0, 1, s1, s2, &st, segs, &nseg, a.err, &rr);
+      if (lane == 0)
+        walk_side(arena, R.ei, R.ej, R.score, a.pad1, a.pad2, x0, y0, 1, s1, s2, a.go, a.ge, tab, &st, segs, &nseg,
+                  a.err, &rr);
       __syncwarp();
       // left side: rows A_1.. = pad1[x0 - 1 ..] backwards
       const SideOut L = side_dp<-1>(a.pad1 + x0 - 1, r.pos1, a.pad2 + y0 - 1, r.pos2, a.go, a.ge, a.xdrop, tab, Sbuf,
                                     arena, a.err, lane);
       __syncwarp();
       if (lane == 0) {
-        walk_side(arena, L.ei, L.ej, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, &st, segs, &nseg, a.err, &lr);
+        walk_side(arena, L.ei, L.ej, L.score, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, a.go, a.ge, tab, &st, segs,
+                  &nseg, a.err, &lr);
         // the runs that reach the anchor from both sides are one segment
         if (rr.len > 0 || lr.len > 0) {
           Run m = rr.len > 0 ? rr : lr;
