@@ -125,6 +125,20 @@ def test_thresholds_and_gap_costs(B, plain):
         assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want_h, prm))
 
 
+def test_ungapped_threshold_range_edges(B, plain):
+    # S1 at the ends of its range: the stage-2 kernels find the hit rows from
+    # the sign of m - S1 in int16, which stays exact from -30000 to 30000
+    g1, o1, g2, o2 = plain
+    for s1 in (30000, 29, -30000):
+        got = B.hits_numpy(B.plast_ungapped(g1, g2, B.plast_default_params(s1=s1)))
+        want = oracle.ungapped(o1, o2, oracle.Params(s1=s1))
+        assert same(got, want), s1
+        if s1 == 30000:
+            assert len(want) == 0
+        if s1 == -30000:
+            assert len(want) == B.plast_pair_count(g1, g2)  # every pair
+
+
 def test_gap_cost_limits(B, plain):
     g1, _, g2, _ = plain
     for go, ge in [(1001, 1), (11, 401), (-1, 1), (11, -1)]:
