@@ -56,16 +56,18 @@ constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 4) * 4;  // per warp: two rows of
 // drop-off line thr = T - X, one 32-bit slot per column (H in the low half,
 // F in the high half): a live cell's H lies in [thr, thr + X + 11] (no cell
 // rises more than one diagonal step, at most 11, above the best of the
-// earlier rows), and a dead cell, or an F below the line, is stored as
-// -32768.  Decoded, such a value lies more than 32,000 below the line and
-// everything computed from it (by adding a score or subtracting gap costs)
-// stays below the line of this row and of every later one, so it can neither
-// keep a cell alive nor equal the H of a live cell: the scores, end cells
-// and paths are those of minus infinity, with no test per use.  Slot 0 of a
-// row (the column left of its first) and the slot after its last column
-// hold -32768 too, so the row below reads out-of-range columns as dead with
-// one clamp of the index.
-constexpr uint32_t FG_DEAD = 0x80008000u;
+// earlier rows), and a dead cell is stored as -30000 in both halves.
+// Decoded, such a value lies 30,000 below the line and everything computed
+// from it (adding a score, subtracting gap costs) stays below the line of
+// this row and of every later one, so it can neither keep a cell alive nor
+// equal the H of a live cell: the scores, end cells and paths are those of
+// minus infinity, with no test per use.  A live cell's F needs no clamp: it
+// comes from a dead slot (so it lies within go + ge + 11 of -30000) or from
+// a live H above (within go + ge of the line), so it stays in int16.  Slots
+// 0 and 1 of a row buffer and the two after a row hold the dead value too,
+// so the row below reads out-of-range columns through one clamped index.
+constexpr int FG_DEAD16 = -30000;
+constexpr uint32_t FG_DEAD = 0x8AD08AD0u;  // FG_DEAD16 in both halves
 constexpr int FG_SLOTS = FG_W + 4;  // per row buffer: two dead slots before the row, two after
 
 // One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
@@ -157,10 +159,8 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       const int32_t H0s = live0 ? H0 : FG_NEG, H1s = live1 ? H1 : FG_NEG;
       if (in0 || in1) {
         const int w = j0 - o;  // even
-        const uint32_t v0 = live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)max(F0 - thr, -32768), 0x5410u)
-                                  : FG_DEAD;
-        const uint32_t v1 = live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)max(F1 - thr, -32768), 0x5410u)
-                                  : FG_DEAD;
+        const uint32_t v0 = live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)(F0 - thr), 0x5410u) : FG_DEAD;
+        const uint32_t v1 = live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)(F1 - thr), 0x5410u) : FG_DEAD;
         *reinterpret_cast<uint2*>(Sc + w + 2) = make_uint2(v0, v1);
         *reinterpret_cast<uint32_t*>(hval + off + w) = __byte_perm(v0, v1, 0x5410u);  // the two H halves
       }
@@ -240,7 +240,7 @@ __device__ __forceinline__ int32_t stored_h(const uint8_t* arena, int i, int j) 
   const int k = j - t[0];
   if (k < 0 || k >= t[3]) return FG_NEG;
   const int v = reinterpret_cast<const int16_t*>(arena)[t[1] + k];
-  return v == -32768 ? FG_NEG : v + t[2];
+  return v == FG_DEAD16 ? FG_NEG : v + t[2];
 }
 
 // Lane 0: the path of a side from its end cell (ei, ej), whose H is `score`,
