@@ -69,8 +69,8 @@ def merge_queries(reqs: list) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
 
 
 def split_records(recs: np.ndarray, first: np.ndarray) -> list:
-    """Records of a merged batch, cut per request, seq1 renumbered locally.
-    ``recs`` is sorted by seq1 (canonical order)."""
+    """Records (or alignments) of a merged batch, cut per request, seq1
+    renumbered locally.  ``recs`` is sorted by seq1 (canonical order)."""
     out = []
     cuts = np.searchsorted(recs["seq1"], first)
     for q in range(len(first) - 1):
@@ -199,9 +199,15 @@ def latency_summary(reqs: list[Request], pairs: int, wall: float) -> dict:
 
 
 class GpuExecutor:
-    """Runs batches through the library against a resident bank (bank 2)."""
+    """Runs batches through the library against a resident bank (bank 2).
+    With ``full_gapped`` a request's result is its stage-3.2 alignments
+    (plast_alignment rows, drop-off ``xdrop``, kept at ``s3`` or more) rather
+    than its stage-3.1 records: the redundancy lists of stage 3.2 are kept
+    per pair of sequences, and a pair belongs to one request, so a request's
+    alignments are the same alone and in any batch."""
 
-    def __init__(self, codes: np.ndarray, seq_off: np.ndarray, params=None, device: int = 0):
+    def __init__(self, codes: np.ndarray, seq_off: np.ndarray, params=None, device: int = 0,
+                 full_gapped: bool = False, xdrop: int | None = None, s3: int = 47):
         import torch
 
         from . import binding as B
@@ -214,6 +220,9 @@ class GpuExecutor:
         d = B.DeviceBank.from_host(codes, seq_off, self.device)
         self.bank = B.plast_index_bank(d.codes, d.seq_off, params)
         self.n_resident = len(codes)
+        self.full_gapped = full_gapped
+        self.xdrop = B.PLAST_XDROP if xdrop is None else xdrop
+        self.s3 = s3
         self._streams = threading.local()
 
     def _stream(self):
@@ -229,7 +238,10 @@ class GpuExecutor:
         copies, pairs / 128 reserved; pairs ~ 2e-4 per residue pair)."""
         res = sum(len(r.codes) for r in reqs)
         pairs = 2.1e-4 * res * self.n_resident
-        return int(70 * res + 24 * (pairs / 128 + (1 << 20)))
+        mem = int(70 * res + 24 * (pairs / 128 + (1 << 20)))
+        if self.full_gapped:  # stage 3.2: the warps' working space and about 200 B per record
+            mem += (2 << 30) + int(200 * 2.5e-4 * pairs)
+        return mem
 
     def execute(self, reqs: list):
         B, torch = self.B, self.torch
@@ -244,7 +256,12 @@ class GpuExecutor:
             q = B.plast_index_bank(dc, do, self.params, stream=st)
             pairs = B.plast_pair_count(q, self.bank)
             recs = B.plast_search(q, self.bank, self.params, stream=st)
-            host = B.gapped_numpy(recs)
+            if self.full_gapped:
+                al, _ = B.plast_full_gapped(q, self.bank, recs, self.params, xdrop=self.xdrop, s3=self.s3,
+                                            stream=st)
+                host = B.alignments_numpy(al)
+            else:
+                host = B.gapped_numpy(recs)
             q.free()
         return split_records(host, first), pairs
 

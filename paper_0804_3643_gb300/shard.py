@@ -6,8 +6,11 @@ split into contiguous sequence ranges gives each rank an independent search
 against the whole bank 1; no data moves between ranks until the records are
 gathered.  The records of a shard number bank-2 sequences from the shard's
 first one; merging renumbers them and restores the canonical order
-(seq1, pos1, seq2, pos2).  Plain host code: the per-rank search is the
-library's plast_search on that rank's GPU.
+(seq1, pos1, seq2, pos2).  Stage 3.2 shards the same way: its redundancy
+lists are kept per pair of sequences, and a pair lies in one shard, so each
+rank extends its own records and the alignments merge like the records.
+Plain host code: the per-rank work is the library's plast_search (and
+plast_full_gapped) on that rank's GPU.
 """
 from __future__ import annotations
 
@@ -36,8 +39,9 @@ def shard_bank(codes: np.ndarray, seq_off: np.ndarray, rank: int, world: int):
 
 
 def merge_records(parts: list) -> np.ndarray:
-    """Records of all shards, as (records, first bank-2 sequence) pairs, in
-    canonical order with global bank-2 sequence numbers."""
+    """Records (plast_gapped) or alignments (plast_alignment) of all shards,
+    as (rows, first bank-2 sequence) pairs, in canonical order with global
+    bank-2 sequence numbers."""
     recs = []
     for r, first in parts:
         r = np.array(r, copy=True)

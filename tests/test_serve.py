@@ -8,6 +8,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_0804_3643_gb300 import serve, synth
 
 
@@ -122,3 +123,21 @@ def test_gpu_result_same_alone_and_in_the_mix():
         assert np.array_equal(r.result.view(np.uint8), alone.view(np.uint8))
         n_rec += len(alone)
     assert n_rec > 0
+    # the same requests served with their stage-3.2 alignments: alone = in
+    # the mix, and equal to the oracle's stage 3.2 of the request's records
+    ex.full_gapped = True
+    for r in reqs:
+        r.result = None
+    srv = serve.Server(ex.execute, ex.mem_of, slots=2, max_batch_seqs=60, max_batch_requests=5)
+    srv.run(reqs, realtime=False, timeout=300)
+    assert max(len(b.requests) for b in srv.batches) > 1
+    o2 = oracle.make_bank(bank.codes, bank.seq_off)
+    n_al = 0
+    for r in reqs:
+        alone = ex.alone(r)
+        assert np.array_equal(r.result.view(np.uint8), alone.view(np.uint8))
+        o1 = oracle.make_bank(r.codes, r.seq_off)
+        want = oracle.full_gapped(o1, o2, oracle.small_gapped(o1, o2, oracle.ungapped(o1, o2)))
+        assert np.array_equal(alone.view(np.uint8), want.view(np.uint8))
+        n_al += len(alone)
+    assert n_al > 0

@@ -49,6 +49,21 @@ def test_merged_shards_equal_unsharded(banks, world):
     assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
 
 
+def test_merged_shard_alignments_equal_unsharded(banks):
+    # stage 3.2 per shard: a pair of sequences lies in one shard, so its
+    # redundancy list does too
+    b1, b2 = banks
+    o1 = oracle.make_bank(b1.codes, b1.seq_off)
+    want = oracle.full_gapped(o1, oracle.make_bank(b2.codes, b2.seq_off), search(b1, b2.codes, b2.seq_off))
+    assert len(want) > 10
+    parts = []
+    for r in range(3):
+        c, o, first = shard.shard_bank(b2.codes, b2.seq_off, r, 3)
+        parts.append((oracle.full_gapped(o1, oracle.make_bank(c, o), search(b1, c, o)), first))
+    got = shard.merge_records(parts)
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
