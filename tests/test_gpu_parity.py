@@ -228,7 +228,13 @@ def test_tplastn_parity_small(B):
     assert len(want) > 0
     assert same(got, want)
     recs, _ = B.plast_search_ex(g1, g2)
-    assert same(B.gapped_numpy(recs), oracle.small_gapped(o1, o2, want))
+    w_recs = oracle.small_gapped(o1, o2, want)
+    assert same(B.gapped_numpy(recs), w_recs)
+    # stage 3.2 through the translated frames (extensions cross stop codons)
+    al, ext = B.plast_full_gapped(g1, g2, recs)
+    w_al, w_ext = oracle.full_gapped(o1, o2, w_recs, threads=8, return_extended=True)
+    assert ext == w_ext and len(w_al) > 0
+    assert same(B.alignments_numpy(al), w_al)
 
 
 def test_errors(B):
