@@ -342,7 +342,7 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, int32_t score, c
   flush(true);
 }
 
-__global__ void __launch_bounds__(FG_WARPS * 32, 5) k_full_gapped(FullArgs a) {
+__global__ void __launch_bounds__(FG_WARPS * 32, 6) k_full_gapped(FullArgs a) {
   __shared__ int8_t tab[NCODE * NCODE];
   extern __shared__ __align__(16) int16_t fsm[];
   for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
@@ -438,7 +438,7 @@ cudaError_t launch_full_gapped(const FullArgs& a, int64_t warps, cudaStream_t st
   return cudaGetLastError();
 }
 
-int64_t full_gapped_warps(int n_sms) { return (int64_t)n_sms * 5 * FG_WARPS; }
+int64_t full_gapped_warps(int n_sms) { return (int64_t)n_sms * 6 * FG_WARPS; }
 
 // ---------------------------------------------------------------------------
 // Ordering and output
