@@ -29,18 +29,21 @@
 //
 // Each live cell leaves its H (int16, relative to its row's drop-off line)
 // in the warp's arena (global memory), a dead one a dead marker.  After the
-// side's last row, lane 0 walks back from the end cell (first maximum in
-// row-major order) to the anchor, taking at each cell the source the
-// recurrences give in the order of preference diagonal, E, F, and opening a
-// gap in preference to extending one of equal value, all from the stored H
-// values of the cell's row and the row above (an E is recomputed along its
-// row when the diagonal does not give the cell's H); it counts the
+// side's last row, the warp walks back from the end cell (first maximum in
+// row-major order) to the anchor, 32 steps at a time, taking at each cell
+// the source the recurrences give in the order of preference diagonal, E,
+// F, and opening a gap in preference to extending one of equal value, all
+// from the stored H values of the cell's row and the row above (an E is
+// recomputed along its row when the diagonal does not give the cell's H);
+// it counts the
 // alignment's columns, identities and gap runs and emits its gap-free
 // segments (diagonal pos1 - pos2, first and last pos1).
 //
 // Limits (reported as PLAST_E_CAPACITY by the call): a row of more than
 // FG_W computed columns, more than FG_ARENA bytes of H values and row table
-// for one side, more than FG_SEGS segments for one pair of sequences.
+// for one side, more than FG_SEGS segments for one pair of sequences (and,
+// as a guard that no path the recurrences give can trip, a walk leaving
+// the grid).
 #include <stdint.h>
 
 #include "common.cuh"
@@ -221,9 +224,9 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   return out;
 }
 
-// Lane 0: the path of a side from its end cell back to the anchor.  Columns
-// (cell (i, j) holds residues x = x0 + dx * (i - 1), y = y0 + dy * (j - 1) of
-// the padded banks) are counted into *st; gap-free runs are appended to segs
+// The path of a side from its end cell back to the anchor.  Columns (cell
+// (i, j) holds residues x = x0 + dx * (i - 1), y = y0 + dy * (j - 1) of the
+// padded banks) are counted into *st; gap-free runs are appended to segs
 // (pos1 coordinates are local: x - xoff), except the run that reaches the
 // anchor, returned in *anchor_run (valid when its length is > 0).
 struct PathStats {
@@ -233,32 +236,43 @@ struct Run {
   int32_t diag, start, stop, len;
 };
 
-// H(i, j) of a side from its arena (FG_NEG where the cell is dead or was not
-// computed).
-__device__ __forceinline__ int32_t stored_h(const uint8_t* arena, int i, int j) {
-  const int32_t* t = reinterpret_cast<const int32_t*>(arena) + 4 * i;
-  const int k = j - t[0];
-  if (k < 0 || k >= t[3]) return FG_NEG;
-  const int v = reinterpret_cast<const int16_t*>(arena)[t[1] + k];
-  return v == FG_DEAD16 ? FG_NEG : v + t[2];
+// A row's table entry (origin, offset, line, stored columns) as one 16-byte
+// load, and H(i, j) of that row from it (FG_NEG where the cell is dead or was
+// not computed).
+__device__ __forceinline__ int4 row_entry(const uint8_t* arena, int i) {
+  return *reinterpret_cast<const int4*>(arena + 16 * (int64_t)i);
+}
+__device__ __forceinline__ int32_t entry_h(const int16_t* hval, const int4& t, int j) {
+  const int k = j - t.x;
+  if (k < 0 || k >= t.w) return FG_NEG;
+  const int v = hval[t.y + k];
+  return v == FG_DEAD16 ? FG_NEG : v + t.z;
 }
 
-// Lane 0: the path of a side from its end cell (ei, ej), whose H is `score`,
-// back to the anchor.  Row i takes A_i = pad1[x1 + dir (i - 1)], column j
-// B_j = pad2[y1 + dir (j - 1)].  At a cell in state H the diagonal is taken
-// when H = H(i - 1, j - 1) + s(A_i, B_j) with the diagonal cell live, else E
-// when H equals the row's E there (max over the live cells k < j of the row
-// of H(i, k) - go - (j - k) ge, the value the extension's prefix maximum
-// gives: a term through a dropped cell lies below the line), else F; a gap
-// opens at the first cell back where its value equals the live neighbour's
-// H - go - ge.  Columns are counted into *st; gap-free runs are appended to
-// segs (pos1 coordinates are local: x - xoff), except the run that reaches
-// the anchor, returned in *anchor_run (valid when its length is > 0).
+// The whole warp walks the path of a side from its end cell (ei, ej), whose
+// H is `score`, back to the anchor; every lane keeps the same state.  Row i
+// takes A_i = pad1[x1 + dir (i - 1)], column j B_j = pad2[y1 + dir (j - 1)].
+// At a cell in state H the diagonal is taken when H = H(i - 1, j - 1) +
+// s(A_i, B_j) with the diagonal cell live, else E when H equals the row's E
+// there (max over the live cells k < j of the row of H(i, k) - go - (j - k)
+// ge, the value the extension's prefix maximum gives: a term through a
+// dropped cell lies below the line), else F; a gap opens at the first cell
+// back where its value equals the live neighbour's H - go - ge.  The steps
+// are tested 32 at a time, lane t taking the t-th: a run of diagonal steps
+// ends at the first lane whose test fails (one ballot), a gap at the first
+// lane whose cell closes it, and the E of a cell is one warp maximum of
+// H(i, k) + k ge over the row.  Columns are counted into *st; gap-free runs
+// are appended to segs by lane 0 (pos1 coordinates are local: x - xoff),
+// except the run that reaches the anchor, returned in *anchor_run (valid
+// when its length is > 0).  A path that would leave the grid (the
+// recurrences never lead there) stops with FG_ERR_PATH.
 __device__ void walk_side(const uint8_t* arena, int ei, int ej, int32_t score, const int8_t* pad1,
                           const int8_t* pad2, int64_t x1, int64_t y1, int dir, int64_t xoff, int64_t yoff, int go,
                           int ge, const int8_t* tab, PathStats* st, int32_t* segs, int* nseg, int* err,
-                          Run* anchor_run) {
+                          Run* anchor_run, int lane) {
+  const unsigned FULL = 0xffffffffu;
   const int goe = go + ge;
+  const int16_t* hval = reinterpret_cast<const int16_t*>(arena);
   int i = ei, j = ej, state = 0, prev_gap = 0;
   int32_t v = score;  // the value of the current state at (i, j)
   Run cur = {0, 0, 0, 0};
@@ -267,44 +281,79 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, int32_t score, c
     if (at_anchor) {
       *anchor_run = cur;
     } else if (*nseg < FG_SEGS) {
-      segs[3 * *nseg] = cur.diag;
-      segs[3 * *nseg + 1] = cur.start;
-      segs[3 * *nseg + 2] = cur.stop;
+      if (lane == 0) {
+        segs[3 * *nseg] = cur.diag;
+        segs[3 * *nseg + 1] = cur.start;
+        segs[3 * *nseg + 2] = cur.stop;
+      }
       (*nseg)++;
-    } else {
+    } else if (lane == 0) {
       atomicOr(err, FG_ERR_SEGS);
     }
     cur.len = 0;
   };
   while (i > 0 || j > 0) {
+    if (i < 0 || j < 0) {
+      if (lane == 0) atomicOr(err, FG_ERR_PATH);
+      break;
+    }
     if (state == 0) {
-      const int64_t x = x1 + (int64_t)dir * (i - 1), y = y1 + (int64_t)dir * (j - 1);
-      const int32_t hd = i > 0 && j > 0 ? stored_h(arena, i - 1, j - 1) : FG_NEG;
-      if (hd > FG_NEG && v == hd + tab[pad1[x] * NCODE + pad2[y]]) {
-        // residue pair (A_i, B_j)
-        if (pad1[x] == pad2[y]) st->identities++;
-        else st->mismatches++;
-        st->length++;
-        const int32_t px = (int32_t)(x - xoff), py = (int32_t)(y - yoff);
-        if (cur.len > 0 && cur.diag == px - py) {
-          cur.start = min(cur.start, px);
-          cur.stop = max(cur.stop, px);
-          cur.len++;
+      // diagonal steps: lane t tests cell (i - t, j - t) against (i - t - 1,
+      // j - t - 1), the value there being the H the step before it reaches
+      const int it = i - lane, jt = j - lane;
+      const bool on = it > 0 && jt > 0;
+      int32_t hd = FG_NEG, sc = 0;
+      bool ident = false;
+      if (on) {
+        const int64_t x = x1 + (int64_t)dir * (it - 1), y = y1 + (int64_t)dir * (jt - 1);
+        const int ra = pad1[x], rb = pad2[y];
+        hd = entry_h(hval, row_entry(arena, it - 1), jt - 1);
+        sc = tab[ra * NCODE + rb];
+        ident = ra == rb;
+      }
+      int32_t vt = __shfl_up_sync(FULL, hd, 1);
+      if (lane == 0) vt = v;
+      const unsigned okm = __ballot_sync(FULL, on && hd > FG_NEG && vt == hd + sc);
+      const unsigned idm = __ballot_sync(FULL, ident);
+      const int k = okm == FULL ? 32 : __ffs(~okm) - 1;  // leading diagonal steps
+      if (k > 0) {
+        const unsigned km = k == 32 ? FULL : (1u << k) - 1u;
+        const int nid = __popc(idm & km);
+        st->identities += nid;
+        st->mismatches += k - nid;
+        st->length += k;
+        // residue pairs (A_{i-t}, B_{j-t}), t < k: one diagonal, pos1 px0 - dir t
+        const int32_t px0 = (int32_t)(x1 + (int64_t)dir * (i - 1) - xoff);
+        const int32_t py0 = (int32_t)(y1 + (int64_t)dir * (j - 1) - yoff);
+        const int32_t pxl = px0 - dir * (k - 1);
+        const int32_t lo = min(px0, pxl), hi = max(px0, pxl);
+        if (cur.len > 0 && cur.diag == px0 - py0) {
+          cur.start = min(cur.start, lo);
+          cur.stop = max(cur.stop, hi);
+          cur.len += k;
         } else {
           flush(false);
-          cur.diag = px - py;
-          cur.start = cur.stop = px;
-          cur.len = 1;
+          cur.diag = px0 - py0;
+          cur.start = lo;
+          cur.stop = hi;
+          cur.len = k;
         }
         prev_gap = 0;
-        i--;
-        j--;
-        v = hd;
-      } else {
-        // E of the cell from its row, left to right
-        const int32_t* t = reinterpret_cast<const int32_t*>(arena) + 4 * i;
-        int32_t e = FG_NEG;
-        for (int k = t[0]; k < j; k++) e = max(e - ge, stored_h(arena, i, k) - goe);
+        v = __shfl_sync(FULL, hd, k - 1);
+        i -= k;
+        j -= k;
+      }
+      if (k < 32 && (i > 0 || j > 0)) {
+        // E of the cell from its row: max over the live k < j of
+        // H(i, k) - goe - (j - 1 - k) ge
+        const int4 tc = row_entry(arena, i);
+        int32_t m = FG_NEG;
+        for (int c = tc.x + lane; c < j; c += 32) {
+          const int32_t h = entry_h(hval, tc, c);
+          if (h > FG_NEG) m = max(m, h + c * ge);
+        }
+        m = __reduce_max_sync(FULL, m);
+        const int32_t e = m > FG_NEG ? m - goe - (j - 1) * ge : FG_NEG;
         state = v == e ? 1 : 2;
         // (row 0 has no F and column 0 no E: the recurrences never lead
         // there; the walk stays on the grid regardless)
@@ -315,28 +364,27 @@ __device__ void walk_side(const uint8_t* arena, int ei, int ej, int32_t score, c
       flush(false);  // a gap ends the current run
       if (prev_gap != state) st->gap_opens++;
       prev_gap = state;
-      st->length++;
       // a run is a stretch of equal gap columns, whatever the path's
-      // opening decisions (with a free opening a run may open twice)
+      // opening decisions (with a free opening a run may open twice).  Lane
+      // t tests the t-th step: its value v + t ge against the live
+      // neighbour's H - goe (left for E, above for F)
+      int32_t hn = FG_NEG;
       if (state == 1) {  // gap in A: B_j against nothing
-        const int32_t hl = stored_h(arena, i, j - 1);
-        if (hl > FG_NEG && v == hl - goe) {
-          state = 0;
-          v = hl;
-        } else {
-          v += ge;
-        }
-        j--;
+        if (j - lane - 1 >= 0) hn = entry_h(hval, row_entry(arena, i), j - lane - 1);
       } else {           // gap in B: A_i against nothing
-        const int32_t hu = stored_h(arena, i - 1, j);
-        if (hu > FG_NEG && v == hu - goe) {
-          state = 0;
-          v = hu;
-        } else {
-          v += ge;
-        }
-        i--;
+        if (i - lane - 1 >= 0) hn = entry_h(hval, row_entry(arena, i - lane - 1), j);
       }
+      const unsigned cm = __ballot_sync(FULL, hn > FG_NEG && v + lane * ge == hn - goe);
+      const int n = cm ? __ffs(cm) : 32;  // steps taken
+      st->length += n;
+      if (cm) {
+        v = __shfl_sync(FULL, hn, n - 1);
+        state = 0;
+      } else {
+        v += 32 * ge;
+      }
+      if (prev_gap == 1) j -= n;
+      else i -= n;
     }
   }
   flush(true);
@@ -377,17 +425,16 @@ __global__ void __launch_bounds__(FG_WARPS * 32, 6) k_full_gapped(FullArgs a) {
       __syncwarp();
       PathStats st = {0, 0, 0, 0};
       Run rr = {0, 0, 0, 0}, lr = {0, 0, 0, 0};
-      if (lane == 0)
-        walk_side(arena, R.ei, R.ej, R.score, a.pad1, a.pad2, x0, y0, 1, s1, s2, a.go, a.ge, tab, &st, segs, &nseg,
-                  a.err, &rr);
+      walk_side(arena, R.ei, R.ej, R.score, a.pad1, a.pad2, x0, y0, 1, s1, s2, a.go, a.ge, tab, &st, segs, &nseg,
+                a.err, &rr, lane);
       __syncwarp();
       // left side: rows A_1.. = pad1[x0 - 1 ..] backwards
       const SideOut L = side_dp<-1>(a.pad1 + x0 - 1, r.pos1, a.pad2 + y0 - 1, r.pos2, a.go, a.ge, a.xdrop, tab, Sbuf,
                                     arena, a.err, lane);
       __syncwarp();
+      walk_side(arena, L.ei, L.ej, L.score, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, a.go, a.ge, tab, &st, segs,
+                &nseg, a.err, &lr, lane);
       if (lane == 0) {
-        walk_side(arena, L.ei, L.ej, L.score, a.pad1, a.pad2, x0 - 1, y0 - 1, -1, s1, s2, a.go, a.ge, tab, &st, segs,
-                  &nseg, a.err, &lr);
         // the runs that reach the anchor from both sides are one segment
         if (rr.len > 0 || lr.len > 0) {
           Run m = rr.len > 0 ? rr : lr;

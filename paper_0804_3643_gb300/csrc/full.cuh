@@ -7,7 +7,7 @@ namespace plast {
 constexpr int FG_W = 1024;                  // computed columns of one row a warp can hold
 constexpr int64_t FG_ARENA = 1 << 20;       // row table + H values (int16) of one side, per warp
 constexpr int FG_SEGS = 8192;               // gap-free segments kept for one pair of sequences
-constexpr int FG_ERR_WIDTH = 1, FG_ERR_ARENA = 2, FG_ERR_SEGS = 4;
+constexpr int FG_ERR_WIDTH = 1, FG_ERR_ARENA = 2, FG_ERR_SEGS = 4, FG_ERR_PATH = 8;
 
 struct FullArgs {
   const int8_t* pad1;
