@@ -85,7 +85,12 @@ constexpr int FG_SLOTS = FG_W + 4;  // per row buffer: two dead slots before the
 // one pass and one scan.  Column j is kept in slot j - o + 2 (slots 0 and 1
 // and the two after the row hold the dead value), so the two slots a lane
 // reads and writes are one aligned 8-byte word; the E scan runs over the
-// lanes' pairwise maxima.
+// lanes' pairwise maxima.  Values are computed relative to the line of the
+// row above (the stored int16 decode with no add), the live test and the
+// stored values relative to the row's own line.  Each lane keeps, over the
+// row's chunks, its first and last live column and its best key (H - line)
+// << 11 | (2047 - (j - o)) of a live cell; three warp reductions at the
+// row's end give the live window, the row maximum and its first column.
 struct SideOut {
   int32_t score, ei, ej;
   int64_t cells;  // computed cells, every row
@@ -118,11 +123,12 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     const uint32_t* Sp = Sbuf + pb * FG_SLOTS;
     uint32_t* Sc = Sbuf + cb * FG_SLOTS;
     const int32_t thr = T - X;
+    const int32_t trel = thr - pthr;  // the row's line relative to the row above's
     const int ai = i > 0 ? A[DIR * (i - 1)] : 0;
     const int8_t* trow = tab + ai * NCODE;
     int32_t carryP = FG_NEG;
-    int32_t rmax = FG_NEG, rarg = 0;
-    int lo = -1, hi = -1, cend = c0;
+    int32_t lkey = -1, llo = 0x7fffffff, lhi = -1;  // this lane's best key, first and last live column
+    int cend = c0;
     bool overflow = false;
     for (int cs = o; cs <= lb; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
@@ -138,16 +144,15 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       const int kp = j0 - po + 2;
       const uint32_t sm = Sp[min(kp - 1, pw2)];
       const uint2 sv = *reinterpret_cast<const uint2*>(Sp + min(kp, pw2));
-      const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu) + pthr;
-      const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu) + pthr, fu0 = ((int32_t)sv.x >> 16) + pthr;
-      const int32_t hu1 = (int32_t)(int16_t)(sv.y & 0xffffu) + pthr, fu1 = ((int32_t)sv.y >> 16) + pthr;
+      const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu);
+      const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu), fu0 = (int32_t)sv.x >> 16;
+      const int32_t hu1 = (int32_t)(int16_t)(sv.y & 0xffffu), fu1 = (int32_t)sv.y >> 16;
       // (j = 0 and columns past the sequence end read the sentinel padding)
       const int32_t D0 = hd0 + trow[B[DIR * (j0 - 1)]], D1 = hu0 + trow[B[DIR * j0]];
-      const int32_t hg0 = hu0 - goe, hg1 = hu1 - goe;
-      const int32_t F0 = max(fu0 - ge, hg0), F1 = max(fu1 - ge, hg1);
+      const int32_t F0 = max(fu0 - ge, hu0 - goe), F1 = max(fu1 - ge, hu1 - goe);
       int32_t DF0 = max(D0, F0);
       const int32_t DF1 = max(D1, F1);
-      if (i == 0 && j0 == 0) DF0 = 0;
+      if (i == 0 && j0 == 0) DF0 = 0;  // the anchor (row 0's row above is empty, its line 0)
       // E from the exclusive prefix maximum of DF(k) + k ge over the row (a
       // lane below the shuffle distance gets its own value back)
       const int32_t P0 = in0 ? DF0 + j0 * ge : FG_NEG, P1 = in1 ? DF1 + j1 * ge : FG_NEG;
@@ -158,36 +163,23 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       ex = lane == 0 ? carryP : max(ex, carryP);
       const int32_t E0 = ex - go - j0 * ge, E1 = max(ex, P0) - go - j1 * ge;
       const int32_t H0 = max(DF0, E0), H1 = max(DF1, E1);
-      const bool live0 = in0 && H0 >= thr, live1 = in1 && H1 >= thr;
-      const int32_t H0s = live0 ? H0 : FG_NEG, H1s = live1 ? H1 : FG_NEG;
+      const bool live0 = in0 && H0 >= trel, live1 = in1 && H1 >= trel;
+      const int32_t r0 = H0 - trel, r1 = H1 - trel;  // against the row's line
       if (in0 || in1) {
         const int w = j0 - o;  // even
-        const uint32_t v0 = live0 ? __byte_perm((uint32_t)(H0 - thr), (uint32_t)(F0 - thr), 0x5410u) : FG_DEAD;
-        const uint32_t v1 = live1 ? __byte_perm((uint32_t)(H1 - thr), (uint32_t)(F1 - thr), 0x5410u) : FG_DEAD;
+        const uint32_t v0 = live0 ? __byte_perm((uint32_t)r0, (uint32_t)(F0 - trel), 0x5410u) : FG_DEAD;
+        const uint32_t v1 = live1 ? __byte_perm((uint32_t)r1, (uint32_t)(F1 - trel), 0x5410u) : FG_DEAD;
         *reinterpret_cast<uint2*>(Sc + w + 2) = make_uint2(v0, v1);
         *reinterpret_cast<uint32_t*>(hval + off + w) = __byte_perm(v0, v1, 0x5410u);  // the two H halves
       }
-      // live window, row maximum (first column on ties)
-      const unsigned lm0 = __ballot_sync(0xffffffffu, live0), lm1 = __ballot_sync(0xffffffffu, live1);
-      const unsigned lm = lm0 | lm1;
-      if (lm) {
-        if (lo < 0) {
-          const int l = __ffs(lm) - 1;
-          lo = cs + 2 * l + (((lm0 >> l) & 1u) ? 0 : 1);
-        }
-        const int l = 31 - __clz(lm);
-        hi = cs + 2 * l + (int)((lm1 >> l) & 1u);
-        const int32_t m = __reduce_max_sync(0xffffffffu, max(H0s, H1s));
-        if (m > rmax) {
-          rmax = m;
-          const unsigned c = __ballot_sync(0xffffffffu, H0s == m), d = __ballot_sync(0xffffffffu, H1s == m);
-          const int f = __ffs(c | d) - 1;
-          rarg = cs + 2 * f + (((c >> f) & 1u) ? 0 : 1);
-        }
-      }
+      const int kc = 2047 - (j0 - o);
+      lkey = max(lkey, max(live0 ? (r0 << 11) | kc : -1, live1 ? (r1 << 11) | (kc - 1) : -1));
+      llo = min(llo, live0 ? j0 : live1 ? j1 : 0x7fffffff);
+      lhi = max(lhi, live1 ? j1 : live0 ? j0 : -1);
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
       cend = min(cs + 64, lb + 1);
-      if (cs + 63 >= lim && !(lm1 >> 31)) break;  // past the row above's reach, last cell dropped
+      // past the row above's reach with the chunk's last cell dropped: the row ends
+      if (cs + 63 >= lim && !__shfl_sync(0xffffffffu, (int)live1, 31)) break;
     }
     if (overflow) {
       if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
@@ -195,7 +187,12 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     }
     const int cw = (cend - o + 1) & ~1;  // stored columns, even
     out.cells += cend - c0;
-    if (rmax == FG_NEG) break;  // no live cell: the side ends
+    const int32_t key = __reduce_max_sync(0xffffffffu, lkey);
+    if (key < 0) break;  // no live cell: the side ends
+    const int32_t rmax = (key >> 11) + thr;
+    const int rarg = o + 2047 - (key & 2047);
+    plo = __reduce_min_sync(0xffffffffu, llo);
+    phi = __reduce_max_sync(0xffffffffu, lhi);
     if (lane == 0) {
       rowtab[4 * i] = o;
       rowtab[4 * i + 1] = off;
@@ -210,8 +207,6 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       bj = rarg;
     }
     T = max(T, rmax);
-    plo = lo;
-    phi = hi;
     po = o;
     pw2 = cw + 2;
     pthr = thr;
