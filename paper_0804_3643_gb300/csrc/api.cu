@@ -1055,9 +1055,9 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
   CK(sc.get(&arena, (size_t)warps * FG_ARENA));
   CK(sc.get(&segs, (size_t)warps * 3 * FG_SEGS));
   CK(sc.get(&d_err, 1));
-  CK(sc.get(&d_cells, 1));
+  CK(sc.get(&d_cells, 2));  // the cell count, then the kernel's work counter
   CK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-  CK(cudaMemsetAsync(d_cells, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(d_cells, 0, 2 * sizeof(unsigned long long), st));
   FullArgs fa;
   fa.pad1 = b1->pad;
   fa.pad2 = b2->pad;
@@ -1076,6 +1076,7 @@ int plast_full_gapped(const plast_bank* b1, const plast_bank* b2, const plast_pa
   fa.segs = segs;
   fa.err = d_err;
   fa.cells = d_cells;
+  fa.next = reinterpret_cast<unsigned*>(d_cells + 1);
   t_timer.reset();
   t_timer.mark(0, st);
   CK(launch_full_gapped(fa, warps, st));

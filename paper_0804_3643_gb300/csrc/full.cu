@@ -7,7 +7,8 @@
 // Work split.  The records of one pair of sequences depend on one another
 // through the segment list, so one warp takes all the records of a pair, in
 // the processing order (decreasing small gapped score, then pos1, then
-// pos2); pairs are independent and spread over the warps.
+// pos2); pairs are independent, and a warp takes the next one from a shared
+// counter when it is done with the last.
 //
 // One side of one record is an anchored dynamic programme without a band,
 // cut by the drop-off X row by row: a cell whose H is more than X below T,
@@ -397,7 +398,14 @@ __global__ void __launch_bounds__(FG_WARPS * 32, 6) k_full_gapped(FullArgs a) {
   uint8_t* arena = a.arena + gw * FG_ARENA;
   int32_t* segs = a.segs + gw * 3 * FG_SEGS;
   const int64_t ng = *a.ng_dev;
-  for (int64_t g = gw; g < ng; g += (int64_t)gridDim.x * FG_WARPS) {
+  for (;;) {
+    // the next pair of sequences from a shared counter: pairs differ widely
+    // in work, and a fixed share per warp left a fifth of the warps' time
+    // idle at the end
+    unsigned gn = 0;
+    if (lane == 0) gn = atomicAdd(a.next, 1u);
+    const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gn, 0);
+    if (g >= ng) break;
     int nseg = 0;
     for (int64_t k = a.gstart[g]; k < a.gstart[g + 1]; k++) {
       const uint32_t rec = a.proc[k];

@@ -25,6 +25,7 @@ struct FullArgs {
   int32_t* segs;            // 3 * FG_SEGS ints per warp
   int* err;                 // FG_ERR_* bits
   unsigned long long* cells;  // computed dynamic-programming cells, summed
+  unsigned* next;             // the next pair of sequences to take (zero at launch)
 };
 
 // Warps the stage-3.2 kernel runs with on a GPU of n_sms SMs (the arena and
