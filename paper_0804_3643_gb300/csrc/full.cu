@@ -114,6 +114,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first dead slot after it
   int32_t pthr = 0;                       // the row above's drop-off line
   int pb = 0;                             // buffer holding the row above
+  int ai = 0;                             // A_i of the row (row 0: none)
   if (lane == 0) Sbuf[2] = Sbuf[3] = FG_DEAD;  // row 0 has no row above: an empty one
   __syncwarp();
   for (int i = 0; i <= la; i++) {
@@ -125,21 +126,26 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     uint32_t* Sc = Sbuf + cb * FG_SLOTS;
     const int32_t thr = T - X;
     const int32_t trel = thr - pthr;  // the row's line relative to the row above's
-    const int ai = i > 0 ? A[DIR * (i - 1)] : 0;
     const int8_t* trow = tab + ai * NCODE;
+    ai = i < la ? A[DIR * i] : 0;  // the next row's residue, loaded a row ahead
     int32_t carryP = FG_NEG;
     int32_t lkey = -1, llo = 0x7fffffff, lhi = -1;  // this lane's best key, first and last live column
     int cend = c0;
     bool overflow = false;
+    // a row that fits whole needs no test per chunk
+    const bool fits = lb - o + 4 <= FG_W && off + (lb - o) + 1 < FG_ARENA / 2;
     for (int cs = o; cs <= lb; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
       const int wl = min(cs + 63, lb) - o;
-      if (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA / 2) {
+      if (!fits && (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA / 2)) {
         overflow = true;
         break;
       }
+      // (a column left of c0 reads only dead cells of the row above and dead
+      // E terms: it comes out dead, and its prefix term lies below every
+      // live one to its right; a column past lb feeds only columns past lb)
       const int j0 = cs + 2 * lane, j1 = j0 + 1;
-      const bool in0 = j0 >= c0 && j0 <= lb, in1 = j1 <= lb;
+      const bool in0 = j0 <= lb, in1 = j1 <= lb;
       // row above: columns j0 - 1, j0, j0 + 1 at slots kp - 1, kp, kp + 1
       // (kp = j0 - po + 2, even), clamped to the dead slots after it
       const int kp = j0 - po + 2;
@@ -156,7 +162,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       if (i == 0 && j0 == 0) DF0 = 0;  // the anchor (row 0's row above is empty, its line 0)
       // E from the exclusive prefix maximum of DF(k) + k ge over the row (a
       // lane below the shuffle distance gets its own value back)
-      const int32_t P0 = in0 ? DF0 + j0 * ge : FG_NEG, P1 = in1 ? DF1 + j1 * ge : FG_NEG;
+      const int32_t P0 = DF0 + j0 * ge, P1 = DF1 + j1 * ge;
       int32_t incl = max(P0, P1);
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) incl = max(incl, __shfl_up_sync(0xffffffffu, incl, d));
