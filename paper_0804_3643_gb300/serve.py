@@ -239,8 +239,10 @@ class GpuExecutor:
         res = sum(len(r.codes) for r in reqs)
         pairs = 2.1e-4 * res * self.n_resident
         mem = int(70 * res + 24 * (pairs / 128 + (1 << 20)))
-        if self.full_gapped:  # stage 3.2: the warps' working space and about 200 B per record
-            mem += (2 << 30) + int(200 * 2.5e-4 * pairs)
+        if self.full_gapped:  # stage 3.2: the warps' working space (a 1 MiB arena and
+            # 96 KiB of segment lists for each of 24 warps per SM) and about 200 B per record
+            n_sm = self.torch.cuda.get_device_properties(self.device).multi_processor_count
+            mem += n_sm * 24 * ((1 << 20) + 3 * 8192 * 4) + int(200 * 2.5e-4 * pairs)
         return mem
 
     def execute(self, reqs: list):
