@@ -54,7 +54,7 @@ namespace plast {
 
 constexpr int FG_WARPS = 4;  // warps per CTA
 constexpr int32_t FG_NEG = -(1 << 28);
-constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 4) * 4;  // per warp: two rows of (H, F) int16 slots
+constexpr int FG_SMEM = FG_WARPS * (FG_W + 4) * 4;  // per warp: one row of (H, F) int16 slots
 
 // The row above is kept in shared memory as int16 values relative to its
 // drop-off line thr = T - X, one 32-bit slot per column (H in the low half,
@@ -68,11 +68,12 @@ constexpr int FG_SMEM = FG_WARPS * 2 * (FG_W + 4) * 4;  // per warp: two rows of
 // minus infinity, with no test per use.  A live cell's F needs no clamp: it
 // comes from a dead slot (so it lies within go + ge + 11 of -30000) or from
 // a live H above (within go + ge of the line), so it stays in int16.  Slots
-// 0 and 1 of a row buffer and the two after a row hold the dead value too,
-// so the row below reads out-of-range columns through one clamped index.
+// 0 and 1 of the row buffer hold the dead value too, and a column past the
+// row above's last stored one reads as dead (one compare on the slot), so
+// the row below reads out-of-range columns with no other test.
 constexpr int FG_DEAD16 = -30000;
 constexpr uint32_t FG_DEAD = 0x8AD08AD0u;  // FG_DEAD16 in both halves
-constexpr int FG_SLOTS = FG_W + 4;  // per row buffer: two dead slots before the row, two after
+constexpr int FG_SLOTS = FG_W + 4;  // the row buffer: two dead slots before the row, two spare
 
 // One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
 // B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
@@ -84,7 +85,7 @@ constexpr int FG_SLOTS = FG_W + 4;  // per row buffer: two dead slots before the
 // column c0 (a column left of c0 is not computed: it is dead and feeds
 // nothing), so that a row of the random extensions (about 40 columns) takes
 // one pass and one scan.  Column j is kept in slot j - o + 2 (slots 0 and 1
-// and the two after the row hold the dead value), so the two slots a lane
+// hold the dead value), so the two slots a lane
 // reads and writes are one aligned 8-byte word; the E scan runs over the
 // lanes' pairwise maxima.  Values are computed relative to the line of the
 // row above (the stored int16 decode with no add), the live test and the
@@ -111,19 +112,22 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   }
   int off = (int)(tab_bytes / 2);  // in int16 units, even
   int32_t T = 0, best = 0, bi = 0, bj = 0;
-  int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first dead slot after it
+  int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first slot after it
   int32_t pthr = 0;                       // the row above's drop-off line
-  int pb = 0;                             // buffer holding the row above
   int ai = 0;                             // A_i of the row (row 0: none)
-  if (lane == 0) Sbuf[2] = Sbuf[3] = FG_DEAD;  // row 0 has no row above: an empty one
-  __syncwarp();
+  __syncwarp();  // (row 0 has no row above: pw2 = 2 makes it an empty one)
   for (int i = 0; i <= la; i++) {
     const int c0 = i == 0 ? 0 : plo;
     const int o = c0 & ~1;                 // the row's origin (even)
     const int lim = i == 0 ? 0 : phi + 1;  // the last column a cell of the row above can feed
-    const int cb = pb ^ 1;
-    const uint32_t* Sp = Sbuf + pb * FG_SLOTS;
-    uint32_t* Sc = Sbuf + cb * FG_SLOTS;
+    // the row is written over the row above in the same buffer: a chunk
+    // reads the row above before it stores (its scan's shuffles come
+    // between), the row's origin is never left of the row above's, so a
+    // chunk overwrites only columns left of what later chunks read, but for
+    // the row-above column just left of the next chunk, which lane 31 of
+    // this chunk hands on
+    uint32_t* Sp = Sbuf;
+    uint32_t carry_sm = 0;  // the row above's slot of column cs - 1 (chunks after the first)
     const int32_t thr = T - X;
     const int32_t trel = thr - pthr;  // the row's line relative to the row above's
     const int8_t* trow = tab + ai * NCODE;
@@ -147,10 +151,14 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       const int j0 = cs + 2 * lane, j1 = j0 + 1;
       const bool in0 = j0 <= lb, in1 = j1 <= lb;
       // row above: columns j0 - 1, j0, j0 + 1 at slots kp - 1, kp, kp + 1
-      // (kp = j0 - po + 2, even), clamped to the dead slots after it
+      // (kp = j0 - po + 2, even); the loads stay inside the buffer
       const int kp = j0 - po + 2;
-      const uint32_t sm = Sp[min(kp - 1, pw2)];
-      const uint2 sv = *reinterpret_cast<const uint2*>(Sp + min(kp, pw2));
+      // (the slots from pw2 on may hold this row's own earlier chunks: a
+      // column there is past the row above and takes the dead value)
+      const uint32_t sm = lane == 0 && cs > o ? carry_sm : kp - 1 < pw2 ? Sp[min(kp - 1, pw2)] : FG_DEAD;
+      uint2 sv = *reinterpret_cast<const uint2*>(Sp + min(kp, pw2));
+      if (kp >= pw2) sv = make_uint2(FG_DEAD, FG_DEAD);
+      carry_sm = __shfl_sync(0xffffffffu, sv.y, 31);
       const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu);
       const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu), fu0 = (int32_t)sv.x >> 16;
       const int32_t hu1 = (int32_t)(int16_t)(sv.y & 0xffffu), fu1 = (int32_t)sv.y >> 16;
@@ -176,7 +184,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
         const int w = j0 - o;  // even
         const uint32_t v0 = live0 ? __byte_perm((uint32_t)r0, (uint32_t)(F0 - trel), 0x5410u) : FG_DEAD;
         const uint32_t v1 = live1 ? __byte_perm((uint32_t)r1, (uint32_t)(F1 - trel), 0x5410u) : FG_DEAD;
-        *reinterpret_cast<uint2*>(Sc + w + 2) = make_uint2(v0, v1);
+        *reinterpret_cast<uint2*>(Sp + w + 2) = make_uint2(v0, v1);
         *reinterpret_cast<uint32_t*>(hval + off + w) = __byte_perm(v0, v1, 0x5410u);  // the two H halves
       }
       const int kc = 2047 - (j0 - o);
@@ -205,7 +213,6 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       rowtab[4 * i + 1] = off;
       rowtab[4 * i + 2] = thr;
       rowtab[4 * i + 3] = cw;
-      Sc[cw + 2] = Sc[cw + 3] = FG_DEAD;  // the dead slots after the row
     }
     off += cw;
     if (rmax > best) {
@@ -217,7 +224,6 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     po = o;
     pw2 = cw + 2;
     pthr = thr;
-    pb = cb;
     __syncwarp();
   }
   out.score = best;
@@ -398,8 +404,8 @@ __global__ void __launch_bounds__(FG_WARPS * 32, 6) k_full_gapped(FullArgs a) {
   for (int t = threadIdx.x; t < NCODE * NCODE; t += blockDim.x) tab[t] = c_score[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* Sbuf = reinterpret_cast<uint32_t*>(fsm) + warp * 2 * FG_SLOTS;
-  if (lane == 0) Sbuf[0] = Sbuf[1] = Sbuf[FG_SLOTS] = Sbuf[FG_SLOTS + 1] = FG_DEAD;  // never written
+  uint32_t* Sbuf = reinterpret_cast<uint32_t*>(fsm) + warp * FG_SLOTS;
+  if (lane == 0) Sbuf[0] = Sbuf[1] = FG_DEAD;  // never written
   const int64_t gw = (int64_t)blockIdx.x * FG_WARPS + warp;
   uint8_t* arena = a.arena + gw * FG_ARENA;
   int32_t* segs = a.segs + gw * 3 * FG_SEGS;
