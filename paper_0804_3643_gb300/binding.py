@@ -430,6 +430,28 @@ def alignments_numpy(t: torch.Tensor) -> np.ndarray:
     return t.contiguous().cpu().numpy().reshape(-1).view(ALIGN_DTYPE)
 
 
+def alignments_tabular(al, names1=None, names2=None) -> list[str]:
+    """Tab-separated lines of plast_alignment rows in the column order of
+    BLAST's -m 8 report (the output Section 3.3.5 describes): query,
+    subject, percent identity, alignment length, mismatches, gap opens,
+    query start, query end, subject start, subject end (1-based, inclusive),
+    then the raw score where -m 8 has the E-value and bit score, which need
+    statistics the paper does not give.  ``al`` is a device tensor of records
+    or their numpy view; names1 / names2 map sequence indices to names (the
+    index itself by default)."""
+    a = al if isinstance(al, np.ndarray) else alignments_numpy(al)
+    out = []
+    for r in a:
+        q = names1[r["seq1"]] if names1 is not None else str(int(r["seq1"]))
+        t = names2[r["seq2"]] if names2 is not None else str(int(r["seq2"]))
+        length = int(r["length"])
+        pid = 100.0 * int(r["identities"]) / length if length else 0.0
+        out.append(f"{q}\t{t}\t{pid:.2f}\t{length}\t{int(r['mismatches'])}\t{int(r['gap_opens'])}\t"
+                   f"{int(r['q_start']) + 1}\t{int(r['q_end'])}\t{int(r['s_start']) + 1}\t{int(r['s_end'])}\t"
+                   f"{int(r['score'])}")
+    return out
+
+
 NOALLOC_MAX_HITS = 65536
 
 
