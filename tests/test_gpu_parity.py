@@ -360,7 +360,14 @@ def test_plastx_both_translated(B):
     assert same(B.hits_numpy(B.plast_ungapped(got[0], got[1])), want_h)
     recs, n_ung = B.plast_search_ex(got[0], got[1])
     assert n_ung == len(want_h)
-    assert same(B.gapped_numpy(recs), oracle.small_gapped(want[0], want[1], want_h))
+    w_recs = oracle.small_gapped(want[0], want[1], want_h)
+    assert same(B.gapped_numpy(recs), w_recs)
+    # stage 3.2 on the translated frames (extensions run through stop codons
+    # on both sides)
+    al, ext = B.plast_full_gapped(got[0], got[1], recs)
+    w_al, w_ext = oracle.full_gapped(want[0], want[1], w_recs, threads=8, return_extended=True)
+    assert ext == w_ext and len(w_al) > 0
+    assert same(B.alignments_numpy(al), w_al)
 
 
 def test_plastx_translated_queries(B):
