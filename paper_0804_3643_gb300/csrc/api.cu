@@ -447,6 +447,45 @@ void build_tiles(const plast_bank* b1, const plast_bank* b2, bool largest_first,
                    largest_first ? num_sms() : 0);
 }
 
+// The survivor rate of the last stage 2 of each pair of banks, to size the
+// next one's survivor buffer.  The first guess, pairs / 128, holds for
+// ordinary protein banks (about 1 / 570 at S1 = 38), but keys with
+// low-complexity runs pass far more often, and an overflowing first run is
+// run again with the exact count; with the rate of the pair's last search
+// the buffer fits at once.  Sizing only: no result depends on it.
+struct RateHint {
+  const plast_bank* b1;
+  const plast_bank* b2;
+  double rate;
+};
+std::mutex g_hint_mu;
+RateHint g_hints[32] = {};
+int g_hint_next = 0;
+
+double rate_hint(const plast_bank* b1, const plast_bank* b2) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  for (const RateHint& h : g_hints)
+    if (h.b1 == b1 && h.b2 == b2) return h.rate;
+  return 0.0;
+}
+
+void set_rate_hint(const plast_bank* b1, const plast_bank* b2, double rate) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  for (RateHint& h : g_hints)
+    if (h.b1 == b1 && h.b2 == b2) {
+      h.rate = rate;
+      return;
+    }
+  g_hints[g_hint_next] = RateHint{b1, b2, rate};
+  g_hint_next = (g_hint_next + 1) % 32;
+}
+
+void forget_rate_hints(const plast_bank* b) {
+  std::lock_guard<std::mutex> lk(g_hint_mu);
+  for (RateHint& h : g_hints)
+    if (h.b1 == b || h.b2 == b) h = RateHint{nullptr, nullptr, 0.0};
+}
+
 // Device state shared by the stage-2 calls: sorted survivor keys and values.
 struct Survivors {
   uint64_t* key = nullptr;
@@ -479,6 +518,8 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
   CK(cudaMemcpyAsync(d_tiles, tl.tiles.data(), nt * sizeof(int4), cudaMemcpyHostToDevice, st));
 
   int64_t cap = tl.pairs / 128 + (1 << 20);
+  const double hint = rate_hint(b1, b2);
+  if (hint > 0.0) cap = std::max<int64_t>(cap, (int64_t)(hint * 1.1 * (double)tl.pairs) + (1 << 20));
   for (int attempt = 0; attempt < 2; attempt++) {
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
@@ -506,6 +547,7 @@ int run_ungapped(const plast_bank* b1, const plast_bank* b2, const plast_params&
     unsigned long long n = 0;
     CK(cudaMemcpyAsync(&n, d_count, sizeof(n), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (tl.pairs > 0) set_rate_hint(b1, b2, (double)n / (double)tl.pairs);
     if ((int64_t)n > cap) {
       sc.release(k0);
       sc.release(v0);
@@ -617,6 +659,7 @@ int plast_set_schedule(int mode) {
 
 void plast_bank_free(plast_bank* b) {
   if (!b) return;
+  forget_rate_hints(b);
   if (b->ready) {
     cudaEventSynchronize(b->ready);  // the build may still be running on its stream
     cudaEventDestroy(b->ready);
