@@ -370,6 +370,24 @@ def _records(out: torch.Tensor | None, cap: int, nbytes: int) -> torch.Tensor:
     return torch.empty(max(cap, 1) * nbytes, dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
 
 
+# The output count of the last automatically sized call of each kind on each
+# pair of banks: a repeated call on the same banks is sized at once (the
+# first guess from the pair count is run again with the exact count when it
+# overflows, and banks with low-complexity runs overflow it).
+_last_count: dict = {}
+
+
+def _auto_cap(kind: str, b1: Bank, b2: Bank, guess: int) -> int:
+    last = _last_count.get((kind, b1.handle.value, b2.handle.value))
+    return max(guess, int(last * 1.05) + 4096) if last is not None else guess
+
+
+def _note_count(kind: str, b1: Bank, b2: Bank, n: int) -> None:
+    if len(_last_count) > 256:
+        _last_count.clear()
+    _last_count[(kind, b1.handle.value, b2.handle.value)] = n
+
+
 def plast_ungapped(b1: Bank, b2: Bank, params: plast_params | None = None, cap: int | None = None,
                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """Stage-2 hits as a uint8 device tensor [n, 20] (plast_hit records).
@@ -377,12 +395,15 @@ def plast_ungapped(b1: Bank, b2: Bank, params: plast_params | None = None, cap: 
     (one retry with the exact count); otherwise PLAST_E_CAPACITY raises."""
     auto = cap is None and out is None
     if cap is None:
-        cap = out.numel() // HIT_BYTES if out is not None else plast_pair_count(b1, b2) // 64 + 4096
+        cap = (out.numel() // HIT_BYTES if out is not None
+               else _auto_cap("ungapped", b1, b2, plast_pair_count(b1, b2) // 64 + 4096))
     for _ in range(2):
         buf = _records(out, cap, HIT_BYTES)
         n = ctypes.c_int64()
         rc = lib().plast_ungapped(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
                                   _ptr(buf), cap, ctypes.byref(n), _stream(stream))
+        if auto and rc in (0, PLAST_E_CAPACITY):
+            _note_count("ungapped", b1, b2, n.value)
         if rc == PLAST_E_CAPACITY and auto:
             cap, out = n.value, None
             continue
@@ -479,12 +500,15 @@ def plast_search(b1: Bank, b2: Bank, params: plast_params | None = None, cap: in
     sized automatically unless ``cap`` or ``out`` is given, as plast_ungapped."""
     auto = cap is None and out is None
     if cap is None:
-        cap = out.numel() // GAPPED_BYTES if out is not None else plast_pair_count(b1, b2) // 256 + 4096
+        cap = (out.numel() // GAPPED_BYTES if out is not None
+               else _auto_cap("search", b1, b2, plast_pair_count(b1, b2) // 256 + 4096))
     for _ in range(2):
         buf = _records(out, cap, GAPPED_BYTES)
         n = ctypes.c_int64()
         rc = lib().plast_search(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
                                 _ptr(buf), cap, ctypes.byref(n), _stream(stream))
+        if auto and rc in (0, PLAST_E_CAPACITY):
+            _note_count("search", b1, b2, n.value)
         if rc == PLAST_E_CAPACITY and auto:
             cap, out = n.value, None
             continue
@@ -509,7 +533,8 @@ def plast_search_ex(b1: Bank, b2: Bank, params: plast_params | None = None, s0: 
     (records [n, 28] uint8 device tensor, number of stage-2 hits)."""
     auto = cap is None and out is None
     if cap is None:
-        cap = out.numel() // GAPPED_BYTES if out is not None else plast_pair_count(b1, b2) // 256 + 4096
+        cap = (out.numel() // GAPPED_BYTES if out is not None
+               else _auto_cap("search", b1, b2, plast_pair_count(b1, b2) // 256 + 4096))
     k, kp, nk = _keys_arg(keys)
     for _ in range(2):
         buf = _records(out, cap, GAPPED_BYTES)
@@ -517,6 +542,8 @@ def plast_search_ex(b1: Bank, b2: Bank, params: plast_params | None = None, s0: 
         rc = lib().plast_search_ex(b1.handle, b2.handle, ctypes.byref(params) if params is not None else None,
                                    int(s0), kp, nk, _ptr(buf), cap, ctypes.byref(n), ctypes.byref(nu),
                                    _stream(stream))
+        if auto and rc in (0, PLAST_E_CAPACITY) and keys is None and not s0:
+            _note_count("search", b1, b2, n.value)
         if rc == PLAST_E_CAPACITY and auto:
             cap, out = n.value, None
             continue
