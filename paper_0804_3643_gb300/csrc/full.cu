@@ -75,17 +75,18 @@ constexpr int FG_DEAD16 = -30000;
 constexpr uint32_t FG_DEAD = 0x8AD08AD0u;  // FG_DEAD16 in both halves
 constexpr int FG_SLOTS = FG_W + 4;  // the row buffer: two dead slots before the row, two spare
 
-// One side of one anchor.  Row i takes A_i = A[(i - 1) * as], column j takes
-// B_j = B[(j - 1) * bs]; la / lb residues.  Returns the side's score and its
-// end cell; the directions and the row table (origin, offset per row) are in
-// `arena`.  *err gets FG_ERR_* bits on a capacity overflow.
+// One side of one anchor.  Row i takes A_i = A[DIR (i - 1)], column j takes
+// B_j = B[DIR (j - 1)]; la / lb residues.  Returns the side's score, its end
+// cell and its computed cells; the H values and the row table (origin,
+// offset, line, stored columns per row) are in `arena`.  *err gets FG_ERR_*
+// bits on a capacity overflow.
 //
 // A row is computed 64 columns at a time, two adjacent columns j0 = cs + 2l
 // and j0 + 1 per lane, from an even origin o at or left of the row's first
-// column c0 (a column left of c0 is not computed: it is dead and feeds
-// nothing), so that a row of the random extensions (about 40 columns) takes
-// one pass and one scan.  Column j is kept in slot j - o + 2 (slots 0 and 1
-// hold the dead value), so the two slots a lane
+// column c0 (the column left of c0 that the rounding may add comes out
+// dead and is not counted), so that a row of the random extensions (about
+// 40 columns) takes one pass and one scan.  Column j is kept in slot
+// j - o + 2 (slots 0 and 1 hold the dead value), so the two slots a lane
 // reads and writes are one aligned 8-byte word; the E scan runs over the
 // lanes' pairwise maxima.  Values are computed relative to the line of the
 // row above (the stored int16 decode with no add), the live test and the
