@@ -151,14 +151,18 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       // live one to its right; a column past lb feeds only columns past lb)
       const int j0 = cs + 2 * lane, j1 = j0 + 1;
       const bool in0 = j0 <= lb, in1 = j1 <= lb;
-      // row above: columns j0 - 1, j0, j0 + 1 at slots kp - 1, kp, kp + 1
-      // (kp = j0 - po + 2, even); the loads stay inside the buffer
+      // row above: columns j0 and j0 + 1 at slots kp, kp + 1 (kp = j0 - po +
+      // 2, even; the load stays inside the buffer), column j0 - 1 from the
+      // lane to the left (lane 0: from lane 31 of the chunk before, and in a
+      // row's first chunk column o - 1, left of the row above's first live
+      // column, dead)
       const int kp = j0 - po + 2;
       // (the slots from pw2 on may hold this row's own earlier chunks: a
       // column there is past the row above and takes the dead value)
-      const uint32_t sm = lane == 0 && cs > o ? carry_sm : kp - 1 < pw2 ? Sp[min(kp - 1, pw2)] : FG_DEAD;
       uint2 sv = *reinterpret_cast<const uint2*>(Sp + min(kp, pw2));
       if (kp >= pw2) sv = make_uint2(FG_DEAD, FG_DEAD);
+      uint32_t sm = __shfl_up_sync(0xffffffffu, sv.y, 1);
+      if (lane == 0) sm = cs > o ? carry_sm : FG_DEAD;
       carry_sm = __shfl_sync(0xffffffffu, sv.y, 31);
       const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu);
       const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu), fu0 = (int32_t)sv.x >> 16;
