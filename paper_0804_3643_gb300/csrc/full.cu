@@ -213,12 +213,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     const int rarg = o + 2047 - (key & 2047);
     plo = __reduce_min_sync(0xffffffffu, llo);
     phi = __reduce_max_sync(0xffffffffu, lhi);
-    if (lane == 0) {
-      rowtab[4 * i] = o;
-      rowtab[4 * i + 1] = off;
-      rowtab[4 * i + 2] = thr;
-      rowtab[4 * i + 3] = cw;
-    }
+    if (lane == 0) *reinterpret_cast<int4*>(rowtab + 4 * i) = make_int4(o, off, thr, cw);
     off += cw;
     if (rmax > best) {
       best = rmax;
