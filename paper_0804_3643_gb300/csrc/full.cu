@@ -113,6 +113,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   }
   int off = (int)(tab_bytes / 2);  // in int16 units, even
   int32_t T = 0, best = 0, bi = 0, bj = 0;
+  int32_t cells = 0;  // computed cells (at most the arena's columns)
   int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first slot after it
   int32_t pthr = 0;                       // the row above's drop-off line
   int ai = 0;                             // A_i of the row (row 0: none)
@@ -135,11 +136,11 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     ai = i < la ? A[DIR * i] : 0;  // the next row's residue, loaded a row ahead
     int32_t carryP = FG_NEG;
     int32_t lkey = -1, llo = 0x7fffffff, lhi = -1;  // this lane's best key, first and last live column
-    int cend = c0;
     bool overflow = false;
     // a row that fits whole needs no test per chunk
     const bool fits = lb - o + 4 <= FG_W && off + (lb - o) + 1 < FG_ARENA / 2;
-    for (int cs = o; cs <= lb; cs += 64) {
+    int cs = o;  // (o <= c0 <= lb: the row has at least one chunk)
+    for (;; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
       const int wl = min(cs + 63, lb) - o;
       if (!fits && (wl + 4 > FG_W || off + wl + 1 >= FG_ARENA / 2)) {
@@ -163,7 +164,6 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       if (kp >= pw2) sv = make_uint2(FG_DEAD, FG_DEAD);
       uint32_t sm = __shfl_up_sync(0xffffffffu, sv.y, 1);
       if (lane == 0) sm = cs > o ? carry_sm : FG_DEAD;
-      carry_sm = __shfl_sync(0xffffffffu, sv.y, 31);
       const int32_t hd0 = (int32_t)(int16_t)(sm & 0xffffu);
       const int32_t hu0 = (int32_t)(int16_t)(sv.x & 0xffffu), fu0 = (int32_t)sv.x >> 16;
       const int32_t hu1 = (int32_t)(int16_t)(sv.y & 0xffffu), fu1 = (int32_t)sv.y >> 16;
@@ -196,17 +196,20 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
       lkey = max(lkey, max(live0 ? (r0 << 11) | kc : -1, live1 ? (r1 << 11) | (kc - 1) : -1));
       llo = min(llo, live0 ? j0 : live1 ? j1 : 0x7fffffff);
       lhi = max(lhi, live1 ? j1 : live0 ? j0 : -1);
+      // past the sequence end, or past the row above's reach with the
+      // chunk's last cell dropped: the row ends
+      if (cs + 64 > lb || (cs + 63 >= lim && !__shfl_sync(0xffffffffu, (int)live1, 31))) break;
+      // what the next chunk takes from this one's lane 31
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
-      cend = min(cs + 64, lb + 1);
-      // past the row above's reach with the chunk's last cell dropped: the row ends
-      if (cs + 63 >= lim && !__shfl_sync(0xffffffffu, (int)live1, 31)) break;
+      carry_sm = __shfl_sync(0xffffffffu, sv.y, 31);
     }
     if (overflow) {
       if (lane == 0) atomicOr(err, FG_ERR_WIDTH);
       return out;
     }
-    const int cw = (cend - o + 1) & ~1;  // stored columns, even
-    out.cells += cend - c0;
+    const int cend = min(cs + 64, lb + 1);  // past the row's last computed column
+    const int cw = (cend - o + 1) & ~1;     // stored columns, even
+    cells += cend - c0;
     const int32_t key = __reduce_max_sync(0xffffffffu, lkey);
     if (key < 0) break;  // no live cell: the side ends
     const int32_t rmax = (key >> 11) + thr;
@@ -229,6 +232,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
   out.score = best;
   out.ei = bi;
   out.ej = bj;
+  out.cells = cells;
   return out;
 }
 
