@@ -112,6 +112,9 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     return out;
   }
   int off = (int)(tab_bytes / 2);  // in int16 units, even
+  // a side whose rows all fit whole, even at their widest (la + 1 rows of at
+  // most lb + 2 stored columns), needs no capacity test at all
+  const bool side_fits = lb + 4 <= FG_W && off + (int64_t)(la + 1) * (lb + 2) < FG_ARENA / 2;
   int32_t T = 0, best = 0, bi = 0, bj = 0;
   int32_t cells = 0;  // computed cells (at most the arena's columns)
   int plo = 0, phi = 0, po = 0, pw2 = 2;  // the row above: live columns, origin, first slot after it
@@ -138,7 +141,7 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
     int32_t lkey = -1, llo = 0x7fffffff, lhi = -1;  // this lane's best key, first and last live column
     bool overflow = false;
     // a row that fits whole needs no test per chunk
-    const bool fits = lb - o + 4 <= FG_W && off + (lb - o) + 1 < FG_ARENA / 2;
+    const bool fits = side_fits || (lb - o + 4 <= FG_W && off + (lb - o) + 1 < FG_ARENA / 2);
     int cs = o;  // (o <= c0 <= lb: the row has at least one chunk)
     for (;; cs += 64) {
       // capacity of the chunk's last column (the same test for every lane)
