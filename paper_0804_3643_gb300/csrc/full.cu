@@ -195,13 +195,15 @@ __device__ SideOut side_dp(const int8_t* A, int la, const int8_t* B, int lb, int
         *reinterpret_cast<uint2*>(Sp + w + 2) = make_uint2(v0, v1);
         *reinterpret_cast<uint32_t*>(hval + off + w) = __byte_perm(v0, v1, 0x5410u);  // the two H halves
       }
+      // (the key as r * 2048 + code: r >= 0 and code < 2048 for a live cell;
+      // a multiply-add leaves the ALU pipe, the bound, to the maxima)
       const int kc = 2047 - (j0 - o);
-      lkey = max(lkey, max(live0 ? (r0 << 11) | kc : -1, live1 ? (r1 << 11) | (kc - 1) : -1));
+      lkey = max(lkey, max(live0 ? r0 * 2048 + kc : -1, live1 ? r1 * 2048 + (kc - 1) : -1));
       llo = min(llo, live0 ? j0 : live1 ? j1 : 0x7fffffff);
       lhi = max(lhi, live1 ? j1 : live0 ? j0 : -1);
       // past the sequence end, or past the row above's reach with the
       // chunk's last cell dropped: the row ends
-      if (cs + 64 > lb || (cs + 63 >= lim && !__shfl_sync(0xffffffffu, (int)live1, 31))) break;
+      if (cs + 64 > lb || (cs + 63 >= lim && !(__ballot_sync(0xffffffffu, live1) >> 31))) break;
       // what the next chunk takes from this one's lane 31
       carryP = max(carryP, __shfl_sync(0xffffffffu, incl, 31));
       carry_sm = __shfl_sync(0xffffffffu, sv.y, 31);
